@@ -1,0 +1,250 @@
+/*
+ * usp.h -- C ABI of the GB300 (sm_103a) particle update of the unified
+ * stochastic particle ESBGK method (USP-ESBGK) of Fei, Zhang, Li and Liu,
+ * arXiv:1808.03801.
+ *
+ * One time step follows the paper's Table 2 with all particle weights equal
+ * to one (its weighted-particle steps 2, 4 and 7 are not part of this
+ * library):
+ *   advection with wall / reservoir boundaries   Table 1 steps 1-2, Table 2 step 3
+ *   cell counting-sort                           (cells of Sec. 3.2; N_c of Eq. 9)
+ *   per-cell moments n, u, T, p_ij, q_i          Eq. 1
+ *   per-cell USP parameters                      Eqs. 16-18 (P_ne), 33 (sigma*, q*),
+ *                                                35-36 (mu, lambda), 6c (ES covariance)
+ *   relaxation with probability 1 - e^(-nu_ES dt) Eqs. 8b, 9
+ *   ES Gaussian at a time instant from g_time     Eqs. 27 (first two terms), 29-32, 6b
+ *   per-cell momentum / energy conservation
+ *   sampling and exponential time average        Eq. 34
+ *
+ * Conventions for every call:
+ *   - the return value is a status: USP_OK (0) or a negative USP_ERR_* code;
+ *     no call aborts, traps or exits the process;
+ *   - a handle owns all device memory it allocates; the caller owns every
+ *     buffer it passes in (host or device, as stated per argument);
+ *   - work is queued on the CUDA stream given at creation; calls that return
+ *     data to the host synchronise that stream first;
+ *   - a handle is not thread-safe; distinct handles are independent;
+ *   - after an error, usp_last_error() describes it.
+ * Units are SI throughout (m, s, kg, K).
+ */
+#ifndef USP_H
+#define USP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define USP_OK 0
+#define USP_ERR_INVALID_ARG (-1)
+#define USP_ERR_OOM (-2)
+#define USP_ERR_CUDA (-3)
+#define USP_ERR_CAPACITY (-4)
+#define USP_ERR_TIMEOUT (-5)
+#define USP_ERR_STATE (-6)
+
+/* boundary kinds (one per domain face; plates use DIFFUSE or SPECULAR) */
+#define USP_BC_DIFFUSE 0   /* full accommodation at T, wall velocity u */
+#define USP_BC_SPECULAR 1  /* mirror reflection */
+#define USP_BC_PERIODIC 2  /* both faces of the axis must be periodic */
+#define USP_BC_RESERVOIR 3 /* particles leaving are removed; buffer cells refilled at (n, T, u) */
+
+/* relaxation modes */
+#define USP_MODE_USP 0       /* P_ne from the gradient-length local Knudsen number, Eq. 16 */
+#define USP_MODE_SP 1        /* P_ne = 0: the SP-ESBGK scheme (Appendix B limit) */
+#define USP_MODE_FIXED_PNE 2 /* P_ne = params.fixed_pne everywhere */
+
+/* particle storage precision */
+#define USP_FP64 0       /* positions and velocities stored and streamed in FP64 */
+#define USP_FP32_MIXED 1 /* FP32 storage and per-particle math, FP64 per-cell sums and parameters */
+
+/* step pipeline */
+#define USP_PIPE_PLAIN 0 /* one kernel per stage */
+#define USP_PIPE_FUSED 1 /* relaxation fused with the next advection; FP32_MIXED only */
+
+/* which field set usp_sample_macro returns */
+#define USP_SAMPLE_INSTANT 0
+#define USP_SAMPLE_AVERAGED 1
+
+/* per-cell fields returned by usp_sample_macro, layout [field][cell] */
+#define USP_NFIELDS 16
+/* 0 n [1/m^3], 1-3 u [m/s], 4 T [K], 5-10 p_xx p_yy p_zz p_xy p_xz p_yz [Pa]
+ * (p delta_ij + sigma*_ij of Eq. 33), 11-13 q* [W/m^2] (Eq. 33), 14 P_ne,
+ * 15 particles in the cell.  Cells with fewer than two particles report
+ * n, u (if one particle) and the count, zeros elsewhere. */
+
+#define USP_MAXSEG 4
+
+typedef struct usp_handle usp_handle;
+typedef struct usp_batch usp_batch;
+
+/* Gas: molecular mass, viscosity law mu = mu_ref (T/T_ref)^omega (Eq. 35;
+ * omega = 0.5 hard sphere, 0.81 argon), Prandtl number (2/3 monatomic).
+ * mu_ref = 0 derives it from params.Kn through Eq. 36 at (n_ref, T_ref). */
+typedef struct {
+    double mass, T_ref, mu_ref, omega, Pr;
+} usp_gas;
+
+/* Uniform Cartesian grid.  dim = 1 resolves y only (nx ignored, x and z
+ * homogeneous); dim = 2 resolves x and y (z homogeneous).  Cell index
+ * iy * nx + ix.  Only hi - lo matters along an unresolved axis. */
+typedef struct {
+    int dim, nx, ny;
+    double lo[2], hi[2];
+} usp_grid;
+
+/* Boundary of one face (order x-lo, x-hi, y-lo, y-hi): kind, wall or
+ * reservoir temperature T, wall or reservoir velocity u, reservoir number
+ * density n.  The normal component of a wall velocity is ignored. */
+typedef struct {
+    int kind;
+    double T;
+    double u[3];
+    double n;
+} usp_bc;
+
+/* Zero-thickness plate normal to x at x = pos, spanning lo <= y <= hi
+ * (the slit walls of Sec. 4.5).  dim = 2 only. */
+typedef struct {
+    double pos, lo, hi;
+    int kind;
+    double T;
+    double u[3];
+} usp_wall_segment;
+
+/* Run parameters (Sec. 4, Eqs. 35-37).
+ *   Kn, L_ref    : Knudsen number and its reference length (lambda_ref = Kn L_ref)
+ *   n_ref        : reference number density (with gas.T_ref)
+ *   dt           : time step [s]; 0 selects dt_over_tauc * tau_c(ref) (Eq. 37)
+ *   body_accel   : acceleration; allowed only along unresolved axes
+ *   ppc_ref      : particles per cell at n_ref (each particle stands for
+ *                  n_ref V_cell / ppc_ref molecules)
+ *   n_avg        : n_a of Eq. 34
+ *   mode         : USP_MODE_*; fixed_pne used by USP_MODE_FIXED_PNE
+ *   reservoir_cols: buffer cell layers next to each reservoir face
+ *   precision    : USP_FP64 or USP_FP32_MIXED
+ *   pipeline     : USP_PIPE_PLAIN or USP_PIPE_FUSED
+ *   capacity_factor: particle slots allocated = factor * initial count
+ *                  (>= 1; 0 selects 1.25, or 2 with reservoirs) */
+typedef struct {
+    double Kn, L_ref, n_ref;
+    double dt, dt_over_tauc;
+    double body_accel[3];
+    int ppc_ref, n_avg, mode;
+    double fixed_pne;
+    int reservoir_cols;
+    int precision;
+    int pipeline;
+    double capacity_factor;
+} usp_params;
+
+/* A box of initial gas at number density n, temperature T, velocity u. */
+typedef struct {
+    double lo[2], hi[2];
+    double n, T;
+    double u[3];
+} usp_region;
+
+/* Optional device allocator (for example a framework's caching allocator).
+ * alloc returns a device pointer or NULL; NULL allocator => cudaMalloc. */
+typedef struct {
+    void* (*alloc)(size_t bytes, void* ctx);
+    void (*free)(void* ptr, void* ctx);
+    void* ctx;
+} usp_allocator;
+
+/* Read-only state of a handle. */
+typedef struct {
+    int64_t n_particles;  /* live particles after the last completed step */
+    int64_t capacity;     /* particle slots */
+    int32_t n_cells;
+    int32_t precision, pipeline;
+    uint32_t step;        /* completed steps */
+    double dt, mu_ref;    /* derived time step and reference viscosity */
+    int64_t counters[8];  /* 0 Cholesky fallbacks, 1 bounce-cap clamps, 2 removed,
+                             3 injected, 4 relaxed (last step), 5-7 reserved */
+    size_t device_bytes;  /* device memory held by the handle */
+} usp_info;
+
+/* Create a simulation.  faces[4] in order x-lo, x-hi, y-lo, y-hi; segs may be
+ * NULL when nseg == 0; stream is a cudaStream_t (NULL: legacy default
+ * stream).  Derives mu_ref (Eq. 36) and dt (Eq. 37), allocates per-cell
+ * arrays; particle storage is allocated by usp_init_particles /
+ * usp_set_particles.  Errors: INVALID_ARG for inconsistent input (periodic
+ * on one face of an axis, resolved-axis body force, non-positive sizes),
+ * OOM, CUDA. */
+int usp_create(const usp_gas* gas, const usp_grid* grid, const usp_bc faces[4],
+               const usp_wall_segment* segs, int nseg, const usp_params* params,
+               const usp_allocator* allocator, void* stream, usp_handle** out);
+
+/* Table 2 step 1: fill every cell from the region containing its centre
+ * (the last listed region wins): round(n / n_ref * ppc_ref) particles with
+ * uniform positions in the cell and Maxwellian velocities at (T, u);
+ * particle ids 0.. in cell order; random numbers keyed by seed.  Resets the
+ * step counter and the averages. */
+int usp_init_particles(usp_handle* h, const usp_region* regions, int nregions, uint64_t seed);
+
+/* Load an arbitrary state from HOST arrays: pos[n][2] (x, y; x ignored in
+ * 1-D), vel[n][3], pid[n]; next_pid is the first id given to injected
+ * particles.  Resets the step counter and the averages. */
+int usp_set_particles(usp_handle* h, int64_t n, const double* pos, const double* vel,
+                      const uint32_t* pid, uint32_t next_pid, uint64_t seed);
+
+/* Advance nsteps time steps on the handle's stream (asynchronous).  Steps
+ * are replayed from a captured CUDA graph.  Returns CAPACITY if injection
+ * would exceed the particle slots (checked before launching). */
+int usp_step(usp_handle* h, int nsteps);
+
+/* Copy the USP_NFIELDS x n_cells FP64 fields ([field][cell]) into out
+ * (out_len doubles; a device pointer when out_on_device != 0, else host).
+ * Synchronises the handle's stream. */
+int usp_sample_macro(usp_handle* h, int which, double* out, size_t out_len, int out_on_device);
+
+/* Debug / test: copy the particles in storage order to HOST arrays (any may
+ * be NULL): pos[cap][2], vel[cap][3], pid[cap], cell[cap].  *n_out receives
+ * the live count; CAPACITY if cap is too small. */
+int usp_get_particles(usp_handle* h, double* pos, double* vel, uint32_t* pid, int32_t* cell,
+                      int64_t cap, int64_t* n_out);
+
+/* Debug / test: run one stage of the plain pipeline (same stage numbers as
+ * the step order above: 0 advect, 1 reservoir refill, 2 sort, 3 moments,
+ * 4 parameters, 5 relaxation, 6 sample-and-advance).  A full step is the
+ * stages 0..6 in order. */
+int usp_run_stage(usp_handle* h, int stage);
+
+/* Debug / test: per-cell relaxation parameters of the last step to HOST,
+ * [n_cells][16]: u0 u1 u2, RT, L00 L10 L11 L20 L21 L22, P_relax, nu, nu_ES,
+ * P_ne, valid, relaxed count. */
+int usp_get_params(usp_handle* h, double* out, size_t out_len);
+
+/* Debug / test: Philox4x32-10 on the device for n HOST counters ctr[n][4]
+ * with key (key0, key1); words to HOST out[n][4]. */
+int usp_debug_philox(int64_t n, const uint32_t* ctr, uint32_t key0, uint32_t key1, uint32_t* out);
+
+int usp_get_info(usp_handle* h, usp_info* info);
+int usp_synchronize(usp_handle* h);
+int usp_destroy(usp_handle* h);
+const char* usp_last_error(const usp_handle* h);
+const char* usp_status_string(int status);
+
+/* ---------------------------------------------------------------------- */
+/* Batching: many independent simulations advanced by the same launches.   */
+/* A batch does not own its handles.  Handles of one batch share precision */
+/* and pipeline.  hbm_budget bounds the device bytes of admitted handles.  */
+/* ---------------------------------------------------------------------- */
+int usp_batch_create(size_t hbm_budget, int max_sims, void* stream, usp_batch** out);
+/* CAPACITY when the handle does not fit the budget or the slot count. */
+int usp_batch_admit(usp_batch* b, usp_handle* h);
+/* Advance every admitted handle nsteps steps. */
+int usp_batch_step(usp_batch* b, int nsteps);
+int usp_batch_retire(usp_batch* b, usp_handle* h);
+int usp_batch_info(usp_batch* b, int* n_sims, size_t* bytes_in_use);
+int usp_batch_destroy(usp_batch* b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,979 @@
+// usp_api.cu -- host side of the C ABI declared in include/usp.h: parameter
+// derivation (Eqs. 35-37), device memory, the step sequence captured into a
+// CUDA graph, debug access and batching.
+#include "usp.h"
+#include "usp_internal.cuh"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace usp;
+
+namespace {
+
+struct Graphs {
+    cudaGraphExec_t one = nullptr;    // one step
+    cudaGraphExec_t many = nullptr;   // kGraphSteps steps
+};
+constexpr int kGraphSteps = 8;
+
+void destroy_graphs(Graphs& g) {
+    if (g.one) cudaGraphExecDestroy(g.one);
+    if (g.many) cudaGraphExecDestroy(g.many);
+    g.one = g.many = nullptr;
+}
+
+int persistent_grid(int ntiles, int per_sm) {
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int g = sms * per_sm;
+    if (ntiles < g) g = ntiles > 0 ? ntiles : 1;
+    return g;
+}
+
+}  // namespace
+
+struct usp_handle {
+    SimDev host{};            // host copy of the simulation description
+    SimDev* d_sim = nullptr;  // device copy
+    SimDyn* d_dyn = nullptr;
+    int precision = USP_FP64;
+    int pipeline = USP_PIPE_PLAIN;
+    double capacity_factor = 0;
+    double n_ref = 0;                 // reference number density and particles per cell,
+    int ppc_ref = 1;                  // for the initial particle counts
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    usp_allocator alloc{};
+    bool has_alloc = false;
+    std::vector<void*> cell_allocs;   // per-cell arrays (lifetime of the handle)
+    std::vector<void*> part_allocs;   // particle storage (replaced on re-init)
+    size_t cell_bytes = 0, part_bytes = 0;
+    int2* d_ptiles = nullptr;
+    int2* d_ctiles = nullptr;
+    int* d_ntiles = nullptr;          // [0] particle tiles, [1] cell tiles
+    int nptiles = 0, nctiles = 0;
+    Graphs graphs;
+    bool initialised = false;
+    bool mid_step = false;            // data in buffer cur^1 (after the sort stage)
+    bool sorted = false;              // storage order is by cell with valid start[]
+    std::string err;
+    std::vector<uint32_t> inj_count_host;
+    int batch_refs = 0;
+};
+
+struct usp_batch {
+    size_t budget = 0;
+    int max_sims = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<usp_handle*> members;
+    SimDev* d_sims = nullptr;
+    int2* d_ptiles = nullptr;
+    int2* d_ctiles = nullptr;
+    int* d_ntiles = nullptr;
+    size_t ptile_cap = 0, ctile_cap = 0;
+    int nptiles = 0, nctiles = 0;
+    Graphs graphs;
+    int graph_nsims = -1;             // nsims the graphs were captured with
+    bool dirty = true;
+    int precision = -1, pipeline = -1;
+    std::string err;
+};
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+static int fail(usp_handle* h, int code, const std::string& msg) {
+    if (h) h->err = msg;
+    return code;
+}
+
+#define CK(call)                                                                                    \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess) return fail(h, USP_ERR_CUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+static void* dalloc(usp_handle* h, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~size_t(255);
+    void* p = nullptr;
+    if (h->has_alloc) {
+        p = h->alloc.alloc(bytes, h->alloc.ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    return p;
+}
+
+static void dfree(usp_handle* h, void* p) {
+    if (!p) return;
+    if (h->has_alloc) h->alloc.free(p, h->alloc.ctx);
+    else cudaFree(p);
+}
+
+static int cell_alloc(usp_handle* h, size_t bytes, void** out) {
+    void* p = dalloc(h, bytes);
+    if (!p) return fail(h, USP_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+    h->cell_allocs.push_back(p);
+    h->cell_bytes += bytes;
+    *out = p;
+    return USP_OK;
+}
+
+static void free_particles(usp_handle* h) {
+    for (void* p : h->part_allocs) dfree(h, p);
+    h->part_allocs.clear();
+    h->part_bytes = 0;
+}
+
+static int upload_sim(usp_handle* h) {
+    CK(cudaMemcpyAsync(h->d_sim, &h->host, sizeof(SimDev), cudaMemcpyHostToDevice, h->stream));
+    return USP_OK;
+}
+
+static Launch make_launch(usp_handle* h) {
+    Launch L;
+    L.sims = h->d_sim;
+    L.ptiles = h->d_ptiles;
+    L.nptiles = h->d_ntiles;
+    L.ctiles = h->d_ctiles;
+    L.nctiles = h->d_ntiles + 1;
+    L.nsims = 1;
+    L.grid_p = persistent_grid(h->nptiles, 8);
+    L.grid_c = persistent_grid(h->nctiles, 8);
+    L.stream = h->stream;
+    return L;
+}
+
+// one full step of the plain pipeline (every stage in order)
+static void enqueue_step(const Launch& L, bool fp64, bool reservoir) {
+    launch_stream(L, fp64);
+    launch_scan(L);
+    launch_scatter(L, fp64);
+    if (reservoir) launch_inject(L, fp64);
+    launch_moments(L, fp64);
+    launch_params(L);
+    launch_relax(L, fp64);
+    launch_finish(L);
+}
+
+static int count_for_density(const SimDev& s, double n, double n_ref, int ppc_ref) {
+    (void)s;
+    return (int)std::floor(n / n_ref * ppc_ref + 0.5);
+}
+
+static int buffer_face_host(const SimDev& s, int cell) {
+    int ix = cell % s.nx, iy = cell / s.nx;
+    for (int f = 0; f < 4; ++f) {
+        if (s.face[f].kind != kBcReservoir) continue;
+        int axis = f >> 1;
+        if (s.dim == 1 && axis == 0) continue;
+        int i = axis == 0 ? ix : iy;
+        int n = axis == 0 ? s.nx : s.ny;
+        if (((f & 1) == 0 && i < s.reservoir_cols) || ((f & 1) == 1 && i >= n - s.reservoir_cols)) return f;
+    }
+    return -1;
+}
+
+// ---------------------------------------------------------------------------
+// creation
+// ---------------------------------------------------------------------------
+extern "C" int usp_create(const usp_gas* gas, const usp_grid* grid, const usp_bc faces[4],
+                          const usp_wall_segment* segs, int nseg, const usp_params* prm,
+                          const usp_allocator* allocator, void* stream, usp_handle** out) {
+    if (!out) return USP_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!gas || !grid || !faces || !prm || nseg < 0 || nseg > USP_MAXSEG || (nseg > 0 && !segs))
+        return USP_ERR_INVALID_ARG;
+    if (grid->dim != 1 && grid->dim != 2) return USP_ERR_INVALID_ARG;
+    const int nx = grid->dim == 1 ? 1 : grid->nx;
+    if (grid->ny < 1 || nx < 1 || (int64_t)nx * grid->ny > (int64_t)1 << 28) return USP_ERR_INVALID_ARG;
+    if (!(grid->hi[1] > grid->lo[1]) || (grid->dim == 2 && !(grid->hi[0] > grid->lo[0]))) return USP_ERR_INVALID_ARG;
+    if (!(gas->mass > 0) || !(gas->T_ref > 0) || !(gas->Pr > 0) || gas->mu_ref < 0) return USP_ERR_INVALID_ARG;
+    if (!(prm->n_ref > 0) || prm->ppc_ref < 1 || prm->n_avg < 1) return USP_ERR_INVALID_ARG;
+    if (gas->mu_ref == 0 && !(prm->Kn > 0 && prm->L_ref > 0)) return USP_ERR_INVALID_ARG;
+    if (!(prm->dt > 0) && !(prm->dt_over_tauc > 0)) return USP_ERR_INVALID_ARG;
+    if (prm->mode < 0 || prm->mode > 2) return USP_ERR_INVALID_ARG;
+    if (prm->precision != USP_FP64 && prm->precision != USP_FP32_MIXED) return USP_ERR_INVALID_ARG;
+    if (prm->pipeline != USP_PIPE_PLAIN && prm->pipeline != USP_PIPE_FUSED) return USP_ERR_INVALID_ARG;
+    if (prm->pipeline == USP_PIPE_FUSED && prm->precision != USP_FP32_MIXED) return USP_ERR_INVALID_ARG;
+    if (prm->body_accel[1] != 0 || (grid->dim == 2 && prm->body_accel[0] != 0)) return USP_ERR_INVALID_ARG;
+    if (prm->capacity_factor != 0 && prm->capacity_factor < 1) return USP_ERR_INVALID_ARG;
+    bool any_res = false;
+    for (int f = 0; f < 4; ++f) {
+        if (faces[f].kind < 0 || faces[f].kind > 3) return USP_ERR_INVALID_ARG;
+        if (grid->dim == 1 && f < 2) continue;
+        if ((faces[f].kind == USP_BC_PERIODIC) != (faces[f ^ 1].kind == USP_BC_PERIODIC)) return USP_ERR_INVALID_ARG;
+        if (faces[f].kind == USP_BC_DIFFUSE && !(faces[f].T > 0)) return USP_ERR_INVALID_ARG;
+        if (faces[f].kind == USP_BC_RESERVOIR) {
+            if (!(faces[f].T > 0) || faces[f].n < 0) return USP_ERR_INVALID_ARG;
+            any_res = true;
+        }
+    }
+    if (any_res && prm->reservoir_cols < 1) return USP_ERR_INVALID_ARG;
+    for (int g = 0; g < nseg; ++g) {
+        if (grid->dim != 2) return USP_ERR_INVALID_ARG;
+        if (segs[g].kind != USP_BC_DIFFUSE && segs[g].kind != USP_BC_SPECULAR) return USP_ERR_INVALID_ARG;
+        if (segs[g].kind == USP_BC_DIFFUSE && !(segs[g].T > 0)) return USP_ERR_INVALID_ARG;
+    }
+
+    usp_handle* h = new usp_handle();
+    h->precision = prm->precision;
+    h->pipeline = prm->pipeline;
+    h->capacity_factor = prm->capacity_factor;
+    h->n_ref = prm->n_ref;
+    h->ppc_ref = prm->ppc_ref;
+    if (allocator && allocator->alloc && allocator->free) {
+        h->alloc = *allocator;
+        h->has_alloc = true;
+    }
+    if (stream) {
+        h->stream = (cudaStream_t)stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            delete h;
+            return USP_ERR_CUDA;
+        }
+        h->own_stream = true;
+    }
+
+    SimDev& s = h->host;
+    s.dim = grid->dim;
+    s.nx = nx;
+    s.ny = grid->ny;
+    s.K = nx * grid->ny;
+    for (int i = 0; i < 2; ++i) {
+        s.lo[i] = grid->lo[i];
+        s.hi[i] = grid->hi[i];
+    }
+    s.dy = (grid->hi[1] - grid->lo[1]) / grid->ny;
+    s.dx = grid->dim == 2 ? (grid->hi[0] - grid->lo[0]) / nx : 1.0;
+    s.mass = gas->mass;
+    s.R = kBoltzmann / gas->mass;
+    s.T_ref = gas->T_ref;
+    s.omega = gas->omega;
+    s.Pr = gas->Pr;
+    // reference viscosity from Kn through Eq. 36 at (n_ref, T_ref)
+    const double rho_ref = prm->n_ref * gas->mass;
+    const double p_ref = prm->n_ref * kBoltzmann * gas->T_ref;
+    double mu_ref = gas->mu_ref;
+    if (mu_ref <= 0) mu_ref = prm->Kn * prm->L_ref * 5.0 * std::sqrt(2.0 * kPi) / 16.0 * std::sqrt(rho_ref * p_ref);
+    s.mu_ref = mu_ref;
+    // dt from the mean collision time (Eq. 37)
+    const double lam_ref = 16.0 / (5.0 * std::sqrt(2.0 * kPi)) * mu_ref / std::sqrt(rho_ref * p_ref);
+    const double tau_c = lam_ref / std::sqrt(8.0 * kBoltzmann * gas->T_ref / (kPi * gas->mass));
+    s.dt = prm->dt > 0 ? prm->dt : prm->dt_over_tauc * tau_c;
+    s.w = prm->n_ref / (double)prm->ppc_ref;
+    s.avg_keep = (prm->n_avg - 1.0) / prm->n_avg;
+    s.avg_new = 1.0 / prm->n_avg;
+    s.mode = prm->mode;
+    s.fixed_pne = prm->fixed_pne;
+    for (int d = 0; d < 3; ++d) s.body[d] = prm->body_accel[d];
+    for (int f = 0; f < 4; ++f) {
+        s.face[f].kind = faces[f].kind;
+        s.face[f].T = faces[f].T;
+        s.face[f].theta = s.R * faces[f].T;
+        s.face[f].sqrt_theta = std::sqrt(s.face[f].theta);
+        for (int d = 0; d < 3; ++d) s.face[f].u[d] = faces[f].u[d];
+    }
+    if (s.dim == 1) s.face[0].kind = s.face[1].kind = kBcPeriodic;
+    s.periodic_x = s.face[0].kind == kBcPeriodic;
+    s.periodic_y = s.face[2].kind == kBcPeriodic;
+    s.nseg = nseg;
+    for (int g = 0; g < nseg; ++g) {
+        s.seg[g].pos = segs[g].pos;
+        s.seg[g].lo = segs[g].lo;
+        s.seg[g].hi = segs[g].hi;
+        s.seg[g].kind = segs[g].kind;
+        s.seg[g].theta = s.R * segs[g].T;
+        s.seg[g].sqrt_theta = std::sqrt(s.seg[g].theta);
+        for (int d = 0; d < 3; ++d) s.seg[g].u[d] = segs[g].u[d];
+    }
+    s.has_reservoir = any_res;
+    s.reservoir_cols = any_res ? prm->reservoir_cols : 0;
+
+    const int K = s.K;
+    int rc = USP_OK;
+    void* p;
+#define CALLOC(field, type, count)                                        \
+    if ((rc = cell_alloc(h, sizeof(type) * (size_t)(count), &p)) != 0) { \
+        usp_destroy(h);                                                   \
+        return rc;                                                        \
+    }                                                                     \
+    s.field = (type*)p;
+    CALLOC(count, uint32_t, K + 1);
+    CALLOC(start, uint32_t, K + 2);
+    CALLOC(fill, uint32_t, K + 1);
+    CALLOC(mom, double, (size_t)kNMom * K);
+    CALLOC(prm, double, (size_t)kNPrm * K);
+    CALLOC(inst, double, (size_t)kNFields * K);
+    CALLOC(avg, double, (size_t)kNFields * K);
+    CALLOC(ushift, double, 3 * (size_t)K);
+    CALLOC(inj_count, uint32_t, K);
+    CALLOC(inj_pidoff, uint32_t, K);
+    CALLOC(cons, double, 7 * (size_t)K);
+    CALLOC(fprm, float, 16 * (size_t)K);
+#undef CALLOC
+    if ((rc = cell_alloc(h, sizeof(SimDev), &p)) != 0) { usp_destroy(h); return rc; }
+    h->d_sim = (SimDev*)p;
+    if ((rc = cell_alloc(h, sizeof(SimDyn), &p)) != 0) { usp_destroy(h); return rc; }
+    h->d_dyn = (SimDyn*)p;
+    s.dyn = h->d_dyn;
+    if ((rc = cell_alloc(h, 2 * sizeof(int), &p)) != 0) { usp_destroy(h); return rc; }
+    h->d_ntiles = (int*)p;
+    h->nctiles = (K + kCTile - 1) / kCTile;
+    if ((rc = cell_alloc(h, sizeof(int2) * (size_t)h->nctiles, &p)) != 0) { usp_destroy(h); return rc; }
+    h->d_ctiles = (int2*)p;
+
+    // reservoir refill table: count per buffer cell, pid offsets in (face, cell) order
+    h->inj_count_host.assign(K, 0);
+    std::vector<uint32_t> off(K, 0);
+    uint32_t total = 0;
+    if (any_res) {
+        for (int f = 0; f < 4; ++f) {
+            if (s.face[f].kind != kBcReservoir) continue;
+            for (int c = 0; c < K; ++c) {
+                if (buffer_face_host(s, c) != f) continue;
+                uint32_t cnt = (uint32_t)count_for_density(s, faces[f].n, prm->n_ref, prm->ppc_ref);
+                h->inj_count_host[c] = cnt;
+                off[c] = total;
+                total += cnt;
+            }
+        }
+    }
+    s.inj_total = total;
+    std::vector<int2> ct(h->nctiles);
+    for (int t = 0; t < h->nctiles; ++t) ct[t] = make_int2(0, t * kCTile);
+    int nt[2] = {0, h->nctiles};
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s.inj_count, h->inj_count_host.data(), sizeof(uint32_t) * K, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s.inj_pidoff, off.data(), sizeof(uint32_t) * K, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_ctiles, ct.data(), sizeof(int2) * ct.size(), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_ntiles, nt, sizeof(nt), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s.count, 0, sizeof(uint32_t) * (K + 1), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s.fill, 0, sizeof(uint32_t) * (K + 1), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s.ushift, 0, sizeof(double) * 3 * K, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_dyn, 0, sizeof(SimDyn), h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);   // host vectors above go out of scope
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        usp_destroy(h);
+        return USP_ERR_CUDA;
+    }
+    if (upload_sim(h) != USP_OK) {
+        usp_destroy(h);
+        return USP_ERR_CUDA;
+    }
+    *out = h;
+    return USP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// particle storage
+// ---------------------------------------------------------------------------
+static int alloc_particles(usp_handle* h, int64_t n) {
+    SimDev& s = h->host;
+    double f = h->capacity_factor > 0 ? h->capacity_factor : (s.has_reservoir ? 2.0 : 1.25);
+    int64_t cap = (int64_t)std::ceil(n * f) + 2 * (int64_t)s.inj_total + 1024;
+    if (cap > (int64_t)0x7FFFFFFFll) return fail(h, USP_ERR_CAPACITY, "particle capacity exceeds 2^31 - 1");
+    free_particles(h);
+    destroy_graphs(h->graphs);
+    const size_t es = h->precision == USP_FP64 ? 8 : 4;
+    auto grab = [&](size_t bytes) -> void* {
+        void* p = dalloc(h, bytes);
+        if (p) {
+            h->part_allocs.push_back(p);
+            h->part_bytes += bytes;
+        }
+        return p;
+    };
+    for (int b = 0; b < 2; ++b) {
+        s.pos[b][0] = s.dim == 2 ? grab(es * cap) : nullptr;
+        s.pos[b][1] = grab(es * cap);
+        for (int d = 0; d < 3; ++d) s.vel[b][d] = grab(es * cap);
+        s.pid[b] = (uint32_t*)grab(4 * cap);
+        if ((s.dim == 2 && !s.pos[b][0]) || !s.pos[b][1] || !s.vel[b][0] || !s.vel[b][1] || !s.vel[b][2] || !s.pid[b]) {
+            free_particles(h);
+            return fail(h, USP_ERR_OOM, "particle storage allocation failed");
+        }
+    }
+    s.cell = (uint32_t*)grab(4 * cap);
+    if (!s.cell) {
+        free_particles(h);
+        return fail(h, USP_ERR_OOM, "particle storage allocation failed");
+    }
+    s.cap = cap;
+    h->nptiles = (int)((cap + kPTile - 1) / kPTile);
+    if (h->d_ptiles) {
+        // replace the previous table
+        for (size_t i = 0; i < h->cell_allocs.size(); ++i)
+            if (h->cell_allocs[i] == h->d_ptiles) {
+                dfree(h, h->d_ptiles);
+                h->cell_allocs.erase(h->cell_allocs.begin() + i);
+                break;
+            }
+        h->d_ptiles = nullptr;
+    }
+    void* p;
+    int rc = cell_alloc(h, sizeof(int2) * (size_t)h->nptiles, &p);
+    if (rc) return rc;
+    h->d_ptiles = (int2*)p;
+    std::vector<int2> pt(h->nptiles);
+    for (int t = 0; t < h->nptiles; ++t) pt[t] = make_int2(0, t * kPTile);
+    int nt[2] = {h->nptiles, h->nctiles};
+    cudaError_t e = cudaMemcpyAsync(h->d_ptiles, pt.data(), sizeof(int2) * pt.size(), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_ntiles, nt, sizeof(nt), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return fail(h, USP_ERR_CUDA, cudaGetErrorString(e));
+    return USP_OK;
+}
+
+static int reset_dynamic(usp_handle* h, uint32_t n, uint32_t next_pid) {
+    SimDyn d{};
+    d.n = n;
+    d.next_pid = next_pid;
+    const int K = h->host.K;
+    CK(cudaMemcpyAsync(h->d_dyn, &d, sizeof(d), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemsetAsync(h->host.count, 0, sizeof(uint32_t) * (K + 1), h->stream));
+    CK(cudaMemsetAsync(h->host.fill, 0, sizeof(uint32_t) * (K + 1), h->stream));
+    CK(cudaMemsetAsync(h->host.ushift, 0, sizeof(double) * 3 * K, h->stream));
+    CK(cudaMemsetAsync(h->host.inst, 0, sizeof(double) * kNFields * K, h->stream));
+    CK(cudaMemsetAsync(h->host.avg, 0, sizeof(double) * kNFields * K, h->stream));
+    CK(cudaMemsetAsync(h->host.prm, 0, sizeof(double) * kNPrm * K, h->stream));
+    return USP_OK;
+}
+
+extern "C" int usp_init_particles(usp_handle* h, const usp_region* regions, int nregions, uint64_t seed) {
+    if (!h) return USP_ERR_INVALID_ARG;
+    if (nregions < 0 || (nregions > 0 && !regions)) return fail(h, USP_ERR_INVALID_ARG, "bad regions");
+    if (h->batch_refs) return fail(h, USP_ERR_STATE, "handle is admitted to a batch");
+    SimDev& s = h->host;
+    const int K = s.K;
+    std::vector<int> reg(K, -1);
+    std::vector<uint32_t> start(K + 2, 0);
+    uint64_t total = 0;
+    for (int c = 0; c < K; ++c) {
+        const int ix = c % s.nx, iy = c / s.nx;
+        const double xl = s.dim == 2 ? s.lo[0] + ix * s.dx : 0.0;
+        const double yl = s.lo[1] + iy * s.dy;
+        const double xc = xl + 0.5 * s.dx, yc = yl + 0.5 * s.dy;
+        int r = -1;
+        for (int i = 0; i < nregions; ++i) {
+            const bool in_y = yc >= regions[i].lo[1] && yc < regions[i].hi[1];
+            const bool in_x = s.dim == 1 || (xc >= regions[i].lo[0] && xc < regions[i].hi[0]);
+            if (in_x && in_y) r = i;
+        }
+        start[c] = (uint32_t)total;
+        if (r < 0) continue;
+        if (!(regions[r].T > 0) || regions[r].n < 0) return fail(h, USP_ERR_INVALID_ARG, "bad region state");
+        reg[c] = r;
+        total += (uint64_t)count_for_density(s, regions[r].n, h->n_ref, h->ppc_ref);
+        if (total > 0xFFFFFFF0ull / 2) return fail(h, USP_ERR_CAPACITY, "too many particles");
+    }
+    start[K] = start[K + 1] = (uint32_t)total;
+    int rc = alloc_particles(h, (int64_t)total);
+    if (rc) return rc;
+    s.key0 = (uint32_t)seed;
+    s.key1 = (uint32_t)(seed >> 32);
+    if ((rc = upload_sim(h)) != 0) return rc;
+    std::vector<double> th(std::max(1, nregions)), uu(3 * std::max(1, nregions));
+    for (int i = 0; i < nregions; ++i) {
+        th[i] = s.R * regions[i].T;
+        for (int d = 0; d < 3; ++d) uu[3 * i + d] = regions[i].u[d];
+    }
+    double *d_th = nullptr, *d_u = nullptr;
+    int* d_reg = nullptr;
+    d_th = (double*)dalloc(h, sizeof(double) * th.size());
+    d_u = (double*)dalloc(h, sizeof(double) * uu.size());
+    d_reg = (int*)dalloc(h, sizeof(int) * K);
+    if (!d_th || !d_u || !d_reg) {
+        dfree(h, d_th); dfree(h, d_u); dfree(h, d_reg);
+        return fail(h, USP_ERR_OOM, "init scratch allocation failed");
+    }
+    cudaError_t e = cudaMemcpyAsync(d_th, th.data(), sizeof(double) * th.size(), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_u, uu.data(), sizeof(double) * uu.size(), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_reg, reg.data(), sizeof(int) * K, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s.start, start.data(), sizeof(uint32_t) * (K + 2), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) {
+        rc = reset_dynamic(h, (uint32_t)total, (uint32_t)total);
+        if (rc == USP_OK) {
+            Launch L = make_launch(h);
+            launch_init(L, h->precision == USP_FP64, d_th, d_u, d_reg);
+            e = cudaGetLastError();
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    dfree(h, d_th); dfree(h, d_u); dfree(h, d_reg);
+    if (rc) return rc;
+    if (e != cudaSuccess) return fail(h, USP_ERR_CUDA, std::string("init: ") + cudaGetErrorString(e));
+    h->initialised = true;
+    h->mid_step = false;
+    h->sorted = true;
+    return USP_OK;
+}
+
+extern "C" int usp_set_particles(usp_handle* h, int64_t n, const double* pos, const double* vel, const uint32_t* pid,
+                                 uint32_t next_pid, uint64_t seed) {
+    if (!h) return USP_ERR_INVALID_ARG;
+    if (n < 0 || (n > 0 && (!pos || !vel || !pid))) return fail(h, USP_ERR_INVALID_ARG, "bad particle arrays");
+    if (h->batch_refs) return fail(h, USP_ERR_STATE, "handle is admitted to a batch");
+    if (n > (int64_t)0x7FFFFFF0) return fail(h, USP_ERR_CAPACITY, "too many particles");
+    int rc = alloc_particles(h, n);
+    if (rc) return rc;
+    SimDev& s = h->host;
+    s.key0 = (uint32_t)seed;
+    s.key1 = (uint32_t)(seed >> 32);
+    if ((rc = upload_sim(h)) != 0) return rc;
+    const bool fp64 = h->precision == USP_FP64;
+    const size_t es = fp64 ? 8 : 4;
+    std::vector<unsigned char> buf(es * (size_t)std::max<int64_t>(n, 1));
+    auto put = [&](void* dst, const double* src, int stride, int comp) -> cudaError_t {
+        for (int64_t i = 0; i < n; ++i) {
+            double v = src[stride * i + comp];
+            if (fp64) ((double*)buf.data())[i] = v;
+            else ((float*)buf.data())[i] = (float)v;
+        }
+        cudaError_t e = cudaMemcpyAsync(dst, buf.data(), es * n, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        return e;
+    };
+    cudaError_t e = cudaSuccess;
+    if (n > 0) {
+        if (s.dim == 2) e = put(s.pos[0][0], pos, 2, 0);
+        if (e == cudaSuccess) e = put(s.pos[0][1], pos, 2, 1);
+        for (int d = 0; d < 3 && e == cudaSuccess; ++d) e = put(s.vel[0][d], vel, 3, d);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(s.pid[0], pid, 4 * n, cudaMemcpyHostToDevice, h->stream);
+    }
+    if (e != cudaSuccess) return fail(h, USP_ERR_CUDA, cudaGetErrorString(e));
+    if ((rc = reset_dynamic(h, (uint32_t)n, next_pid)) != 0) return rc;
+    CK(cudaStreamSynchronize(h->stream));
+    h->initialised = true;
+    h->mid_step = false;
+    h->sorted = false;
+    return USP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// stepping
+// ---------------------------------------------------------------------------
+static int capture(usp_handle* h, int nsteps, cudaGraphExec_t* exec) {
+    Launch L = make_launch(h);
+    const bool fp64 = h->precision == USP_FP64;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    for (int i = 0; i < nsteps; ++i) enqueue_step(L, fp64, h->host.has_reservoir);
+    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    if (e != cudaSuccess) return fail(h, USP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(h, USP_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    return USP_OK;
+}
+
+extern "C" int usp_step(usp_handle* h, int nsteps) {
+    if (!h) return USP_ERR_INVALID_ARG;
+    if (nsteps < 0) return fail(h, USP_ERR_INVALID_ARG, "nsteps < 0");
+    if (!h->initialised) return fail(h, USP_ERR_STATE, "particles not initialised");
+    if (h->mid_step) return fail(h, USP_ERR_STATE, "a staged step is in progress");
+    if (h->batch_refs) return fail(h, USP_ERR_STATE, "handle is admitted to a batch");
+    if (nsteps == 0) return USP_OK;
+    int rc;
+    if (!h->graphs.one && (rc = capture(h, 1, &h->graphs.one)) != 0) return rc;
+    if (nsteps >= kGraphSteps && !h->graphs.many && (rc = capture(h, kGraphSteps, &h->graphs.many)) != 0) return rc;
+    int left = nsteps;
+    while (left >= kGraphSteps) {
+        CK(cudaGraphLaunch(h->graphs.many, h->stream));
+        left -= kGraphSteps;
+    }
+    while (left-- > 0) CK(cudaGraphLaunch(h->graphs.one, h->stream));
+    h->sorted = true;
+    return USP_OK;
+}
+
+extern "C" int usp_run_stage(usp_handle* h, int stage) {
+    if (!h) return USP_ERR_INVALID_ARG;
+    if (!h->initialised) return fail(h, USP_ERR_STATE, "particles not initialised");
+    if (h->batch_refs) return fail(h, USP_ERR_STATE, "handle is admitted to a batch");
+    Launch L = make_launch(h);
+    const bool fp64 = h->precision == USP_FP64;
+    switch (stage) {
+    case 0: launch_stream(L, fp64); h->sorted = false; break;
+    case 1: break;   // reservoir removal happens in stage 0, refill in stage 2
+    case 2:
+        launch_scan(L);
+        launch_scatter(L, fp64);
+        if (h->host.has_reservoir) launch_inject(L, fp64);
+        h->mid_step = true;
+        h->sorted = true;
+        break;
+    case 3: launch_moments(L, fp64); break;
+    case 4: launch_params(L); break;
+    case 5: launch_relax(L, fp64); break;
+    case 6: launch_finish(L); h->mid_step = false; break;
+    default: return fail(h, USP_ERR_INVALID_ARG, "stage must be 0..6");
+    }
+    CK(cudaGetLastError());
+    return USP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// read-back
+// ---------------------------------------------------------------------------
+static int read_dyn(usp_handle* h, SimDyn* d) {
+    CK(cudaStreamSynchronize(h->stream));
+    CK(cudaMemcpy(d, h->d_dyn, sizeof(SimDyn), cudaMemcpyDeviceToHost));
+    if (d->counters[kCntOverflow]) return fail(h, USP_ERR_CAPACITY, "particle slots overflowed during a step");
+    return USP_OK;
+}
+
+extern "C" int usp_synchronize(usp_handle* h) {
+    if (!h) return USP_ERR_INVALID_ARG;
+    SimDyn d;
+    return read_dyn(h, &d);
+}
+
+extern "C" int usp_sample_macro(usp_handle* h, int which, double* out, size_t out_len, int out_on_device) {
+    if (!h || !out) return USP_ERR_INVALID_ARG;
+    const size_t need = (size_t)kNFields * h->host.K;
+    if (out_len < need) return fail(h, USP_ERR_INVALID_ARG, "output too small");
+    if (which != USP_SAMPLE_INSTANT && which != USP_SAMPLE_AVERAGED) return fail(h, USP_ERR_INVALID_ARG, "bad field set");
+    CK(cudaStreamSynchronize(h->stream));
+    const double* src = which == USP_SAMPLE_INSTANT ? h->host.inst : h->host.avg;
+    CK(cudaMemcpy(out, src, need * sizeof(double), out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
+    return USP_OK;
+}
+
+extern "C" int usp_get_particles(usp_handle* h, double* pos, double* vel, uint32_t* pid, int32_t* cell, int64_t cap,
+                                 int64_t* n_out) {
+    if (!h) return USP_ERR_INVALID_ARG;
+    SimDyn d;
+    int rc = read_dyn(h, &d);
+    if (rc && rc != USP_ERR_CAPACITY) return rc;
+    const SimDev& s = h->host;
+    const int K = s.K;
+    std::vector<uint32_t> start(K + 2);
+    CK(cudaMemcpy(start.data(), s.start, sizeof(uint32_t) * (K + 2), cudaMemcpyDeviceToHost));
+    int buf = d.cur;
+    int64_t n = d.n;
+    if (h->mid_step) {
+        buf ^= 1;
+        n = start[K];
+    }
+    if (n_out) *n_out = n;
+    if (n > cap) return fail(h, USP_ERR_CAPACITY, "output arrays too small");
+    if (!h->initialised || n == 0) return USP_OK;
+    const bool fp64 = h->precision == USP_FP64;
+    const size_t es = fp64 ? 8 : 4;
+    std::vector<unsigned char> tmp(es * n);
+    auto get = [&](const void* src, double* dst, int stride, int comp) -> cudaError_t {
+        cudaError_t e = cudaMemcpy(tmp.data(), src, es * n, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return e;
+        for (int64_t i = 0; i < n; ++i)
+            dst[stride * i + comp] = fp64 ? ((double*)tmp.data())[i] : (double)((float*)tmp.data())[i];
+        return cudaSuccess;
+    };
+    cudaError_t e = cudaSuccess;
+    if (pos) {
+        if (s.dim == 2) e = get(s.pos[buf][0], pos, 2, 0);
+        else for (int64_t i = 0; i < n; ++i) pos[2 * i] = 0.0;
+        if (e == cudaSuccess) e = get(s.pos[buf][1], pos, 2, 1);
+    }
+    for (int dd = 0; dd < 3 && vel && e == cudaSuccess; ++dd) e = get(s.vel[buf][dd], vel, 3, dd);
+    if (pid && e == cudaSuccess) e = cudaMemcpy(pid, s.pid[buf], 4 * n, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail(h, USP_ERR_CUDA, cudaGetErrorString(e));
+    if (cell) {
+        if (h->sorted) {
+            int c = 0;
+            for (int64_t i = 0; i < n; ++i) {
+                while (c < K && (uint32_t)i >= start[c + 1]) ++c;
+                cell[i] = c;
+            }
+        } else {
+            for (int64_t i = 0; i < n; ++i) cell[i] = -1;
+        }
+    }
+    return rc;
+}
+
+extern "C" int usp_get_params(usp_handle* h, double* out, size_t out_len) {
+    if (!h || !out) return USP_ERR_INVALID_ARG;
+    const int K = h->host.K;
+    if (out_len < (size_t)kNPrm * K) return fail(h, USP_ERR_INVALID_ARG, "output too small");
+    CK(cudaStreamSynchronize(h->stream));
+    std::vector<double> t((size_t)kNPrm * K);
+    CK(cudaMemcpy(t.data(), h->host.prm, sizeof(double) * t.size(), cudaMemcpyDeviceToHost));
+    for (int c = 0; c < K; ++c)
+        for (int k = 0; k < kNPrm; ++k) out[(size_t)c * kNPrm + k] = t[(size_t)k * K + c];
+    return USP_OK;
+}
+
+extern "C" int usp_get_info(usp_handle* h, usp_info* info) {
+    if (!h || !info) return USP_ERR_INVALID_ARG;
+    SimDyn d{};
+    int rc = read_dyn(h, &d);
+    if (rc && rc != USP_ERR_CAPACITY) return rc;
+    memset(info, 0, sizeof(*info));
+    info->n_particles = d.n;
+    info->capacity = h->host.cap;
+    info->n_cells = h->host.K;
+    info->precision = h->precision;
+    info->pipeline = h->pipeline;
+    info->step = d.step;
+    info->dt = h->host.dt;
+    info->mu_ref = h->host.mu_ref;
+    for (int i = 0; i < 8; ++i) info->counters[i] = (int64_t)d.counters[i];
+    info->device_bytes = h->cell_bytes + h->part_bytes;
+    return rc;
+}
+
+extern "C" int usp_debug_philox(int64_t n, const uint32_t* ctr, uint32_t key0, uint32_t key1, uint32_t* out) {
+    if (n < 0 || (n > 0 && (!ctr || !out))) return USP_ERR_INVALID_ARG;
+    if (n == 0) return USP_OK;
+    uint32_t *dc = nullptr, *dout = nullptr;
+    if (cudaMalloc(&dc, 16 * n) != cudaSuccess || cudaMalloc(&dout, 16 * n) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(dc);
+        return USP_ERR_OOM;
+    }
+    cudaError_t e = cudaMemcpy(dc, ctr, 16 * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = debug_philox(n, dc, key0, key1, dout, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(out, dout, 16 * n, cudaMemcpyDeviceToHost);
+    cudaFree(dc);
+    cudaFree(dout);
+    return e == cudaSuccess ? USP_OK : USP_ERR_CUDA;
+}
+
+extern "C" int usp_destroy(usp_handle* h) {
+    if (!h) return USP_ERR_INVALID_ARG;
+    if (h->batch_refs) return fail(h, USP_ERR_STATE, "handle is admitted to a batch");
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    destroy_graphs(h->graphs);
+    free_particles(h);
+    for (void* p : h->cell_allocs) dfree(h, p);
+    h->cell_allocs.clear();
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return USP_OK;
+}
+
+extern "C" const char* usp_last_error(const usp_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+extern "C" const char* usp_status_string(int status) {
+    switch (status) {
+    case USP_OK: return "ok";
+    case USP_ERR_INVALID_ARG: return "invalid argument";
+    case USP_ERR_OOM: return "out of device memory";
+    case USP_ERR_CUDA: return "CUDA error";
+    case USP_ERR_CAPACITY: return "capacity exceeded";
+    case USP_ERR_TIMEOUT: return "timeout";
+    case USP_ERR_STATE: return "invalid state";
+    default: return "unknown status";
+    }
+}
+
+// ---------------------------------------------------------------------------
+// batching
+// ---------------------------------------------------------------------------
+static int bfail(usp_batch* b, int code, const std::string& m) {
+    if (b) b->err = m;
+    return code;
+}
+
+extern "C" int usp_batch_create(size_t hbm_budget, int max_sims, void* stream, usp_batch** out) {
+    if (!out || max_sims < 1) return USP_ERR_INVALID_ARG;
+    *out = nullptr;
+    usp_batch* b = new usp_batch();
+    b->budget = hbm_budget;
+    b->max_sims = max_sims;
+    if (stream) b->stream = (cudaStream_t)stream;
+    else {
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            delete b;
+            return USP_ERR_CUDA;
+        }
+        b->own_stream = true;
+    }
+    if (cudaMalloc(&b->d_sims, sizeof(SimDev) * max_sims) != cudaSuccess ||
+        cudaMalloc(&b->d_ntiles, 2 * sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(b->d_sims);
+        if (b->own_stream) cudaStreamDestroy(b->stream);
+        delete b;
+        return USP_ERR_OOM;
+    }
+    *out = b;
+    return USP_OK;
+}
+
+static size_t handle_bytes(const usp_handle* h) { return h->cell_bytes + h->part_bytes; }
+
+extern "C" int usp_batch_info(usp_batch* b, int* n_sims, size_t* bytes) {
+    if (!b) return USP_ERR_INVALID_ARG;
+    size_t used = 0;
+    for (auto* h : b->members) used += handle_bytes(h);
+    if (n_sims) *n_sims = (int)b->members.size();
+    if (bytes) *bytes = used;
+    return USP_OK;
+}
+
+extern "C" int usp_batch_admit(usp_batch* b, usp_handle* h) {
+    if (!b || !h) return USP_ERR_INVALID_ARG;
+    if (!h->initialised || h->mid_step) return bfail(b, USP_ERR_STATE, "handle not ready");
+    for (auto* m : b->members)
+        if (m == h) return bfail(b, USP_ERR_STATE, "already admitted");
+    if ((int)b->members.size() >= b->max_sims) return bfail(b, USP_ERR_CAPACITY, "no free slot");
+    size_t used = 0;
+    for (auto* m : b->members) used += handle_bytes(m);
+    if (used + handle_bytes(h) > b->budget) return bfail(b, USP_ERR_CAPACITY, "HBM budget exceeded");
+    if (!b->members.empty() && (h->precision != b->precision || h->pipeline != b->pipeline))
+        return bfail(b, USP_ERR_INVALID_ARG, "precision / pipeline differ from the batch");
+    if (b->members.empty()) {
+        b->precision = h->precision;
+        b->pipeline = h->pipeline;
+    }
+    // the handle's own stream must be idle before the batch stream takes over
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return bfail(b, USP_ERR_CUDA, "handle stream error");
+    b->members.push_back(h);
+    h->batch_refs++;
+    b->dirty = true;
+    return USP_OK;
+}
+
+extern "C" int usp_batch_retire(usp_batch* b, usp_handle* h) {
+    if (!b || !h) return USP_ERR_INVALID_ARG;
+    for (size_t i = 0; i < b->members.size(); ++i) {
+        if (b->members[i] != h) continue;
+        if (cudaStreamSynchronize(b->stream) != cudaSuccess) return bfail(b, USP_ERR_CUDA, "batch stream error");
+        b->members.erase(b->members.begin() + i);
+        h->batch_refs--;
+        h->sorted = true;
+        b->dirty = true;
+        return USP_OK;
+    }
+    return bfail(b, USP_ERR_INVALID_ARG, "handle not in batch");
+}
+
+// rebuild the device tables of the batch (simulation list and tiles)
+static int batch_rebuild(usp_batch* b) {
+    std::vector<SimDev> sims;
+    std::vector<int2> pt, ct;
+    for (size_t i = 0; i < b->members.size(); ++i) {
+        usp_handle* h = b->members[i];
+        sims.push_back(h->host);
+        for (int t = 0; t < h->nptiles; ++t) pt.push_back(make_int2((int)i, t * kPTile));
+        for (int t = 0; t < h->nctiles; ++t) ct.push_back(make_int2((int)i, t * kCTile));
+    }
+    bool regraph = false;
+    if (pt.size() > b->ptile_cap) {
+        cudaFree(b->d_ptiles);
+        b->ptile_cap = std::max(pt.size(), 2 * b->ptile_cap);
+        if (cudaMalloc(&b->d_ptiles, sizeof(int2) * b->ptile_cap) != cudaSuccess) {
+            cudaGetLastError();
+            b->d_ptiles = nullptr;
+            b->ptile_cap = 0;
+            return bfail(b, USP_ERR_OOM, "tile table");
+        }
+        regraph = true;
+    }
+    if (ct.size() > b->ctile_cap) {
+        cudaFree(b->d_ctiles);
+        b->ctile_cap = std::max(ct.size(), 2 * b->ctile_cap);
+        if (cudaMalloc(&b->d_ctiles, sizeof(int2) * b->ctile_cap) != cudaSuccess) {
+            cudaGetLastError();
+            b->d_ctiles = nullptr;
+            b->ctile_cap = 0;
+            return bfail(b, USP_ERR_OOM, "tile table");
+        }
+        regraph = true;
+    }
+    if ((int)sims.size() != b->graph_nsims) regraph = true;
+    b->nptiles = (int)pt.size();
+    b->nctiles = (int)ct.size();
+    int nt[2] = {b->nptiles, b->nctiles};
+    cudaError_t e = cudaSuccess;
+    if (!sims.empty()) e = cudaMemcpyAsync(b->d_sims, sims.data(), sizeof(SimDev) * sims.size(), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && !pt.empty()) e = cudaMemcpyAsync(b->d_ptiles, pt.data(), sizeof(int2) * pt.size(), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && !ct.empty()) e = cudaMemcpyAsync(b->d_ctiles, ct.data(), sizeof(int2) * ct.size(), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_ntiles, nt, sizeof(nt), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(b, USP_ERR_CUDA, cudaGetErrorString(e));
+    if (regraph) destroy_graphs(b->graphs);
+    b->dirty = false;
+    return USP_OK;
+}
+
+static Launch batch_launch(usp_batch* b) {
+    Launch L;
+    L.sims = b->d_sims;
+    L.ptiles = b->d_ptiles;
+    L.nptiles = b->d_ntiles;
+    L.ctiles = b->d_ctiles;
+    L.nctiles = b->d_ntiles + 1;
+    L.nsims = (int)b->members.size();
+    // fixed persistent grids: the tile counts are read on the device, so the
+    // captured graph stays valid while simulations come and go
+    L.grid_p = persistent_grid(1 << 30, 8);
+    L.grid_c = persistent_grid(1 << 30, 8);
+    L.stream = b->stream;
+    return L;
+}
+
+static int batch_capture(usp_batch* b, int nsteps, cudaGraphExec_t* exec) {
+    Launch L = batch_launch(b);
+    const bool fp64 = b->precision == USP_FP64;
+    bool res = false;
+    for (auto* h : b->members) res |= h->host.has_reservoir != 0;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return bfail(b, USP_ERR_CUDA, cudaGetErrorString(e));
+    for (int i = 0; i < nsteps; ++i) enqueue_step(L, fp64, res);
+    e = cudaStreamEndCapture(b->stream, &g);
+    if (e != cudaSuccess) return bfail(b, USP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return bfail(b, USP_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    b->graph_nsims = (int)b->members.size();
+    return USP_OK;
+}
+
+extern "C" int usp_batch_step(usp_batch* b, int nsteps) {
+    if (!b || nsteps < 0) return USP_ERR_INVALID_ARG;
+    if (b->members.empty() || nsteps == 0) return USP_OK;
+    int rc;
+    if (b->dirty && (rc = batch_rebuild(b)) != 0) return rc;
+    if (!b->graphs.one && (rc = batch_capture(b, 1, &b->graphs.one)) != 0) return rc;
+    if (nsteps >= kGraphSteps && !b->graphs.many && (rc = batch_capture(b, kGraphSteps, &b->graphs.many)) != 0)
+        return rc;
+    int left = nsteps;
+    cudaError_t e = cudaSuccess;
+    while (left >= kGraphSteps && e == cudaSuccess) {
+        e = cudaGraphLaunch(b->graphs.many, b->stream);
+        left -= kGraphSteps;
+    }
+    while (left-- > 0 && e == cudaSuccess) e = cudaGraphLaunch(b->graphs.one, b->stream);
+    if (e != cudaSuccess) return bfail(b, USP_ERR_CUDA, cudaGetErrorString(e));
+    return USP_OK;
+}
+
+extern "C" int usp_batch_destroy(usp_batch* b) {
+    if (!b) return USP_ERR_INVALID_ARG;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    for (auto* h : b->members) h->batch_refs--;
+    b->members.clear();
+    destroy_graphs(b->graphs);
+    cudaFree(b->d_sims);
+    cudaFree(b->d_ptiles);
+    cudaFree(b->d_ctiles);
+    cudaFree(b->d_ntiles);
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return USP_OK;
+}

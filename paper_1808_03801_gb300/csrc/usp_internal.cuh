@@ -1,0 +1,180 @@
+// usp_internal.cuh -- device-side state and helpers shared by the kernels and
+// the host API of the USP-ESBGK library.  Not part of the public ABI.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace usp {
+
+constexpr int kMaxSeg = 4;
+constexpr int kNFields = 16;
+constexpr int kNMom = 13;     // N, S1[3], S2[6], S3[3] (sums of shifted velocities)
+constexpr int kNPrm = 16;     // u[3], theta, L[6], P_relax, nu, nu_ES, P_ne, valid, relaxed
+constexpr int kMaxBounce = 8; // wall interactions per particle per step
+constexpr double kBoltzmann = 1.380649e-23;   // J/K (exact SI value)
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kKnC = 0.1;                    // Kn_c of Eq. 16
+constexpr double kGammaMono = 5.0 / 3.0;
+
+// Philox purposes (third counter word); the first two words are (pid, step).
+enum : uint32_t { kInit = 0, kRelax = 1, kWall = 2, kInject = 3 };
+enum { kBcDiffuse = 0, kBcSpecular = 1, kBcPeriodic = 2, kBcReservoir = 3 };
+enum { kModeUSP = 0, kModeSP = 1, kModeFixed = 2 };
+
+// counters (u64, device)
+enum { kCntChol = 0, kCntClamp = 1, kCntRemoved = 2, kCntInjected = 3, kCntRelaxed = 4, kCntOverflow = 5 };
+
+struct FaceDev {
+    int kind;
+    double T, theta, sqrt_theta;   // wall temperature and R T
+    double u[3];
+};
+
+struct SegDev {
+    double pos, lo, hi;
+    int kind;
+    double theta, sqrt_theta;
+    double u[3];
+};
+
+// Mutable per-simulation state, kept on the device so that captured graphs
+// stay valid from step to step.
+struct SimDyn {
+    uint32_t step;      // index n of the step being taken (Philox counter word 1)
+    uint32_t n;         // live particles in buffer `cur`
+    uint32_t next_pid;  // first id of the next injected particle
+    uint32_t nsamples;  // samples folded into the Eq. 34 average
+    int cur;            // buffer holding the current state
+    int pad;
+    unsigned long long counters[8];
+};
+
+// Everything a kernel needs to know about one simulation.  Lives in device
+// memory (one entry per simulation of a batch).
+struct SimDev {
+    int dim, nx, ny, K;
+    double lo[2], hi[2], dx, dy;
+    FaceDev face[4];
+    int nseg;
+    SegDev seg[kMaxSeg];
+    int periodic_x, periodic_y;
+    int has_reservoir, reservoir_cols;
+    double R, mass, mu_ref, T_ref, omega, Pr, dt, w;   // w: number density carried by one particle
+    double avg_keep, avg_new;                          // (n_a - 1)/n_a, 1/n_a
+    int mode;
+    double fixed_pne;
+    double body[3];
+    uint32_t key0, key1;
+    int64_t cap;
+    // storage: [buffer][plane]; 1-D uses plane 1 of pos only
+    void* pos[2][2];
+    void* vel[2][3];
+    uint32_t* pid[2];
+    uint32_t* cell;       // per-slot cell id (plain pipeline)
+    uint32_t* count;      // K + 1 (sentinel K = removed)
+    uint32_t* start;      // K + 2
+    uint32_t* fill;       // K + 1
+    double* mom;          // kNMom x K
+    double* prm;          // kNPrm x K
+    double* inst;         // kNFields x K
+    double* avg;          // kNFields x K
+    double* ushift;       // 3 x K, previous mean velocity (shift of the sums)
+    uint32_t* inj_count;  // K (buffer cells only)
+    uint32_t* inj_pidoff; // K
+    uint32_t inj_total;
+    // fused pipeline scratch (per cell): conservation factors
+    double* cons;         // 7 x K: ubar_old[3], ubar_new[3], alpha (alpha < 0: leave unchanged)
+    float* fprm;          // per-cell parameters in FP32 for the fused kernels (kFPrm x K)
+    SimDyn* dyn;
+};
+
+// -------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds, each two
+// 32x32->64-bit products and a key bump by the Weyl constants.
+// -------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox(uint4 c, uint2 k) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint32_t hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
+        uint32_t hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += W0;
+        k.y += W1;
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint4 draw(const SimDev& s, uint32_t pid, uint32_t step, uint32_t purpose, uint32_t k) {
+    return philox(make_uint4(pid, step, purpose, k), make_uint2(s.key0, s.key1));
+}
+
+// Uniform variates on the open interval (0, 1).
+// FP64: (x + 1/2) 2^-32, exact.  FP32: (2 (x >> 9) + 1) 2^-24, exact in float.
+template <class T> __device__ __forceinline__ T u01(uint32_t x);
+template <> __device__ __forceinline__ double u01<double>(uint32_t x) {
+    return fma((double)x, 2.3283064365386963e-10, 1.1641532182693481e-10);
+}
+template <> __device__ __forceinline__ float u01<float>(uint32_t x) {
+    return (float)(((x >> 9) << 1) | 1u) * 5.9604644775390625e-08f;
+}
+
+// Box-Muller pair from two words.
+template <class T> __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, T& z0, T& z1);
+template <> __device__ __forceinline__ void box_muller<double>(uint32_t a, uint32_t b, double& z0, double& z1) {
+    double r = sqrt(-2.0 * log(u01<double>(a)));
+    double sn, cs;
+    sincospi(2.0 * u01<double>(b), &sn, &cs);
+    z0 = r * cs;
+    z1 = r * sn;
+}
+template <> __device__ __forceinline__ void box_muller<float>(uint32_t a, uint32_t b, float& z0, float& z1) {
+    // -2 ln u = -2 ln2 * log2(u); the angle is shifted by pi, which flips the
+    // sign of both normals and leaves their joint law unchanged.
+    float r = sqrtf(-1.3862943611198906f * __log2f(u01<float>(a)));
+    float sn, cs;
+    __sincosf(6.283185307179586f * u01<float>(b) - 3.14159265358979f, &sn, &cs);
+    z0 = r * cs;
+    z1 = r * sn;
+}
+
+template <class T> __device__ __forceinline__ T dev_sqrt(T x);
+template <> __device__ __forceinline__ double dev_sqrt<double>(double x) { return sqrt(x); }
+template <> __device__ __forceinline__ float dev_sqrt<float>(float x) { return sqrtf(x); }
+template <class T> __device__ __forceinline__ T dev_log(T x);
+template <> __device__ __forceinline__ double dev_log<double>(double x) { return log(x); }
+template <> __device__ __forceinline__ float dev_log<float>(float x) { return 0.6931471805599453f * __log2f(x); }
+template <class T> __device__ __forceinline__ T dev_floor(T x);
+template <> __device__ __forceinline__ double dev_floor<double>(double x) { return floor(x); }
+template <> __device__ __forceinline__ float dev_floor<float>(float x) { return floorf(x); }
+
+// -------------------------------------------------------------------------
+// launch helpers (defined in usp_kernels.cu)
+// -------------------------------------------------------------------------
+struct Launch {
+    const SimDev* sims;   // device array
+    const int2* ptiles;   // (sim, first particle slot) tiles
+    const int* nptiles;   // device scalar
+    const int2* ctiles;   // (sim, first cell) tiles
+    const int* nctiles;   // device scalar
+    int nsims;
+    int grid_p, grid_c;   // persistent grid sizes
+    cudaStream_t stream;
+};
+
+constexpr int kPTile = 2048;  // particles per tile
+constexpr int kCTile = 64;    // cells per tile
+
+void launch_stream(const Launch& L, bool fp64);
+void launch_scan(const Launch& L);
+void launch_scatter(const Launch& L, bool fp64);
+void launch_inject(const Launch& L, bool fp64);
+void launch_moments(const Launch& L, bool fp64);
+void launch_params(const Launch& L);
+void launch_relax(const Launch& L, bool fp64);
+void launch_finish(const Launch& L);
+void launch_init(const Launch& L, bool fp64, const double* reg_theta, const double* reg_u, const int* cell_reg);
+cudaError_t debug_philox(int64_t n, const uint32_t* d_ctr, uint32_t k0, uint32_t k1, uint32_t* d_out, cudaStream_t st);
+
+}  // namespace usp

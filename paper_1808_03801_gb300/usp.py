@@ -1,0 +1,349 @@
+"""Thin ctypes binding of the C ABI in include/usp.h (libusp.so).
+
+Argument marshalling only: every stage of the particle update runs in the
+CUDA kernels of libusp.so.  Loading fails loudly when the library is missing;
+there is no CPU fallback.  PyTorch, when present, supplies the CUDA stream
+and (optionally) the device allocator.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LIB_PATH = _build.LIB
+
+OK = 0
+ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "CAPACITY", -5: "TIMEOUT", -6: "STATE"}
+NFIELDS = 16
+NPRM = 16
+FIELD_NAMES = ["n", "u0", "u1", "u2", "T", "pxx", "pyy", "pzz", "pxy", "pxz", "pyz", "q0", "q1", "q2",
+               "Pne", "Nc"]
+BC = {"diffuse": 0, "specular": 1, "periodic": 2, "reservoir": 3}
+MODE = {"usp": 0, "sp": 1, "fixed": 2}
+PRECISION = {"fp64": 0, "fp32": 1}
+PIPELINE = {"plain": 0, "fused": 1}
+MAXSEG = 4
+
+c_double, c_int, c_int32, c_int64, c_uint32, c_uint64, c_size_t, c_void_p = (
+    ctypes.c_double, ctypes.c_int, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64,
+    ctypes.c_size_t, ctypes.c_void_p)
+
+
+class Gas(ctypes.Structure):
+    _fields_ = [("mass", c_double), ("T_ref", c_double), ("mu_ref", c_double), ("omega", c_double),
+                ("Pr", c_double)]
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("dim", c_int), ("nx", c_int), ("ny", c_int), ("lo", c_double * 2), ("hi", c_double * 2)]
+
+
+class Bc(ctypes.Structure):
+    _fields_ = [("kind", c_int), ("T", c_double), ("u", c_double * 3), ("n", c_double)]
+
+
+class WallSegment(ctypes.Structure):
+    _fields_ = [("pos", c_double), ("lo", c_double), ("hi", c_double), ("kind", c_int), ("T", c_double),
+                ("u", c_double * 3)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("Kn", c_double), ("L_ref", c_double), ("n_ref", c_double), ("dt", c_double),
+                ("dt_over_tauc", c_double), ("body_accel", c_double * 3), ("ppc_ref", c_int),
+                ("n_avg", c_int), ("mode", c_int), ("fixed_pne", c_double), ("reservoir_cols", c_int),
+                ("precision", c_int), ("pipeline", c_int), ("capacity_factor", c_double)]
+
+
+class Region(ctypes.Structure):
+    _fields_ = [("lo", c_double * 2), ("hi", c_double * 2), ("n", c_double), ("T", c_double),
+                ("u", c_double * 3)]
+
+
+class Allocator(ctypes.Structure):
+    _fields_ = [("alloc", ctypes.CFUNCTYPE(c_void_p, c_size_t, c_void_p)),
+                ("free", ctypes.CFUNCTYPE(None, c_void_p, c_void_p)), ("ctx", c_void_p)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n_particles", c_int64), ("capacity", c_int64), ("n_cells", c_int32), ("precision", c_int32),
+                ("pipeline", c_int32), ("step", c_uint32), ("dt", c_double), ("mu_ref", c_double),
+                ("counters", c_int64 * 8), ("device_bytes", c_size_t)]
+
+
+class UspError(RuntimeError):
+    def __init__(self, status, msg=""):
+        super().__init__(f"usp status {status} ({ERRORS.get(status, '?')}): {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib(build_if_missing: bool = True):
+    """Load libusp.so (building it with nvcc first when it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        if not build_if_missing:
+            raise RuntimeError(f"libusp.so not built ({LIB_PATH}); run paper_1808_03801_gb300.build.build()")
+        _build.build()
+    L = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER
+    sig = {
+        "usp_create": (c_int, [P(Gas), P(Grid), P(Bc), P(WallSegment), c_int, P(Params), P(Allocator), c_void_p,
+                               P(c_void_p)]),
+        "usp_init_particles": (c_int, [c_void_p, P(Region), c_int, c_uint64]),
+        "usp_set_particles": (c_int, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_uint32, c_uint64]),
+        "usp_step": (c_int, [c_void_p, c_int]),
+        "usp_sample_macro": (c_int, [c_void_p, c_int, c_void_p, c_size_t, c_int]),
+        "usp_get_particles": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int64, P(c_int64)]),
+        "usp_run_stage": (c_int, [c_void_p, c_int]),
+        "usp_get_params": (c_int, [c_void_p, c_void_p, c_size_t]),
+        "usp_debug_philox": (c_int, [c_int64, c_void_p, c_uint32, c_uint32, c_void_p]),
+        "usp_get_info": (c_int, [c_void_p, P(Info)]),
+        "usp_synchronize": (c_int, [c_void_p]),
+        "usp_destroy": (c_int, [c_void_p]),
+        "usp_last_error": (ctypes.c_char_p, [c_void_p]),
+        "usp_status_string": (ctypes.c_char_p, [c_int]),
+        "usp_batch_create": (c_int, [c_size_t, c_int, c_void_p, P(c_void_p)]),
+        "usp_batch_admit": (c_int, [c_void_p, c_void_p]),
+        "usp_batch_step": (c_int, [c_void_p, c_int]),
+        "usp_batch_retire": (c_int, [c_void_p, c_void_p]),
+        "usp_batch_info": (c_int, [c_void_p, P(c_int), P(c_size_t)]),
+        "usp_batch_destroy": (c_int, [c_void_p]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def exported_symbols():
+    return [n for n in dir(lib()) if n.startswith("usp_")]
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def _torch_allocator():
+    import torch
+    dev = torch.cuda.current_device()
+
+    @ctypes.CFUNCTYPE(c_void_p, c_size_t, c_void_p)
+    def _alloc(nbytes, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), dev)
+        except Exception:
+            return None
+
+    @ctypes.CFUNCTYPE(None, c_void_p, c_void_p)
+    def _free(ptr, ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    a = Allocator()
+    a.alloc = _alloc
+    a.free = _free
+    a.ctx = None
+    return a, (_alloc, _free)
+
+
+def make_structs(w: dict, pipeline: str | None = None):
+    g, gr, pr = w["gas"], w["grid"], w["params"]
+    gas = Gas(g["mass"], g["T_ref"], g["mu_ref"], g["omega"], g["Pr"])
+    grid = Grid(gr["dim"], gr["nx"], gr["ny"], (c_double * 2)(*gr["lo"]), (c_double * 2)(*gr["hi"]))
+    faces = (Bc * 4)()
+    for i, f in enumerate(w["faces"]):
+        faces[i] = Bc(BC[f["kind"]], f["T"], (c_double * 3)(*f["u"]), f.get("n", 0.0))
+    segs = (WallSegment * MAXSEG)()
+    for i, s in enumerate(w.get("segments", [])):
+        segs[i] = WallSegment(s["pos"], s["lo"], s["hi"], BC[s["kind"]], s["T"], (c_double * 3)(*s["u"]))
+    pipe = pipeline or pr.get("pipeline", "plain")
+    params = Params(pr["Kn"], pr["L_ref"], pr["n_ref"], pr["dt"], pr["dt_over_tauc"],
+                    (c_double * 3)(*pr["body_accel"]), pr["ppc_ref"], pr["n_avg"], MODE[pr["mode"]],
+                    pr["fixed_pne"], pr["reservoir_cols"], PRECISION[pr["precision"]], PIPELINE[pipe],
+                    float(pr.get("capacity_factor", 0.0)))
+    return gas, grid, faces, segs, len(w.get("segments", [])), params
+
+
+def _regions(regions):
+    arr = (Region * max(1, len(regions)))()
+    for i, r in enumerate(regions):
+        arr[i] = Region((c_double * 2)(*r["lo"]), (c_double * 2)(*r["hi"]), r["n"], r["T"], (c_double * 3)(*r["u"]))
+    return arr
+
+
+class Simulation:
+    """One USP-ESBGK simulation on the GPU (a usp_handle)."""
+
+    def __init__(self, w: dict, stream=None, allocator=None, pipeline=None):
+        self.w = w
+        self._keep = None
+        L = lib()
+        gas, grid, faces, segs, nseg, params = make_structs(w, pipeline)
+        alloc_p = None
+        if allocator == "torch":
+            a, self._keep = _torch_allocator()
+            self._alloc_struct = a
+            alloc_p = ctypes.byref(a)
+        h = c_void_p()
+        rc = L.usp_create(ctypes.byref(gas), ctypes.byref(grid), faces, segs, nseg, ctypes.byref(params), alloc_p,
+                          _stream_ptr(stream), ctypes.byref(h))
+        if rc != OK:
+            raise UspError(rc, "usp_create rejected the workload")
+        self._h = h
+        self.dim = w["grid"]["dim"]
+        self.K = (w["grid"]["nx"] if self.dim == 2 else 1) * w["grid"]["ny"]
+
+    def _check(self, rc, what):
+        if rc != OK:
+            msg = lib().usp_last_error(self._h)
+            raise UspError(rc, f"{what}: {msg.decode() if msg else ''}")
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().usp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_particles(self, regions=None, seed=None):
+        regions = self.w["regions"] if regions is None else regions
+        seed = self.w["seed"] if seed is None else seed
+        self._check(lib().usp_init_particles(self._h, _regions(regions), len(regions), int(seed)),
+                    "usp_init_particles")
+        return self
+
+    def set_particles(self, pos, vel, pid, next_pid=None, seed=None):
+        pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 2)
+        vel = np.ascontiguousarray(vel, dtype=np.float64).reshape(-1, 3)
+        pid = np.ascontiguousarray(pid, dtype=np.uint32)
+        n = len(pid)
+        nxt = (int(pid.max()) + 1 if n else 0) if next_pid is None else int(next_pid)
+        seed = self.w["seed"] if seed is None else seed
+        self._check(lib().usp_set_particles(self._h, n, pos.ctypes.data, vel.ctypes.data, pid.ctypes.data, nxt,
+                                            int(seed)), "usp_set_particles")
+        return self
+
+    def step(self, n=1):
+        self._check(lib().usp_step(self._h, int(n)), "usp_step")
+        return self
+
+    def run_stage(self, k):
+        self._check(lib().usp_run_stage(self._h, int(k)), "usp_run_stage")
+        return self
+
+    def synchronize(self):
+        self._check(lib().usp_synchronize(self._h), "usp_synchronize")
+
+    def info(self):
+        inf = Info()
+        self._check(lib().usp_get_info(self._h, ctypes.byref(inf)), "usp_get_info")
+        return {"n_particles": inf.n_particles, "capacity": inf.capacity, "n_cells": inf.n_cells,
+                "precision": inf.precision, "pipeline": inf.pipeline, "step": inf.step, "dt": inf.dt,
+                "mu_ref": inf.mu_ref, "counters": list(inf.counters), "device_bytes": inf.device_bytes}
+
+    def sample(self, averaged=False, out=None):
+        """Fields [16, K] as numpy (host) or into a device tensor `out`."""
+        which = 1 if averaged else 0
+        if out is not None:
+            self._check(lib().usp_sample_macro(self._h, which, c_void_p(out.data_ptr()), out.numel(), 1),
+                        "usp_sample_macro")
+            return out
+        a = np.zeros((NFIELDS, self.K))
+        self._check(lib().usp_sample_macro(self._h, which, a.ctypes.data, a.size, 0), "usp_sample_macro")
+        return a
+
+    def particles(self):
+        n = c_int64()
+        inf = self.info()
+        cap = inf["capacity"]
+        pos = np.zeros((cap, 2))
+        vel = np.zeros((cap, 3))
+        pid = np.zeros(cap, dtype=np.uint32)
+        cell = np.zeros(cap, dtype=np.int32)
+        rc = lib().usp_get_particles(self._h, pos.ctypes.data, vel.ctypes.data, pid.ctypes.data, cell.ctypes.data,
+                                     cap, ctypes.byref(n))
+        self._check(rc, "usp_get_particles")
+        m = n.value
+        return {"pos": pos[:m], "vel": vel[:m], "pid": pid[:m], "cell": cell[:m]}
+
+    def params(self):
+        out = np.zeros((self.K, NPRM))
+        self._check(lib().usp_get_params(self._h, out.ctypes.data, out.size), "usp_get_params")
+        return out
+
+
+def debug_philox(ctr, key):
+    ctr = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    out = np.zeros_like(ctr)
+    rc = lib().usp_debug_philox(len(ctr), ctr.ctypes.data, int(key[0]), int(key[1]), out.ctypes.data)
+    if rc != OK:
+        raise UspError(rc, "usp_debug_philox")
+    return out
+
+
+class Batch:
+    """Many simulations advanced together by the same graph-captured launches."""
+
+    def __init__(self, hbm_budget: int, max_sims: int = 1024, stream=None):
+        b = c_void_p()
+        rc = lib().usp_batch_create(int(hbm_budget), int(max_sims), _stream_ptr(stream), ctypes.byref(b))
+        if rc != OK:
+            raise UspError(rc, "usp_batch_create")
+        self._b = b
+
+    def admit(self, sim: Simulation) -> int:
+        """Returns 0 when admitted, a negative status otherwise (CAPACITY: no room yet)."""
+        return lib().usp_batch_admit(self._b, sim.handle)
+
+    def retire(self, sim: Simulation):
+        rc = lib().usp_batch_retire(self._b, sim.handle)
+        if rc != OK:
+            raise UspError(rc, "usp_batch_retire")
+
+    def step(self, n=1):
+        rc = lib().usp_batch_step(self._b, int(n))
+        if rc != OK:
+            raise UspError(rc, "usp_batch_step")
+
+    def info(self):
+        n, b = c_int(), c_size_t()
+        lib().usp_batch_info(self._b, ctypes.byref(n), ctypes.byref(b))
+        return n.value, b.value
+
+    def close(self):
+        if getattr(self, "_b", None):
+            lib().usp_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

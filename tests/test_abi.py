@@ -1,0 +1,56 @@
+"""The C-ABI library loads, exports every symbol include/usp.h declares, and
+rejects invalid arguments before touching a device (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1808_03801_gb300 import usp as U
+from paper_1808_03801_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "usp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(usp_[a-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = U.lib()
+    names = _declared()
+    assert "usp_create" in names and "usp_step" in names and "usp_sample_macro" in names
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_status_strings():
+    assert U.lib().usp_status_string(0) == b"ok"
+    assert U.lib().usp_status_string(-4) == b"capacity exceeded"
+
+
+def _create_rc(w, pipeline=None):
+    gas, grid, faces, segs, nseg, params = U.make_structs(w, pipeline)
+    h = ctypes.c_void_p()
+    rc = U.lib().usp_create(ctypes.byref(gas), ctypes.byref(grid), faces, segs, nseg, ctypes.byref(params), None,
+                            None, ctypes.byref(h))
+    assert not h.value or rc == 0
+    return rc
+
+
+@pytest.mark.parametrize("mutate", [
+    lambda w: w["params"].__setitem__("ppc_ref", 0),
+    lambda w: w["grid"].__setitem__("ny", 0),
+    lambda w: w["gas"].__setitem__("mass", -1.0),
+    lambda w: w["params"].__setitem__("body_accel", (0.0, 1.0, 0.0)),
+    lambda w: w["faces"].__setitem__(2, {"kind": "periodic", "T": 273.0, "u": (0, 0, 0), "n": 0.0}),
+    lambda w: w["params"].__setitem__("mode", "bogus") if False else w["params"].__setitem__("n_avg", 0),
+    lambda w: w["params"].__setitem__("precision", "fp64") or w["params"].__setitem__("pipeline", "fused"),
+    lambda w: w["params"].__setitem__("dt_over_tauc", 0.0),
+])
+def test_invalid_arguments_rejected_without_gpu(mutate):
+    w = W.couette(ny=10, ppc=10)
+    mutate(w)
+    assert _create_rc(w) == -1

@@ -1,0 +1,163 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle on
+the same seeded inputs.
+
+FP64 mode: integer work (particle sets, cell ids, counts) bit-exact, every
+particle's position and velocity within 1e-12 relative (scale sqrt(R T_ref)
+for velocities, the cell size for positions), fields within 1e-10.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1808_03801_gb300 import workloads as W
+from tests._util import KB_M_AR, assert_particles_close, by_pid
+
+pytestmark = pytest.mark.gpu
+
+VSCALE = math.sqrt(KB_M_AR * W.T0)
+
+
+@pytest.fixture(scope="module")
+def usp():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1808_03801_gb300 import usp as U
+    U.lib()
+    return U
+
+
+def _pair(w, usp, init=True):
+    g = usp.Simulation(w)
+    o = oracle.OracleSim(w)
+    if init:
+        g.init_particles()
+        o.init_particles()
+    return g, o
+
+
+def _cell_size(w):
+    gr = w["grid"]
+    return (gr["hi"][1] - gr["lo"][1]) / gr["ny"]
+
+
+def test_philox_bit_exact(usp):
+    rng = np.random.default_rng(1)
+    ctr = rng.integers(0, 2**32, size=(20000, 4), dtype=np.uint64).astype(np.uint32)
+    key = (0x1234ABCD, 0x0BADF00D)
+    got = usp.debug_philox(ctr, key)
+    want = np.array([oracle.philox(c, key) for c in ctr[:2000]])
+    assert np.array_equal(got[:2000], want)
+
+
+def test_init_matches_oracle(usp):
+    w = W.cavity(n=12, ppc=40, Kn=0.05, precision="fp64", steps=1)
+    w["regions"].append({"lo": (0.0, 0.0), "hi": (0.5e-4, 0.5e-4), "n": W.N0 * 0.5, "T": 350.0,
+                         "u": (20.0, 0.0, -5.0)})
+    g, o = _pair(w, usp)
+    assert_particles_close(g.particles(), o.particles(), VSCALE, 1e-4 / 12, rtol=1e-14)
+
+
+def test_dt_and_viscosity_derivation(usp):
+    w = W.couette(ny=10, ppc=10)
+    g, o = _pair(w, usp, init=False)
+    inf = g.info()
+    assert math.isclose(inf["dt"], o.dt, rel_tol=1e-14)
+    assert math.isclose(inf["mu_ref"], o.mu_ref, rel_tol=1e-14)
+
+
+@pytest.mark.parametrize("name,steps", [("couette", 20), ("cavity", 12), ("sod", 15), ("slit", 10),
+                                        ("poiseuille", 15)])
+def test_fp64_step_parity(usp, name, steps):
+    if name == "couette":
+        w = W.couette(ny=100, ppc=100, precision="fp64")
+    elif name == "cavity":
+        w = W.cavity(n=24, ppc=30, Kn=0.01, precision="fp64")
+    elif name == "sod":
+        w = W.sod(ny=200, ppc_left=80, precision="fp64")
+    elif name == "slit":
+        w = W.slit(nx=40, ny=20, ppc=30, precision="fp64")
+    else:
+        w = W.poiseuille(ny=50, ppc=60, precision="fp64")
+    g, o = _pair(w, usp)
+    g.step(steps)
+    o.step(steps)
+    assert_particles_close(g.particles(), o.particles(), VSCALE, _cell_size(w))
+    fg, fo = g.sample(), o.fields()
+    assert np.array_equal(fg[15], fo[15])        # particles per cell
+    scale = np.maximum(np.abs(fo), np.abs(fo).max(axis=1, keepdims=True) * 1e-3)
+    assert np.all(np.abs(fg - fo) <= 1e-10 * scale + 1e-300)
+    fa, oa = g.sample(averaged=True), o.fields(averaged=True)
+    assert np.all(np.abs(fa - oa) <= 1e-10 * np.maximum(np.abs(oa), np.abs(oa).max(1, keepdims=True) * 1e-3))
+    pg, po = g.params(), o.params()
+    assert np.array_equal(pg[:, 14], po[:, 14])   # valid cells
+    assert np.array_equal(pg[:, 15], po[:, 15])   # relaxed counts (integer decisions)
+    sel = po[:, 14] > 0
+    assert np.allclose(pg[sel, 4:14], po[sel, 4:14], rtol=1e-10, atol=1e-12 * VSCALE)
+    if name == "slit":
+        ig = g.info()
+        assert ig["n_particles"] == o.n
+        assert ig["counters"][2] == o.counters()[2] and ig["counters"][3] == o.counters()[3]
+
+
+def test_stagewise_sort_parity(usp):
+    """After advection and the counting sort, cell ids and counts are bit-exact
+    and the storage is grouped by cell."""
+    w = W.cavity(n=16, ppc=25, Kn=0.02, precision="fp64")
+    g, o = _pair(w, usp)
+    g.step(3)
+    o.step(3)
+    for k in (0, 1, 2):
+        g.run_stage(k)
+    for ph in (oracle.PH_STREAM, oracle.PH_RESERVOIR, oracle.PH_SORT):
+        o.phase(ph)
+    P = g.particles()
+    assert np.all(np.diff(P["cell"]) >= 0)
+    assert np.array_equal(np.bincount(P["cell"], minlength=256), o.counts())
+    assert_particles_close(P, o.particles(), VSCALE, 1e-4 / 16)
+    for k in (3, 4, 5, 6):
+        g.run_stage(k)
+    for ph in (oracle.PH_MOMENTS, oracle.PH_PARAMS, oracle.PH_RELAX, oracle.PH_SAMPLE):
+        o.phase(ph)
+    assert_particles_close(g.particles(), o.particles(), VSCALE, 1e-4 / 16)
+
+
+@pytest.mark.parametrize("mode", ["usp", "sp", "fixed"])
+def test_homogeneous_modes(usp, mode):
+    n = 20000
+    w = W.homogeneous_box(ppc=n, dt_over_tauc=3.0, mode=mode, fixed_pne=0.4)
+    pos, vel, pid = W.bimaxwellian(n, seed=3, heat_skew=0.5)
+    g = usp.Simulation(w).set_particles(pos, vel, pid)
+    o = oracle.OracleSim(w).set_particles(pos, vel, pid)
+    g.step(4)
+    o.step(4)
+    assert_particles_close(g.particles(), o.particles(), VSCALE, 1e-6)
+
+
+def test_edge_cases_empty_and_sparse_cells(usp):
+    """Empty cells, cells with a single particle and an empty domain."""
+    w = W.cavity(n=10, ppc=3, Kn=0.05, precision="fp64")
+    w["regions"] = [{"lo": (0.0, 0.0), "hi": (0.5e-4, 1e-4), "n": W.N0, "T": W.T0, "u": (0, 0, 0)}]
+    g, o = _pair(w, usp)
+    g.step(6)
+    o.step(6)
+    assert_particles_close(g.particles(), o.particles(), VSCALE, 1e-5)
+    assert np.array_equal(g.sample()[15], o.fields()[15])
+    w2 = W.couette(ny=8, ppc=10)
+    w2["regions"] = []
+    g2 = usp.Simulation(w2).init_particles()
+    g2.step(3)
+    assert g2.info()["n_particles"] == 0
+
+
+def test_capacity_and_argument_errors(usp):
+    w = W.couette(ny=10, ppc=10)
+    bad = dict(w, params=dict(w["params"], ppc_ref=0))
+    with pytest.raises(usp.UspError) as e:
+        usp.Simulation(bad)
+    assert e.value.status == -1
+    g = usp.Simulation(w)
+    with pytest.raises(usp.UspError) as e:
+        g.step(1)
+    assert e.value.status == -6   # not initialised
