@@ -242,6 +242,9 @@ int usp_batch_admit(usp_batch* b, usp_handle* h);
 int usp_batch_step(usp_batch* b, int nsteps);
 int usp_batch_retire(usp_batch* b, usp_handle* h);
 int usp_batch_info(usp_batch* b, int* n_sims, size_t* bytes_in_use);
+/* Debug / profiling: run one stage (as usp_run_stage) over every admitted
+ * simulation; a full step is the stages in order. */
+int usp_batch_run_stage(usp_batch* b, int stage);
 int usp_batch_destroy(usp_batch* b);
 
 #ifdef __cplusplus

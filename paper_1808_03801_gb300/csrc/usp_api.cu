@@ -977,3 +977,32 @@ extern "C" int usp_batch_destroy(usp_batch* b) {
     delete b;
     return USP_OK;
 }
+
+// Debug / profiling: run one stage of the plain pipeline over every admitted
+// simulation (same stage numbers as usp_run_stage).
+extern "C" int usp_batch_run_stage(usp_batch* b, int stage) {
+    if (!b) return USP_ERR_INVALID_ARG;
+    if (b->members.empty()) return USP_OK;
+    int rc;
+    if (b->dirty && (rc = batch_rebuild(b)) != 0) return rc;
+    Launch L = batch_launch(b);
+    const bool fp64 = b->precision == USP_FP64;
+    bool res = false;
+    for (auto* h : b->members) res |= h->host.has_reservoir != 0;
+    switch (stage) {
+    case 0: launch_stream(L, fp64); break;
+    case 1: break;
+    case 2:
+        launch_scan(L);
+        launch_scatter(L, fp64);
+        if (res) launch_inject(L, fp64);
+        break;
+    case 3: launch_moments(L, fp64); break;
+    case 4: launch_params(L); break;
+    case 5: launch_relax(L, fp64); break;
+    case 6: launch_finish(L); break;
+    default: return bfail(b, USP_ERR_INVALID_ARG, "stage must be 0..6");
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? USP_OK : bfail(b, USP_ERR_CUDA, cudaGetErrorString(e));
+}

@@ -116,6 +116,7 @@ def lib(build_if_missing: bool = True):
         "usp_batch_retire": (c_int, [c_void_p, c_void_p]),
         "usp_batch_info": (c_int, [c_void_p, P(c_int), P(c_size_t)]),
         "usp_batch_destroy": (c_int, [c_void_p]),
+        "usp_batch_run_stage": (c_int, [c_void_p, c_int]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -125,22 +126,49 @@ def lib(build_if_missing: bool = True):
     return L
 
 
+_STAGES = {
+    "plain": [(0, "k_stream"), (2, "k_scan+k_scatter"), (3, "k_moments"), (4, "k_params"), (5, "k_relax"),
+              (6, "k_finish")],
+}
+_LAUNCHES = {"plain": 7}
+
+
+def fused_available() -> bool:
+    return hasattr(lib(), "usp_fused_supported") and bool(lib().usp_fused_supported())
+
+
+def stage_list(pipeline: str):
+    """(stage id, kernel names) of one step, for per-kernel timing."""
+    return list(_STAGES[pipeline])
+
+
+def launches_per_step(pipeline: str, reservoir: bool = False) -> int:
+    return _LAUNCHES[pipeline] + (1 if reservoir else 0)
+
+
 def exported_symbols():
     return [n for n in dir(lib()) if n.startswith("usp_")]
 
 
-def _stream_ptr(stream):
-    if stream is None:
-        try:
-            import torch
-            if torch.cuda.is_available():
-                return torch.cuda.current_stream().cuda_stream
-        except Exception:
-            pass
-        return None
+def _resolve_stream(stream):
+    """(torch stream object or None, raw cudaStream_t).  The legacy default
+    stream cannot be captured into a CUDA graph, so when the caller gives no
+    stream and torch's current stream is the default one, a new torch stream
+    is created for the handle."""
     if isinstance(stream, int):
-        return stream
-    return int(stream.cuda_stream)
+        return None, stream
+    if stream is not None:
+        return stream, int(stream.cuda_stream)
+    try:
+        import torch
+        if torch.cuda.is_available():
+            cur = torch.cuda.current_stream()
+            if cur.cuda_stream == 0:
+                cur = torch.cuda.Stream()
+            return cur, int(cur.cuda_stream)
+    except Exception:
+        pass
+    return None, None
 
 
 def _torch_allocator():
@@ -204,8 +232,9 @@ class Simulation:
             self._alloc_struct = a
             alloc_p = ctypes.byref(a)
         h = c_void_p()
+        self.stream, ptr = _resolve_stream(stream)
         rc = L.usp_create(ctypes.byref(gas), ctypes.byref(grid), faces, segs, nseg, ctypes.byref(params), alloc_p,
-                          _stream_ptr(stream), ctypes.byref(h))
+                          ptr, ctypes.byref(h))
         if rc != OK:
             raise UspError(rc, "usp_create rejected the workload")
         self._h = h
@@ -313,7 +342,8 @@ class Batch:
 
     def __init__(self, hbm_budget: int, max_sims: int = 1024, stream=None):
         b = c_void_p()
-        rc = lib().usp_batch_create(int(hbm_budget), int(max_sims), _stream_ptr(stream), ctypes.byref(b))
+        self.stream, ptr = _resolve_stream(stream)
+        rc = lib().usp_batch_create(int(hbm_budget), int(max_sims), ptr, ctypes.byref(b))
         if rc != OK:
             raise UspError(rc, "usp_batch_create")
         self._b = b
@@ -331,6 +361,11 @@ class Batch:
         rc = lib().usp_batch_step(self._b, int(n))
         if rc != OK:
             raise UspError(rc, "usp_batch_step")
+
+    def run_stage(self, k):
+        rc = lib().usp_batch_run_stage(self._b, int(k))
+        if rc != OK:
+            raise UspError(rc, "usp_batch_run_stage")
 
     def info(self):
         n, b = c_int(), c_size_t()

@@ -21,8 +21,9 @@ def assert_particles_close(gpu, orc, vel_scale, pos_scale, rtol=1e-12, check_cel
     bad = dv > tv
     if bad.any():
         i = np.argwhere(bad)[0][0]
-        raise AssertionError(f"velocity mismatch at pid {o['pid'][i]}: gpu {g['vel'][i]} oracle {o['vel'][i]}; "
-                             f"{bad.any(1).sum()} particles differ")
+        rel = (dv / np.maximum(np.abs(o["vel"]), vel_scale)).max()
+        raise AssertionError(f"velocity mismatch at pid {o['pid'][i]}: gpu {g['vel'][i]!r} oracle {o['vel'][i]!r}; "
+                             f"{bad.any(1).sum()} particles differ, max relative difference {rel:.3e}")
     dp = np.abs(g["pos"] - o["pos"])
     tp = rtol * np.maximum(np.abs(o["pos"]), pos_scale)
     bad = dp > tp

@@ -136,13 +136,21 @@ def test_homogeneous_modes(usp, mode):
 
 
 def test_edge_cases_empty_and_sparse_cells(usp):
-    """Empty cells, cells with a single particle and an empty domain."""
+    """Empty cells, cells with one to a few particles and an empty domain.
+
+    With two or three particles in a cell the sample stress can put almost all
+    thermal energy on one axis, which makes RT I + (1 - 1/Pr) sigma*/rho nearly
+    singular; its Cholesky factor then amplifies rounding-order differences
+    (one-pass shifted sums on the GPU, two-pass sums in the oracle) by the
+    condition number, so this sparse case is held to 1e-9 instead of 1e-12.
+    Integer work stays bit-exact."""
     w = W.cavity(n=10, ppc=3, Kn=0.05, precision="fp64")
     w["regions"] = [{"lo": (0.0, 0.0), "hi": (0.5e-4, 1e-4), "n": W.N0, "T": W.T0, "u": (0, 0, 0)}]
     g, o = _pair(w, usp)
     g.step(6)
     o.step(6)
-    assert_particles_close(g.particles(), o.particles(), VSCALE, 1e-5)
+    assert_particles_close(g.particles(), o.particles(), VSCALE, 1e-5, rtol=1e-9)
+    assert np.array_equal(g.params()[:, 15], o.params()[:, 15])
     assert np.array_equal(g.sample()[15], o.fields()[15])
     w2 = W.couette(ny=8, ppc=10)
     w2["regions"] = []
