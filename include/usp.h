@@ -170,8 +170,9 @@ typedef struct {
 } usp_info;
 
 /* Create a simulation.  faces[4] in order x-lo, x-hi, y-lo, y-hi; segs may be
- * NULL when nseg == 0; stream is a cudaStream_t (NULL: legacy default
- * stream).  Derives mu_ref (Eq. 36) and dt (Eq. 37), allocates per-cell
+ * NULL when nseg == 0; stream is a cudaStream_t (NULL: the handle creates
+ * and owns a non-blocking stream, since steps are captured into CUDA graphs
+ * and the legacy default stream cannot be captured).  Derives mu_ref (Eq. 36) and dt (Eq. 37), allocates per-cell
  * arrays; particle storage is allocated by usp_init_particles /
  * usp_set_particles.  Errors: INVALID_ARG for inconsistent input (periodic
  * on one face of an axis, resolved-axis body force, non-positive sizes),
@@ -245,6 +246,12 @@ int usp_batch_info(usp_batch* b, int* n_sims, size_t* bytes_in_use);
 /* Debug / profiling: run one stage (as usp_run_stage) over every admitted
  * simulation; a full step is the stages in order. */
 int usp_batch_run_stage(usp_batch* b, int stage);
+
+/* 1 when the library carries the fused FP32 pipeline (USP_PIPE_FUSED).  Its
+ * stages for usp_run_stage / usp_batch_run_stage are 10 relaxation of the
+ * previous step + advection + bucket scatter, 11 reservoir refill, 12
+ * moments, 13 parameters and fields, 14 bucket layout, 15 end of step. */
+int usp_fused_supported(void);
 int usp_batch_destroy(usp_batch* b);
 
 #ifdef __cplusplus

@@ -63,6 +63,7 @@ struct usp_handle {
     std::string err;
     std::vector<uint32_t> inj_count_host;
     int batch_refs = 0;
+    int fused_R = 8;                  // particles per lane held in registers by the fused kernels
 };
 
 struct usp_batch {
@@ -145,6 +146,7 @@ static Launch make_launch(usp_handle* h) {
     L.ctiles = h->d_ctiles;
     L.nctiles = h->d_ntiles + 1;
     L.nsims = 1;
+    L.dims = h->host.dim == 1 ? 1 : 2;
     L.grid_p = persistent_grid(h->nptiles, 8);
     L.grid_c = persistent_grid(h->nctiles, 8);
     L.stream = h->stream;
@@ -161,6 +163,27 @@ static void enqueue_step(const Launch& L, bool fp64, bool reservoir) {
     launch_params(L);
     launch_relax(L, fp64);
     launch_finish(L);
+}
+
+// one full step of the fused FP32 pipeline
+static void enqueue_fused_step(const Launch& L, int R, bool reservoir) {
+    launch_fused_relax_stream(L, R, false);
+    if (reservoir) launch_fused_inject(L);
+    launch_fused_moments(L, R);
+    launch_fused_params(L);
+    launch_fused_layout(L);
+    launch_fused_finish(L);
+}
+
+static void enqueue_any(usp_handle* h, const Launch& L) {
+    if (h->pipeline == USP_PIPE_FUSED) enqueue_fused_step(L, h->fused_R, h->host.has_reservoir != 0);
+    else enqueue_step(L, h->precision == USP_FP64, h->host.has_reservoir != 0);
+}
+
+static int choose_R(uint32_t max_count) {
+    if (max_count <= 128) return 4;
+    if (max_count <= 256) return 8;
+    return 12;
 }
 
 static int count_for_density(const SimDev& s, double n, double n_ref, int ppc_ref) {
@@ -318,8 +341,18 @@ extern "C" int usp_create(const usp_gas* gas, const usp_grid* grid, const usp_bc
     CALLOC(ushift, double, 3 * (size_t)K);
     CALLOC(inj_count, uint32_t, K);
     CALLOC(inj_pidoff, uint32_t, K);
-    CALLOC(cons, double, 7 * (size_t)K);
-    CALLOC(fprm, float, 16 * (size_t)K);
+    CALLOC(fprm, float, (size_t)kNFPrm * K);
+    if (prm->pipeline == USP_PIPE_FUSED) {
+        for (int b = 0; b < 2; ++b) {
+            CALLOC(lay[b], uint32_t, K + 1);
+            CALLOC(cnt[b], uint32_t, K);
+            CALLOC(sp_pos[b][0], float, kSpillCap);
+            CALLOC(sp_pos[b][1], float, kSpillCap);
+            for (int d = 0; d < 3; ++d) { CALLOC(sp_vel[b][d], float, kSpillCap); }
+            CALLOC(sp_pid[b], uint32_t, kSpillCap);
+            CALLOC(sp_cell[b], uint32_t, kSpillCap);
+        }
+    }
 #undef CALLOC
     if ((rc = cell_alloc(h, sizeof(SimDev), &p)) != 0) { usp_destroy(h); return rc; }
     h->d_sim = (SimDev*)p;
@@ -382,6 +415,11 @@ static int alloc_particles(usp_handle* h, int64_t n) {
     SimDev& s = h->host;
     double f = h->capacity_factor > 0 ? h->capacity_factor : (s.has_reservoir ? 2.0 : 1.25);
     int64_t cap = (int64_t)std::ceil(n * f) + 2 * (int64_t)s.inj_total + 1024;
+    if (h->pipeline == USP_PIPE_FUSED) {
+        // slack buckets: about 1.25 x the largest neighbouring count + 16 per cell
+        const double ff = h->capacity_factor > 0 ? std::max(h->capacity_factor, 1.6) : (s.has_reservoir ? 2.5 : 1.6);
+        cap = (int64_t)std::ceil(n * ff) + 24 * (int64_t)s.K + 4 * (int64_t)s.inj_total + 4096;
+    }
     if (cap > (int64_t)0x7FFFFFFFll) return fail(h, USP_ERR_CAPACITY, "particle capacity exceeds 2^31 - 1");
     free_particles(h);
     destroy_graphs(h->graphs);
@@ -513,9 +551,43 @@ extern "C" int usp_init_particles(usp_handle* h, const usp_region* regions, int 
     dfree(h, d_th); dfree(h, d_u); dfree(h, d_reg);
     if (rc) return rc;
     if (e != cudaSuccess) return fail(h, USP_ERR_CUDA, std::string("init: ") + cudaGetErrorString(e));
+    if (h->pipeline == USP_PIPE_FUSED) {
+        uint32_t mx = 0;
+        for (int c = 0; c < K; ++c) mx = std::max(mx, start[c + 1] - start[c]);
+        h->fused_R = choose_R(mx + mx / 4);
+        Launch L = make_launch(h);
+        launch_fused_setup(L);
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(h->stream));
+    }
     h->initialised = true;
     h->mid_step = false;
     h->sorted = true;
+    return USP_OK;
+}
+
+// order a freshly loaded state by cell (assign + scan + scatter into buffer 1)
+// and build the bucket layout of the fused pipeline
+static int fused_from_unsorted(usp_handle* h) {
+    SimDev& s = h->host;
+    const int K = s.K;
+    Launch L = make_launch(h);
+    launch_assign(L, false);
+    launch_scan(L);
+    launch_scatter(L, false);
+    CK(cudaGetLastError());
+    CK(cudaMemsetAsync(s.fill, 0, sizeof(uint32_t) * (K + 1), h->stream));
+    int one = 1;
+    CK(cudaMemcpyAsync(&h->d_dyn->cur, &one, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    std::vector<uint32_t> start(K + 2);
+    CK(cudaMemcpyAsync(start.data(), s.start, sizeof(uint32_t) * (K + 2), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    uint32_t mx = 0;
+    for (int c = 0; c < K; ++c) mx = std::max(mx, start[c + 1] - start[c]);
+    h->fused_R = choose_R(mx + mx / 4);
+    launch_fused_setup(L);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(h->stream));
     return USP_OK;
 }
 
@@ -554,9 +626,10 @@ extern "C" int usp_set_particles(usp_handle* h, int64_t n, const double* pos, co
     if (e != cudaSuccess) return fail(h, USP_ERR_CUDA, cudaGetErrorString(e));
     if ((rc = reset_dynamic(h, (uint32_t)n, next_pid)) != 0) return rc;
     CK(cudaStreamSynchronize(h->stream));
+    if (h->pipeline == USP_PIPE_FUSED && (rc = fused_from_unsorted(h)) != 0) return rc;
     h->initialised = true;
     h->mid_step = false;
-    h->sorted = false;
+    h->sorted = h->pipeline == USP_PIPE_FUSED;
     return USP_OK;
 }
 
@@ -565,10 +638,9 @@ extern "C" int usp_set_particles(usp_handle* h, int64_t n, const double* pos, co
 // ---------------------------------------------------------------------------
 static int capture(usp_handle* h, int nsteps, cudaGraphExec_t* exec) {
     Launch L = make_launch(h);
-    const bool fp64 = h->precision == USP_FP64;
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-    for (int i = 0; i < nsteps; ++i) enqueue_step(L, fp64, h->host.has_reservoir);
+    for (int i = 0; i < nsteps; ++i) enqueue_any(h, L);
     cudaError_t e = cudaStreamEndCapture(h->stream, &g);
     if (e != cudaSuccess) return fail(h, USP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
     e = cudaGraphInstantiate(exec, g, 0);
@@ -597,27 +669,48 @@ extern "C" int usp_step(usp_handle* h, int nsteps) {
     return USP_OK;
 }
 
+// one stage of a step: plain pipeline 0..6, fused pipeline 10..15
+static int stage_launch(const Launch& L, int pipeline, bool fp64, int R, bool reservoir, int stage) {
+    if (pipeline == USP_PIPE_FUSED) {
+        switch (stage) {
+        case 10: launch_fused_relax_stream(L, R, false); return 0;
+        case 11: if (reservoir) launch_fused_inject(L); return 0;
+        case 12: launch_fused_moments(L, R); return 0;
+        case 13: launch_fused_params(L); return 0;
+        case 14: launch_fused_layout(L); return 0;
+        case 15: launch_fused_finish(L); return 0;
+        default: return -1;
+        }
+    }
+    switch (stage) {
+    case 0: launch_stream(L, fp64); return 0;
+    case 1: return 0;   // reservoir removal happens in stage 0, refill in stage 2
+    case 2:
+        launch_scan(L);
+        launch_scatter(L, fp64);
+        if (reservoir) launch_inject(L, fp64);
+        return 0;
+    case 3: launch_moments(L, fp64); return 0;
+    case 4: launch_params(L); return 0;
+    case 5: launch_relax(L, fp64); return 0;
+    case 6: launch_finish(L); return 0;
+    default: return -1;
+    }
+}
+
 extern "C" int usp_run_stage(usp_handle* h, int stage) {
     if (!h) return USP_ERR_INVALID_ARG;
     if (!h->initialised) return fail(h, USP_ERR_STATE, "particles not initialised");
     if (h->batch_refs) return fail(h, USP_ERR_STATE, "handle is admitted to a batch");
     Launch L = make_launch(h);
-    const bool fp64 = h->precision == USP_FP64;
-    switch (stage) {
-    case 0: launch_stream(L, fp64); h->sorted = false; break;
-    case 1: break;   // reservoir removal happens in stage 0, refill in stage 2
-    case 2:
-        launch_scan(L);
-        launch_scatter(L, fp64);
-        if (h->host.has_reservoir) launch_inject(L, fp64);
-        h->mid_step = true;
-        h->sorted = true;
-        break;
-    case 3: launch_moments(L, fp64); break;
-    case 4: launch_params(L); break;
-    case 5: launch_relax(L, fp64); break;
-    case 6: launch_finish(L); h->mid_step = false; break;
-    default: return fail(h, USP_ERR_INVALID_ARG, "stage must be 0..6");
+    if (stage_launch(L, h->pipeline, h->precision == USP_FP64, h->fused_R, h->host.has_reservoir != 0, stage))
+        return fail(h, USP_ERR_INVALID_ARG, "stage must be 0..6 (plain) or 10..15 (fused)");
+    if (h->pipeline == USP_PIPE_PLAIN) {
+        if (stage == 0) h->sorted = false;
+        if (stage == 2) h->mid_step = h->sorted = true;
+        if (stage == 6) h->mid_step = false;
+    } else {
+        h->mid_step = stage >= 10 && stage < 15;
     }
     CK(cudaGetLastError());
     return USP_OK;
@@ -650,9 +743,83 @@ extern "C" int usp_sample_macro(usp_handle* h, int which, double* out, size_t ou
     return USP_OK;
 }
 
+// fused pipeline: apply the pending relaxation, then gather the buckets and the
+// spill list of the current buffer in cell order
+static int get_particles_fused(usp_handle* h, double* pos, double* vel, uint32_t* pid, int32_t* cell, int64_t cap,
+                               int64_t* n_out) {
+    if (h->mid_step) return fail(h, USP_ERR_STATE, "a staged step is in progress");
+    SimDyn d;
+    int rc = read_dyn(h, &d);
+    if (rc && rc != USP_ERR_CAPACITY) return rc;
+    if (d.relax_pending) {
+        Launch L = make_launch(h);
+        launch_fused_relax_stream(L, h->fused_R, true);
+        CK(cudaGetLastError());
+        int rc2 = read_dyn(h, &d);
+        if (rc2 && rc2 != USP_ERR_CAPACITY) return rc2;
+    }
+    const SimDev& s = h->host;
+    const int K = s.K;
+    const int b = d.cur;
+    std::vector<uint32_t> lay(K + 1), cnt(K);
+    CK(cudaMemcpy(lay.data(), s.lay[b], sizeof(uint32_t) * (K + 1), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(cnt.data(), s.cnt[b], sizeof(uint32_t) * K, cudaMemcpyDeviceToHost));
+    const uint32_t nsp = std::min<uint32_t>(d.sp_n[b], (uint32_t)kSpillCap);
+    int64_t n = 0;
+    for (int c = 0; c < K; ++c) n += cnt[c];
+    if (n_out) *n_out = n;
+    if (n > cap) return fail(h, USP_ERR_CAPACITY, "output arrays too small");
+    const int64_t slots = lay[K];
+    std::vector<float> P[5];
+    const int planes[5][2] = {{0, 0}, {0, 1}, {1, 0}, {1, 1}, {1, 2}};
+    for (int k = 0; k < 5; ++k) {
+        if (k == 0 && s.dim == 1) continue;
+        P[k].resize(std::max<int64_t>(slots, 1));
+        const void* src = planes[k][0] == 0 ? s.pos[b][planes[k][1]] : s.vel[b][planes[k][1]];
+        CK(cudaMemcpy(P[k].data(), src, 4 * slots, cudaMemcpyDeviceToHost));
+    }
+    std::vector<uint32_t> ids(std::max<int64_t>(slots, 1));
+    CK(cudaMemcpy(ids.data(), s.pid[b], 4 * slots, cudaMemcpyDeviceToHost));
+    std::vector<float> SP[5];
+    std::vector<uint32_t> spid(nsp + 1), scell(nsp + 1);
+    for (int k = 0; k < 5; ++k) {
+        if (k == 0 && s.dim == 1) continue;
+        SP[k].resize(nsp + 1);
+        const float* src = planes[k][0] == 0 ? s.sp_pos[b][planes[k][1]] : s.sp_vel[b][planes[k][1]];
+        if (nsp) CK(cudaMemcpy(SP[k].data(), src, 4 * nsp, cudaMemcpyDeviceToHost));
+    }
+    if (nsp) {
+        CK(cudaMemcpy(spid.data(), s.sp_pid[b], 4 * nsp, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(scell.data(), s.sp_cell[b], 4 * nsp, cudaMemcpyDeviceToHost));
+    }
+    int64_t o = 0;
+    auto put = [&](const std::vector<float>* A, size_t i, uint32_t id, int c) {
+        if (pos) {
+            pos[2 * o] = s.dim == 2 ? A[0][i] : 0.0;
+            pos[2 * o + 1] = A[1][i];
+        }
+        if (vel)
+            for (int k = 0; k < 3; ++k) vel[3 * o + k] = A[2 + k][i];
+        if (pid) pid[o] = id;
+        if (cell) cell[o] = c;
+        ++o;
+    };
+    for (int c = 0; c < K; ++c) {
+        const uint32_t capc = lay[c + 1] - lay[c];
+        const uint32_t nb = std::min(cnt[c], capc);
+        for (uint32_t j = 0; j < nb; ++j) put(P, lay[c] + j, ids[lay[c] + j], c);
+        if (cnt[c] > nb)
+            for (uint32_t k = 0; k < nsp; ++k)
+                if ((int)scell[k] == c) put(SP, k, spid[k], c);
+    }
+    if (n_out) *n_out = o;
+    return rc;
+}
+
 extern "C" int usp_get_particles(usp_handle* h, double* pos, double* vel, uint32_t* pid, int32_t* cell, int64_t cap,
                                  int64_t* n_out) {
     if (!h) return USP_ERR_INVALID_ARG;
+    if (h->pipeline == USP_PIPE_FUSED && h->initialised) return get_particles_fused(h, pos, vel, pid, cell, cap, n_out);
     SimDyn d;
     int rc = read_dyn(h, &d);
     if (rc && rc != USP_ERR_CAPACITY) return rc;
@@ -918,6 +1085,8 @@ static Launch batch_launch(usp_batch* b) {
     L.ctiles = b->d_ctiles;
     L.nctiles = b->d_ntiles + 1;
     L.nsims = (int)b->members.size();
+    L.dims = 0;
+    for (auto* h : b->members) L.dims |= h->host.dim == 1 ? 1 : 2;
     // fixed persistent grids: the tile counts are read on the device, so the
     // captured graph stays valid while simulations come and go
     L.grid_p = persistent_grid(1 << 30, 8);
@@ -930,11 +1099,18 @@ static int batch_capture(usp_batch* b, int nsteps, cudaGraphExec_t* exec) {
     Launch L = batch_launch(b);
     const bool fp64 = b->precision == USP_FP64;
     bool res = false;
-    for (auto* h : b->members) res |= h->host.has_reservoir != 0;
+    int R = 4;
+    for (auto* h : b->members) {
+        res |= h->host.has_reservoir != 0;
+        R = std::max(R, h->fused_R);
+    }
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return bfail(b, USP_ERR_CUDA, cudaGetErrorString(e));
-    for (int i = 0; i < nsteps; ++i) enqueue_step(L, fp64, res);
+    for (int i = 0; i < nsteps; ++i) {
+        if (b->pipeline == USP_PIPE_FUSED) enqueue_fused_step(L, R, res);
+        else enqueue_step(L, fp64, res);
+    }
     e = cudaStreamEndCapture(b->stream, &g);
     if (e != cudaSuccess) return bfail(b, USP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
     e = cudaGraphInstantiate(exec, g, 0);
@@ -988,21 +1164,15 @@ extern "C" int usp_batch_run_stage(usp_batch* b, int stage) {
     Launch L = batch_launch(b);
     const bool fp64 = b->precision == USP_FP64;
     bool res = false;
-    for (auto* h : b->members) res |= h->host.has_reservoir != 0;
-    switch (stage) {
-    case 0: launch_stream(L, fp64); break;
-    case 1: break;
-    case 2:
-        launch_scan(L);
-        launch_scatter(L, fp64);
-        if (res) launch_inject(L, fp64);
-        break;
-    case 3: launch_moments(L, fp64); break;
-    case 4: launch_params(L); break;
-    case 5: launch_relax(L, fp64); break;
-    case 6: launch_finish(L); break;
-    default: return bfail(b, USP_ERR_INVALID_ARG, "stage must be 0..6");
+    int R = 4;
+    for (auto* h : b->members) {
+        res |= h->host.has_reservoir != 0;
+        R = std::max(R, h->fused_R);
     }
+    if (stage_launch(L, b->pipeline, fp64, R, res, stage))
+        return bfail(b, USP_ERR_INVALID_ARG, "stage must be 0..6 (plain) or 10..15 (fused)");
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? USP_OK : bfail(b, USP_ERR_CUDA, cudaGetErrorString(e));
 }
+
+extern "C" int usp_fused_supported(void) { return 1; }

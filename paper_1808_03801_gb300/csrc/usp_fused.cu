@@ -1,2 +1,842 @@
-// usp_fused.cu -- placeholder translation unit for the fused FP32 pipeline.
-#include "usp_internal.cuh"
+// usp_fused.cu -- the fused FP32 pipeline of the USP-ESBGK step (sm_103a).
+//
+// One step n reads buffer p = cur and writes buffer q = cur ^ 1:
+//   k_g2      per cell (one warp): the relaxation of step n-1 still pending
+//             on the cell's particles (Eqs. 8b, 9, 27, 29-32 with the per-cell
+//             momentum / energy conservation), then advection of step n with
+//             the boundaries, the new cell, and the write into that cell's
+//             bucket of buffer q (the scatter of the counting sort; the
+//             bucket sizes come from the previous histogram plus slack).
+//   k_inject  reservoir buffer cells refilled into buffer q.
+//   k_g1      per cell (one warp): two-pass moments of Eq. 1 from the
+//             particles held in registers (mean, then central sums).
+//   k_params  per cell: Kn_GLL and P_ne (Eqs. 16-18), sigma* and q* (Eq. 33),
+//             the Cholesky factor of the ES covariance (Eq. 6c) in FP64, the
+//             fields and the average of Eq. 34.
+//   k_layout  per simulation: histogram -> bucket sizes -> exclusive scan,
+//             the layout that the next step writes with.
+//   k_finish  swap buffers, advance the step.
+// Per particle all arithmetic is FP32; FP64 is used once per cell (sums
+// after the warp reduction, the stress tensor, the Cholesky factor, the
+// conservation factors), because FP64 issue rate is scarce on GB300.
+// Each particle is read once and written once by k_g2 and its velocity is
+// read once more by k_g1.
+#include "usp_device.cuh"
+
+namespace usp {
+
+namespace {
+
+constexpr uint32_t kNoCell = 0xFFFFFFFFu;
+
+struct FCell {
+    float u[3], th, L[6], pr, nu, nues, pne;
+    int valid;
+};
+
+__device__ __forceinline__ void load_fcell(const SimDev& s, int c, FCell& f) {
+    const float* P = s.fprm;
+    const int K = s.K;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) f.u[d] = P[(size_t)d * K + c];
+    f.th = P[(size_t)3 * K + c];
+#pragma unroll
+    for (int d = 0; d < 6; ++d) f.L[d] = P[(size_t)(4 + d) * K + c];
+    f.pr = P[(size_t)10 * K + c];
+    f.nu = P[(size_t)11 * K + c];
+    f.nues = P[(size_t)12 * K + c];
+    f.pne = P[(size_t)13 * K + c];
+    f.valid = P[(size_t)14 * K + c] != 0.0f;
+}
+
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// collect up to 32 spill-list indices of `cell` into spl (per warp); returns the count
+__device__ uint32_t collect_spill(const SimDev& s, int b, int cell, uint32_t* spl, int lane) {
+    const uint32_t n = min(s.dyn->sp_n[b], (uint32_t)kSpillCap);
+    uint32_t found = 0;
+    for (uint32_t base = 0; base < n && found < 32; base += 32) {
+        const uint32_t i = base + lane;
+        const bool hit = i < n && s.sp_cell[b][i] == (uint32_t)cell;
+        const unsigned m = __ballot_sync(0xffffffffu, hit);
+        const uint32_t pos = found + __popc(m & lanemask_lt());
+        if (hit && pos < 32) spl[pos] = i;
+        found += __popc(m);
+    }
+    __syncwarp();
+    if (found > 32) {
+        if (lane == 0) atomicAdd(&s.dyn->counters[kCntOverflow], (unsigned long long)(found - 32));
+        found = 32;
+    }
+    return found;
+}
+
+template <int DIM>
+__device__ __forceinline__ void load_particle(const SimDev& s, int b, uint32_t base, uint32_t nb, const uint32_t* spl,
+                                              uint32_t j, float& x, float& y, float& v0, float& v1, float& v2,
+                                              uint32_t& id) {
+    if (j < nb) {
+        const uint32_t i = base + j;
+        if (DIM == 2) x = ((const float*)s.pos[b][0])[i];
+        y = ((const float*)s.pos[b][1])[i];
+        v0 = ((const float*)s.vel[b][0])[i];
+        v1 = ((const float*)s.vel[b][1])[i];
+        v2 = ((const float*)s.vel[b][2])[i];
+        id = s.pid[b][i];
+    } else {
+        const uint32_t i = spl[j - nb];
+        if (DIM == 2) x = s.sp_pos[b][0][i];
+        y = s.sp_pos[b][1][i];
+        v0 = s.sp_vel[b][0][i];
+        v1 = s.sp_vel[b][1][i];
+        v2 = s.sp_vel[b][2][i];
+        id = s.sp_pid[b][i];
+    }
+}
+
+template <int DIM>
+__device__ __forceinline__ void store_velocity(const SimDev& s, int b, uint32_t base, uint32_t nb, const uint32_t* spl,
+                                               uint32_t j, float v0, float v1, float v2) {
+    if (j < nb) {
+        const uint32_t i = base + j;
+        ((float*)s.vel[b][0])[i] = v0;
+        ((float*)s.vel[b][1])[i] = v1;
+        ((float*)s.vel[b][2])[i] = v2;
+    } else {
+        const uint32_t i = spl[j - nb];
+        s.sp_vel[b][0][i] = v0;
+        s.sp_vel[b][1][i] = v1;
+        s.sp_vel[b][2][i] = v2;
+    }
+}
+
+// FP32 advection: straight flight when the path stays strictly inside the
+// domain and crosses no plate, otherwise the full time-of-flight treatment.
+template <int DIM>
+__device__ __forceinline__ bool advect_fast(const SimDev& s, uint32_t step, uint32_t pid, float& x, float& y,
+                                            float* c) {
+    const float tau = (float)s.dt;
+    const float yn = y + c[1] * tau;
+    bool inside = yn > (float)s.lo[1] && yn < (float)s.hi[1];
+    float xn = x;
+    if (DIM == 2) {
+        xn = x + c[0] * tau;
+        inside = inside && xn > (float)s.lo[0] && xn < (float)s.hi[0];
+        for (int g = 0; g < s.nseg; ++g) {
+            const float ps = (float)s.seg[g].pos;
+            if ((x - ps) * (xn - ps) <= 0.0f) inside = false;
+        }
+    }
+    if (inside) {
+        y = yn;
+        if (DIM == 2) x = xn;
+        c[0] += (float)s.body[0] * tau;
+        c[1] += (float)s.body[1] * tau;
+        c[2] += (float)s.body[2] * tau;
+        return true;
+    }
+    return advect<float>(s, step, pid, x, y, c);
+}
+
+// append one particle to the bucket of its cell in buffer b (all 32 lanes
+// call this together; key == kNoCell for lanes with nothing to write)
+template <int DIM>
+__device__ __forceinline__ void emit(const SimDev& s, int b, uint32_t key, float x, float y, float v0, float v1,
+                                     float v2, uint32_t id, int lane) {
+    const unsigned grp = __match_any_sync(0xffffffffu, key);
+    if (key == kNoCell) return;
+    const int leader = __ffs(grp) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(&s.cnt[b][key], (uint32_t)__popc(grp));
+    base = __shfl_sync(grp, base, leader);
+    const uint32_t rank = base + (uint32_t)__popc(grp & lanemask_lt());
+    const uint32_t lo = s.lay[b][key];
+    const uint32_t capd = s.lay[b][key + 1] - lo;
+    if (rank < capd) {
+        const uint32_t i = lo + rank;
+        if (DIM == 2) ((float*)s.pos[b][0])[i] = x;
+        ((float*)s.pos[b][1])[i] = y;
+        ((float*)s.vel[b][0])[i] = v0;
+        ((float*)s.vel[b][1])[i] = v1;
+        ((float*)s.vel[b][2])[i] = v2;
+        s.pid[b][i] = id;
+    } else {
+        const uint32_t k = atomicAdd(&s.dyn->sp_n[b], 1u);
+        if (k < (uint32_t)kSpillCap) {
+            if (DIM == 2) s.sp_pos[b][0][k] = x;
+            s.sp_pos[b][1][k] = y;
+            s.sp_vel[b][0][k] = v0;
+            s.sp_vel[b][1][k] = v1;
+            s.sp_vel[b][2][k] = v2;
+            s.sp_pid[b][k] = id;
+            s.sp_cell[b][k] = key;
+        } else {
+            atomicAdd(&s.dyn->counters[kCntOverflow], 1ull);
+        }
+    }
+}
+
+// per-cell constants of the time-instant draw (Eq. 30)
+struct TimeDraw {
+    float dt, a, em1, ema, inv_nues;
+};
+
+__device__ __forceinline__ void es_draw_f(const SimDev& s, const FCell& f, const TimeDraw& td, uint32_t pid,
+                                          uint32_t step, const uint4& w, float* C) {
+    const float U1 = u01<float>(w.y);
+    const float t = td.a < 1.0f ? log1pf(U1 * td.em1) * td.inv_nues
+                                : td.dt + __logf(U1 + (1.0f - U1) * td.ema) * td.inv_nues;
+    const float sf = f.pne + (1.0f - f.pne) * __expf(-f.nu * t);          // Eq. 32
+    const uint4 v = draw(s, pid, step, kRelax, 1);
+    float z0, z1, z2, z3, z4, z5;
+    box_muller<float>(w.z, w.w, z0, z1);
+    box_muller<float>(v.x, v.y, z2, z3);
+    box_muller<float>(v.z, v.w, z4, z5);
+    const float A = sqrtf(sf), B = sqrtf(fmaxf(1.0f - sf, 0.0f) * f.th);
+    C[0] = A * (f.L[0] * z0) + B * z3;
+    C[1] = A * (f.L[1] * z0 + f.L[2] * z1) + B * z4;
+    C[2] = A * (f.L[3] * z0 + f.L[4] * z1 + f.L[5] * z2) + B * z5;
+}
+
+// ---------------------------------------------------------------------------
+// k_g2: pending relaxation + advection + bucket scatter (FLUSH: relaxation only)
+// ---------------------------------------------------------------------------
+template <int R, int DIM, bool FLUSH>
+__device__ void g2_cell(const SimDev& s, int cell, int p, uint32_t step, bool pending, uint32_t* spl, int lane) {
+    const uint32_t base = s.lay[p][cell];
+    const uint32_t capc = s.lay[p][cell + 1] - base;
+    const uint32_t arrived = s.cnt[p][cell];
+    const uint32_t nb = min(arrived, capc);
+    uint32_t nsp = 0;
+    if (arrived > nb) nsp = collect_spill(s, p, cell, spl, lane);
+    const uint32_t n = nb + nsp;
+    if (n == 0) return;
+    FCell f;
+    load_fcell(s, cell, f);
+    const bool relax = pending && f.valid;
+    if (FLUSH && !relax) return;
+    TimeDraw td;
+    td.dt = (float)s.dt;
+    td.a = f.nues * td.dt;
+    td.em1 = expm1f(td.a);
+    td.ema = __expf(-td.a);
+    td.inv_nues = 1.0f / f.nues;
+    const int q = p ^ 1;
+    const uint32_t CH = 32u * R;
+    const uint32_t nch = (n + CH - 1) / CH;
+
+    // a relaxed particle's new peculiar velocity replaces its old velocity in
+    // v0..v2 once the old one has entered the conservation sums (bit r of sel)
+    float x[R], y[R], v0[R], v1[R], v2[R];
+    uint32_t id[R];
+    unsigned sel = 0;
+    // relaxed-subset sums relative to the cell mean: so, eo (old), sn, en (new)
+    float a0 = 0, a1 = 0, a2 = 0, ae = 0, b0 = 0, b1 = 0, b2 = 0, be = 0, nr = 0;
+    for (uint32_t ch = 0; ch < nch; ++ch) {
+        sel = 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const uint32_t j = ch * CH + r * 32 + lane;
+            x[r] = 0.0f;
+            if (j < n) load_particle<DIM>(s, p, base, nb, spl, j, x[r], y[r], v0[r], v1[r], v2[r], id[r]);
+            if (relax && j < n) {
+                const uint4 w = draw(s, id[r], step, kRelax, 0);
+                if (u01<float>(w.x) < f.pr) {
+                    sel |= 1u << r;
+                    float C[3];
+                    es_draw_f(s, f, td, id[r], step, w, C);
+                    const float o0 = v0[r] - f.u[0], o1 = v1[r] - f.u[1], o2 = v2[r] - f.u[2];
+                    a0 += o0; a1 += o1; a2 += o2;
+                    ae += o0 * o0 + o1 * o1 + o2 * o2;
+                    b0 += C[0]; b1 += C[1]; b2 += C[2];
+                    be += C[0] * C[0] + C[1] * C[1] + C[2] * C[2];
+                    nr += 1.0f;
+                    v0[r] = C[0];
+                    v1[r] = C[1];
+                    v2[r] = C[2];
+                }
+            }
+        }
+    }
+    // conservation factors of the cell (FP64 once per cell)
+    bool apply = false;
+    float uo0 = 0, uo1 = 0, uo2 = 0, mn0 = 0, mn1 = 0, mn2 = 0, alpha = 1;
+    if (relax) {
+        nr = warp_sumf(nr);
+        if (nr >= 2.0f) {
+            a0 = warp_sumf(a0); a1 = warp_sumf(a1); a2 = warp_sumf(a2); ae = warp_sumf(ae);
+            b0 = warp_sumf(b0); b1 = warp_sumf(b1); b2 = warp_sumf(b2); be = warp_sumf(be);
+            const double inv = 1.0 / (double)nr;
+            const double Eo = (double)ae - ((double)a0 * a0 + (double)a1 * a1 + (double)a2 * a2) * inv;
+            const double En = (double)be - ((double)b0 * b0 + (double)b1 * b1 + (double)b2 * b2) * inv;
+            if (En > 0.0) {
+                apply = true;
+                alpha = (float)sqrt(Eo / En);
+                uo0 = (float)((double)f.u[0] + a0 * inv);
+                uo1 = (float)((double)f.u[1] + a1 * inv);
+                uo2 = (float)((double)f.u[2] + a2 * inv);
+                mn0 = (float)(b0 * inv);
+                mn1 = (float)(b1 * inv);
+                mn2 = (float)(b2 * inv);
+            }
+        }
+        if (lane == 0 && apply) atomicAdd(&s.dyn->counters[kCntRelaxed], (unsigned long long)nr);
+    }
+    for (uint32_t ch = 0; ch < nch; ++ch) {
+        if (nch > 1) {
+            sel = 0;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const uint32_t j = ch * CH + r * 32 + lane;
+                x[r] = 0.0f;
+                if (j < n) load_particle<DIM>(s, p, base, nb, spl, j, x[r], y[r], v0[r], v1[r], v2[r], id[r]);
+                if (relax && j < n) {
+                    const uint4 w = draw(s, id[r], step, kRelax, 0);
+                    if (u01<float>(w.x) < f.pr) {
+                        sel |= 1u << r;
+                        float C[3];
+                        es_draw_f(s, f, td, id[r], step, w, C);
+                        v0[r] = C[0];
+                        v1[r] = C[1];
+                        v2[r] = C[2];
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const uint32_t j = ch * CH + r * 32 + lane;
+            if ((sel >> r) & 1u) {
+                if (apply) {
+                    v0[r] = uo0 + alpha * (v0[r] - mn0);
+                    v1[r] = uo1 + alpha * (v1[r] - mn1);
+                    v2[r] = uo2 + alpha * (v2[r] - mn2);
+                } else {   // a lone relaxed particle keeps its old velocity
+                    float ox, oy, ov0, ov1, ov2;
+                    uint32_t oid;
+                    load_particle<DIM>(s, p, base, nb, spl, j, ox, oy, ov0, ov1, ov2, oid);
+                    v0[r] = ov0;
+                    v1[r] = ov1;
+                    v2[r] = ov2;
+                }
+            }
+            if (FLUSH) {
+                if (j < n && apply && ((sel >> r) & 1u))
+                    store_velocity<DIM>(s, p, base, nb, spl, j, v0[r], v1[r], v2[r]);
+                continue;
+            }
+            uint32_t key = kNoCell;
+            float cv[3] = {v0[r], v1[r], v2[r]};
+            if (j < n) {
+                if (advect_fast<DIM>(s, step, id[r], x[r], y[r], cv)) {
+                    const int dc = cell_index<float>(s, x[r], y[r]);
+                    if (!in_buffer(s, dc)) key = (uint32_t)dc;
+                    else atomicAdd(&s.dyn->counters[kCntRemoved], 1ull);
+                }
+            }
+            emit<DIM>(s, q, key, x[r], y[r], cv[0], cv[1], cv[2], id[r], lane);
+        }
+    }
+}
+
+template <int R, int DIM, bool FLUSH>
+__global__ void __launch_bounds__(256, 1) k_g2(const SimDev* __restrict__ sims, const int2* __restrict__ tiles,
+                                            const int* __restrict__ ntiles) {
+    __shared__ uint32_t spl_all[8][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nt = *ntiles;
+    for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+        const int2 tile = tiles[t];
+        const SimDev& s = sims[tile.x];
+        if (s.dim != DIM) continue;
+        const int p = s.dyn->cur;
+        const uint32_t step = s.dyn->step;
+        const bool pending = s.dyn->relax_pending != 0;
+        if (FLUSH && !pending) continue;
+        for (int cc = warp; cc < kCTile; cc += 8) {
+            const int cell = tile.y + cc;
+            if (cell >= s.K) break;
+            g2_cell<R, DIM, FLUSH>(s, cell, p, step, pending, spl_all[warp], lane);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_g1: per-cell moments (Eq. 1), two passes over the cell's particles
+// ---------------------------------------------------------------------------
+template <int R>
+__global__ void __launch_bounds__(256) k_g1(const SimDev* __restrict__ sims, const int2* __restrict__ tiles,
+                                            const int* __restrict__ ntiles) {
+    __shared__ uint32_t spl_all[8][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nt = *ntiles;
+    for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+        const int2 tile = tiles[t];
+        const SimDev& s = sims[tile.x];
+        const int K = s.K;
+        const int q = s.dyn->cur ^ 1;
+        for (int cc = warp; cc < kCTile; cc += 8) {
+            const int cell = tile.y + cc;
+            if (cell >= K) break;
+            const uint32_t base = s.lay[q][cell];
+            const uint32_t capc = s.lay[q][cell + 1] - base;
+            const uint32_t arrived = s.cnt[q][cell];
+            const uint32_t nb = min(arrived, capc);
+            uint32_t nsp = 0;
+            if (arrived > nb) nsp = collect_spill(s, q, cell, spl_all[warp], lane);
+            const uint32_t n = nb + nsp;
+            const uint32_t CH = 32u * R;
+            const uint32_t nch = (n + CH - 1) / CH;
+            float v0[R], v1[R], v2[R];
+            float m0 = 0, m1 = 0, m2 = 0;
+            const float* V0 = (const float*)s.vel[q][0];
+            const float* V1 = (const float*)s.vel[q][1];
+            const float* V2 = (const float*)s.vel[q][2];
+            auto load = [&](uint32_t j, float& a, float& b, float& c) {
+                if (j < nb) {
+                    a = V0[base + j];
+                    b = V1[base + j];
+                    c = V2[base + j];
+                } else {
+                    const uint32_t i = spl_all[warp][j - nb];
+                    a = s.sp_vel[q][0][i];
+                    b = s.sp_vel[q][1][i];
+                    c = s.sp_vel[q][2][i];
+                }
+            };
+            // pass 1: mean
+            for (uint32_t ch = 0; ch < nch; ++ch) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const uint32_t j = ch * CH + r * 32 + lane;
+                    v0[r] = v1[r] = v2[r] = 0.0f;
+                    if (j < n) load(j, v0[r], v1[r], v2[r]);
+                    m0 += v0[r];
+                    m1 += v1[r];
+                    m2 += v2[r];
+                }
+            }
+            m0 = warp_sumf(m0);
+            m1 = warp_sumf(m1);
+            m2 = warp_sumf(m2);
+            const float inv = n > 0 ? 1.0f / (float)n : 0.0f;
+            const float u0 = m0 * inv, u1 = m1 * inv, u2 = m2 * inv;
+            // pass 2: sums of C = c - u0
+            float S[12];
+#pragma unroll
+            for (int k = 0; k < 12; ++k) S[k] = 0.0f;
+            for (uint32_t ch = 0; ch < nch; ++ch) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const uint32_t j = ch * CH + r * 32 + lane;
+                    if (nch > 1) {
+                        v0[r] = v1[r] = v2[r] = 0.0f;
+                        if (j < n) load(j, v0[r], v1[r], v2[r]);
+                    }
+                    if (j < n) {
+                        const float C0 = v0[r] - u0, C1 = v1[r] - u1, C2 = v2[r] - u2;
+                        const float c2 = C0 * C0 + C1 * C1 + C2 * C2;
+                        S[0] += C0; S[1] += C1; S[2] += C2;
+                        S[3] += C0 * C0; S[4] += C1 * C1; S[5] += C2 * C2;
+                        S[6] += C0 * C1; S[7] += C0 * C2; S[8] += C1 * C2;
+                        S[9] += c2 * C0; S[10] += c2 * C1; S[11] += c2 * C2;
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 12; ++k) S[k] = warp_sumf(S[k]);
+            if (lane == 0) {
+                s.mom[cell] = (double)n;
+#pragma unroll
+                for (int k = 0; k < 12; ++k) s.mom[(size_t)(k + 1) * K + cell] = (double)S[k];
+                s.ushift[cell] = u0;
+                s.ushift[(size_t)K + cell] = u1;
+                s.ushift[(size_t)2 * K + cell] = u2;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_params_f: per-cell parameters; FP64 for the stress tensor, Eq. 33 and the
+// Cholesky factor, FP32 for viscosity, mean free path, Kn_GLL and P_ne
+// ---------------------------------------------------------------------------
+struct LocalF {
+    int valid, N;
+    float n, T, umag;
+};
+
+__device__ __forceinline__ void local_f(const SimDev& s, int cell, LocalF& L, double* u, double* P, double* theta) {
+    const int K = s.K;
+    const double* M = s.mom;
+    const int N = (int)M[cell];
+    L.N = N;
+    L.valid = 0;
+    L.n = (float)(N * s.w);
+    L.T = 0;
+    L.umag = 0;
+    if (N < 1) return;
+    const double inv = 1.0 / N;
+    const double d0 = M[K + cell] * inv, d1 = M[2 * K + cell] * inv, d2 = M[3 * K + cell] * inv;
+    const double uu[3] = {s.ushift[cell] + d0, s.ushift[K + cell] + d1, s.ushift[2 * K + cell] + d2};
+    const double p0 = M[4 * K + cell] * inv - d0 * d0, p1 = M[5 * K + cell] * inv - d1 * d1,
+                 p2 = M[6 * K + cell] * inv - d2 * d2;
+    const double th = (p0 + p1 + p2) / 3.0;
+    if (u) {
+        u[0] = uu[0]; u[1] = uu[1]; u[2] = uu[2];
+    }
+    if (P) {
+        P[0] = p0; P[1] = p1; P[2] = p2;
+        P[3] = M[7 * K + cell] * inv - d0 * d1;
+        P[4] = M[8 * K + cell] * inv - d0 * d2;
+        P[5] = M[9 * K + cell] * inv - d1 * d2;
+    }
+    if (theta) *theta = th;
+    L.valid = N >= 2 && th > 0.0;
+    if (!L.valid) return;
+    L.T = (float)(th / s.R);
+    L.umag = sqrtf((float)(uu[0] * uu[0] + uu[1] * uu[1] + uu[2] * uu[2]));
+}
+
+__global__ void __launch_bounds__(128) k_params_f(const SimDev* __restrict__ sims, const int2* __restrict__ tiles,
+                                                  const int* __restrict__ ntiles) {
+    const int nt = *ntiles;
+    for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+        const int2 tile = tiles[t];
+        const SimDev& s = sims[tile.x];
+        const int K = s.K;
+        for (int cc = threadIdx.x; cc < kCTile; cc += blockDim.x) {
+            const int cell = tile.y + cc;
+            if (cell >= K) break;
+            LocalF L;
+            double u[3] = {0, 0, 0}, P[6], th = 0;
+            local_f(s, cell, L, u, P, &th);
+            double f[kNFields];
+            for (int k = 0; k < kNFields; ++k) f[k] = 0.0;
+            f[0] = L.N * s.w;
+            f[15] = L.N;
+            if (L.N >= 1) {
+                f[1] = u[0]; f[2] = u[1]; f[3] = u[2];
+            }
+            float pr[kNFPrm];
+            for (int k = 0; k < kNFPrm; ++k) pr[k] = 0.0f;
+            pr[0] = (float)u[0]; pr[1] = (float)u[1]; pr[2] = (float)u[2];
+            pr[3] = (float)th;
+            if (L.valid) {
+                const float thf = (float)th;
+                const float rho = L.n * (float)s.mass;
+                const float pf = rho * thf;
+                const float mu = (float)s.mu_ref * __powf(L.T / (float)s.T_ref, (float)s.omega);   // Eq. 35
+                const float nu = pf / mu;
+                const float lam = 1.2766152f * mu / sqrtf(rho * pf);     // Eq. 36: 16 / (5 sqrt(2 pi))
+                float pne;
+                if (s.mode == kModeSP) pne = 0.0f;
+                else if (s.mode == kModeFixed) pne = (float)s.fixed_pne;
+                else {
+                    const float Qc[3] = {L.n, L.T, L.umag};
+                    float g2[3] = {0, 0, 0};
+                    for (int axis = s.dim == 1 ? 1 : 0; axis < 2; ++axis) {
+                        const float h = (float)(axis == 0 ? s.dx : s.dy);
+                        int m = neighbor(s, cell, axis, -1), p = neighbor(s, cell, axis, +1);
+                        LocalF Lm, Lp;
+                        if (m >= 0) {
+                            local_f(s, m, Lm, nullptr, nullptr, nullptr);
+                            if (!Lm.valid) m = -1;
+                        }
+                        if (p >= 0) {
+                            local_f(s, p, Lp, nullptr, nullptr, nullptr);
+                            if (!Lp.valid) p = -1;
+                        }
+                        const float Qm[3] = {Lm.n, Lm.T, Lm.umag}, Qp[3] = {Lp.n, Lp.T, Lp.umag};
+                        for (int k = 0; k < 3; ++k) {
+                            float d = 0.0f;
+                            if (m >= 0 && p >= 0) d = (Qp[k] - Qm[k]) / (2.0f * h);
+                            else if (p >= 0) d = (Qp[k] - Qc[k]) / h;
+                            else if (m >= 0) d = (Qc[k] - Qm[k]) / h;
+                            g2[k] += d * d;
+                        }
+                    }
+                    const float a_s = sqrtf((float)kGammaMono * thf);
+                    const float kn = fmaxf(lam * sqrtf(g2[0]) / L.n,
+                                           fmaxf(lam * sqrtf(g2[1]) / L.T, lam * sqrtf(g2[2]) / fmaxf(L.umag, a_s)));
+                    pne = __expf(-kn / (float)kKnC);                                              // Eqs. 16-18
+                }
+                const double fs = 1.0 + 0.5 * s.dt * (double)nu * pne;                         // Eq. 33
+                const double fq = 1.0 + 0.5 * s.dt * (double)nu * s.Pr * pne;
+                const double sig[6] = {(P[0] - th) / fs, (P[1] - th) / fs, (P[2] - th) / fs, P[3] / fs, P[4] / fs,
+                                       P[5] / fs};
+                const double b = 1.0 - 1.0 / s.Pr;                                              // Eq. 6c
+                const double A00 = th + b * sig[0], A11 = th + b * sig[1], A22 = th + b * sig[2];
+                const double A10 = b * sig[3], A20 = b * sig[4], A21 = b * sig[5];
+                double l00 = 0, l10 = 0, l11 = 0, l20 = 0, l21 = 0, l22 = 0;
+                bool ok = A00 > 0.0;
+                if (ok) {
+                    l00 = sqrt(A00);
+                    l10 = A10 / l00;
+                    l20 = A20 / l00;
+                    const double d1 = A11 - l10 * l10;
+                    ok = d1 > 0.0;
+                    if (ok) {
+                        l11 = sqrt(d1);
+                        l21 = (A21 - l20 * l10) / l11;
+                        const double d2 = A22 - l20 * l20 - l21 * l21;
+                        ok = d2 > 0.0;
+                        if (ok) l22 = sqrt(d2);
+                    }
+                }
+                if (!ok) {
+                    const double r = sqrt(th);
+                    l00 = l11 = l22 = r;
+                    l10 = l20 = l21 = 0.0;
+                    atomicAdd(&s.dyn->counters[kCntChol], 1ull);
+                }
+                const float nues = (float)s.Pr * nu;
+                pr[4] = (float)l00; pr[5] = (float)l10; pr[6] = (float)l11;
+                pr[7] = (float)l20; pr[8] = (float)l21; pr[9] = (float)l22;
+                pr[10] = -expm1f(-nues * (float)s.dt);                                        // Eqs. 8b, 9
+                pr[11] = nu;
+                pr[12] = nues;
+                pr[13] = pne;
+                pr[14] = 1.0f;
+                // heat flux from the third central moment of the shifted sums
+                const double* M = s.mom;
+                const double inv = 1.0 / L.N;
+                const double d0 = M[K + cell] * inv, d1 = M[2 * K + cell] * inv, d2 = M[3 * K + cell] * inv;
+                const double m00 = M[4 * K + cell] * inv, m11 = M[5 * K + cell] * inv, m22 = M[6 * K + cell] * inv;
+                const double m01 = M[7 * K + cell] * inv, m02 = M[8 * K + cell] * inv, m12 = M[9 * K + cell] * inv;
+                const double t0 = M[10 * K + cell] * inv, t1 = M[11 * K + cell] * inv, t2 = M[12 * K + cell] * inv;
+                const double tr = m00 + m11 + m22, dd = d0 * d0 + d1 * d1 + d2 * d2;
+                const double Q0 = 0.5 * (t0 - d0 * tr - 2.0 * (m00 * d0 + m01 * d1 + m02 * d2) + 2.0 * d0 * dd);
+                const double Q1 = 0.5 * (t1 - d1 * tr - 2.0 * (m01 * d0 + m11 * d1 + m12 * d2) + 2.0 * d1 * dd);
+                const double Q2 = 0.5 * (t2 - d2 * tr - 2.0 * (m02 * d0 + m12 * d1 + m22 * d2) + 2.0 * d2 * dd);
+                const double rhod = L.N * s.w * s.mass, pd = rhod * th;
+                f[4] = th / s.R;
+                f[5] = pd + rhod * sig[0];
+                f[6] = pd + rhod * sig[1];
+                f[7] = pd + rhod * sig[2];
+                f[8] = rhod * sig[3];
+                f[9] = rhod * sig[4];
+                f[10] = rhod * sig[5];
+                f[11] = rhod * Q0 / fq;
+                f[12] = rhod * Q1 / fq;
+                f[13] = rhod * Q2 / fq;
+                f[14] = pne;
+            }
+            for (int k = 0; k < kNFPrm; ++k) s.fprm[(size_t)k * K + cell] = pr[k];
+            const bool first = s.dyn->nsamples == 0;
+            for (int k = 0; k < kNFields; ++k) {
+                s.inst[(size_t)k * K + cell] = f[k];
+                double* a = &s.avg[(size_t)k * K + cell];
+                *a = first ? f[k] : s.avg_keep * *a + f[k] * s.avg_new;                         // Eq. 34
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_inject_f: reservoir buffer cells, written into buffer q
+// ---------------------------------------------------------------------------
+template <int DIM>
+__global__ void __launch_bounds__(256) k_inject_f(const SimDev* __restrict__ sims, const int2* __restrict__ tiles,
+                                                  const int* __restrict__ ntiles) {
+    const int nt = *ntiles;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+        const int2 tile = tiles[t];
+        const SimDev& s = sims[tile.x];
+        if (!s.has_reservoir || s.dim != DIM) continue;
+        const uint32_t step = s.dyn->step, next_pid = s.dyn->next_pid;
+        const int q = s.dyn->cur ^ 1;
+        for (int cc = warp; cc < kCTile; cc += 8) {
+            const int cell = tile.y + cc;
+            if (cell >= s.K) break;
+            const uint32_t cnt = s.inj_count[cell];
+            if (cnt == 0) continue;
+            const FaceDev& F = s.face[buffer_face(s, cell)];
+            for (uint32_t k0 = 0; k0 < cnt; k0 += 32) {
+                const uint32_t k = k0 + lane;
+                uint32_t key = kNoCell;
+                float x = 0, y = 0, c[3] = {0, 0, 0};
+                uint32_t pid = 0;
+                if (k < cnt) {
+                    pid = next_pid + s.inj_pidoff[cell] + k;
+                    make_particle<float>(s, cell, pid, step, kInject, F.theta, F.u, x, y, c);
+                    key = (uint32_t)cell;
+                }
+                emit<DIM>(s, q, key, x, y, c[0], c[1], c[2], pid, lane);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_layout: histogram -> bucket sizes (slack for arrivals) -> exclusive scan
+// setup == true builds the write layout of buffer cur ^ 1 right after the
+// initial fill (counts of buffer cur from the exact start offsets).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t bucket_size(const SimDev& s, const uint32_t* cnt, int c) {
+    const int ix = c % s.nx, iy = c / s.nx;
+    uint32_t m = 0;
+    for (int dy = -1; dy <= 1; ++dy) {
+        const int jy = iy + dy;
+        if (jy < 0 || jy >= s.ny) continue;
+        for (int dx = (s.dim == 2 ? -1 : 0); dx <= (s.dim == 2 ? 1 : 0); ++dx) {
+            const int jx = ix + dx;
+            if (jx < 0 || jx >= s.nx) continue;
+            m = max(m, cnt[jy * s.nx + jx]);
+        }
+    }
+    return m + (m >> 2) + 16u + (s.has_reservoir ? s.inj_count[c] : 0u);
+}
+
+template <bool SETUP>
+__global__ void __launch_bounds__(1024) k_layout(const SimDev* __restrict__ sims, int nsims) {
+    __shared__ uint32_t warp_sums[32];
+    __shared__ unsigned long long tot_full, tot_exact;
+    __shared__ uint32_t carry;
+    for (int si = blockIdx.x; si < nsims; si += gridDim.x) {
+        const SimDev& s = sims[si];
+        SimDyn* dyn = s.dyn;
+        const int K = s.K;
+        const int cur = dyn->cur;
+        const int src = SETUP ? cur : cur ^ 1;   // counts of the freshly written buffer
+        const int dst = SETUP ? cur ^ 1 : cur;   // layout for the next write
+        if (SETUP) {
+            for (int c = threadIdx.x; c <= K; c += blockDim.x) {
+                s.lay[cur][c] = s.start[c];
+                if (c < K) s.cnt[cur][c] = s.start[c + 1] - s.start[c];
+            }
+            __syncthreads();
+        }
+        const uint32_t* C = s.cnt[src];
+        if (threadIdx.x == 0) {
+            tot_full = 0;
+            tot_exact = 0;
+            carry = 0;
+        }
+        __syncthreads();
+        unsigned long long lf = 0, le = 0;
+        for (int c = threadIdx.x; c < K; c += blockDim.x) {
+            lf += bucket_size(s, C, c);
+            le += C[c];
+        }
+        atomicAdd(&tot_full, lf);
+        atomicAdd(&tot_exact, le);
+        __syncthreads();
+        // bucket sizes with slack when they fit, else the exact demand plus an even share of what is left
+        const unsigned long long demand = tot_exact + (s.has_reservoir ? s.inj_total : 0u);
+        const bool full = tot_full <= (unsigned long long)s.cap;
+        const uint32_t extra = (!full && demand < (unsigned long long)s.cap)
+                                   ? (uint32_t)(((unsigned long long)s.cap - demand) / (unsigned long long)K)
+                                   : 0u;
+        if (!full && demand > (unsigned long long)s.cap && threadIdx.x == 0)
+            atomicAdd(&dyn->counters[kCntOverflow], 1ull);
+        for (int base = 0; base < K; base += blockDim.x) {
+            const int c = base + threadIdx.x;
+            uint32_t v = 0;
+            if (c < K) v = full ? bucket_size(s, C, c) : C[c] + (s.has_reservoir ? s.inj_count[c] : 0u) + extra;
+            uint32_t x = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if ((threadIdx.x & 31) >= o) x += y;
+            }
+            if ((threadIdx.x & 31) == 31) warp_sums[threadIdx.x >> 5] = x;
+            __syncthreads();
+            if (threadIdx.x < 32) {
+                uint32_t ws = threadIdx.x < (blockDim.x >> 5) ? warp_sums[threadIdx.x] : 0u;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, ws, o);
+                    if (threadIdx.x >= o) ws += y;
+                }
+                warp_sums[threadIdx.x] = ws;
+            }
+            __syncthreads();
+            const uint32_t before = (threadIdx.x >= 32 ? warp_sums[(threadIdx.x >> 5) - 1] : 0u) + carry;
+            if (c < K) s.lay[dst][c] = before + x - v;
+            __syncthreads();
+            if (threadIdx.x == blockDim.x - 1) carry = before + x;
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            s.lay[dst][K] = carry;
+            if (!SETUP) dyn->n = (uint32_t)min(tot_exact, (unsigned long long)0xFFFFFFFFu);
+            dyn->sp_n[dst] = 0;
+            if (SETUP) {
+                dyn->sp_n[cur] = 0;
+                dyn->relax_pending = 0;
+            }
+        }
+        for (int c = threadIdx.x; c < K; c += blockDim.x) s.cnt[dst][c] = 0;
+        __syncthreads();
+    }
+}
+
+// end of a fused step (mode 0) or after a flush of the pending relaxation (mode 1)
+__global__ void k_finish_f(const SimDev* __restrict__ sims, int nsims, int mode) {
+    for (int si = blockIdx.x * blockDim.x + threadIdx.x; si < nsims; si += gridDim.x * blockDim.x) {
+        const SimDev& s = sims[si];
+        SimDyn* d = s.dyn;
+        if (mode == 1) {
+            d->relax_pending = 0;
+            continue;
+        }
+        if (s.has_reservoir) {
+            d->next_pid += s.inj_total;
+            d->counters[kCntInjected] += s.inj_total;
+        }
+        d->cur ^= 1;
+        d->step += 1;
+        d->nsamples += 1;
+        d->relax_pending = 1;
+    }
+}
+
+template <int R, bool FLUSH>
+void launch_g2(const Launch& L) {
+    if (L.dims & 1) k_g2<R, 1, FLUSH><<<L.grid_c, 256, 0, L.stream>>>(L.sims, L.ctiles, L.nctiles);
+    if (L.dims & 2) k_g2<R, 2, FLUSH><<<L.grid_c, 256, 0, L.stream>>>(L.sims, L.ctiles, L.nctiles);
+}
+
+}  // namespace
+
+void launch_fused_setup(const Launch& L) { k_layout<true><<<L.nsims, 1024, 0, L.stream>>>(L.sims, L.nsims); }
+
+void launch_fused_relax_stream(const Launch& L, int R, bool flush_only) {
+    if (flush_only) {
+        if (R <= 4) launch_g2<4, true>(L);
+        else if (R <= 8) launch_g2<8, true>(L);
+        else launch_g2<12, true>(L);
+        k_finish_f<<<(L.nsims + 127) / 128, 128, 0, L.stream>>>(L.sims, L.nsims, 1);
+        return;
+    }
+    if (R <= 4) launch_g2<4, false>(L);
+    else if (R <= 8) launch_g2<8, false>(L);
+    else launch_g2<12, false>(L);
+}
+
+void launch_fused_inject(const Launch& L) {
+    if (L.dims & 1) k_inject_f<1><<<L.grid_c, 256, 0, L.stream>>>(L.sims, L.ctiles, L.nctiles);
+    if (L.dims & 2) k_inject_f<2><<<L.grid_c, 256, 0, L.stream>>>(L.sims, L.ctiles, L.nctiles);
+}
+
+void launch_fused_moments(const Launch& L, int R) {
+    if (R <= 4) k_g1<4><<<L.grid_c, 256, 0, L.stream>>>(L.sims, L.ctiles, L.nctiles);
+    else if (R <= 8) k_g1<8><<<L.grid_c, 256, 0, L.stream>>>(L.sims, L.ctiles, L.nctiles);
+    else k_g1<12><<<L.grid_c, 256, 0, L.stream>>>(L.sims, L.ctiles, L.nctiles);
+}
+
+void launch_fused_params(const Launch& L) { k_params_f<<<L.grid_c, 64, 0, L.stream>>>(L.sims, L.ctiles, L.nctiles); }
+
+void launch_fused_layout(const Launch& L) { k_layout<false><<<L.nsims, 1024, 0, L.stream>>>(L.sims, L.nsims); }
+
+void launch_fused_finish(const Launch& L) {
+    k_finish_f<<<(L.nsims + 127) / 128, 128, 0, L.stream>>>(L.sims, L.nsims, 0);
+}
+
+}  // namespace usp

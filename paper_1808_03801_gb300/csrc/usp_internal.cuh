@@ -45,7 +45,8 @@ struct SimDyn {
     uint32_t next_pid;  // first id of the next injected particle
     uint32_t nsamples;  // samples folded into the Eq. 34 average
     int cur;            // buffer holding the current state
-    int pad;
+    int relax_pending;  // fused pipeline: the relaxation of the last step is still to be applied
+    uint32_t sp_n[2];   // fused pipeline: entries in the spill lists
     unsigned long long counters[8];
 };
 
@@ -82,9 +83,14 @@ struct SimDev {
     uint32_t* inj_count;  // K (buffer cells only)
     uint32_t* inj_pidoff; // K
     uint32_t inj_total;
-    // fused pipeline scratch (per cell): conservation factors
-    double* cons;         // 7 x K: ubar_old[3], ubar_new[3], alpha (alpha < 0: leave unchanged)
-    float* fprm;          // per-cell parameters in FP32 for the fused kernels (kFPrm x K)
+    // fused pipeline (FP32 storage): slack-bucket layout per buffer parity
+    uint32_t* lay[2];     // K + 1 bucket offsets of buffer b
+    uint32_t* cnt[2];     // K arrivals into buffer b (bucket + spilled)
+    float* sp_pos[2][2];  // spill lists (kSpillCap entries) per parity
+    float* sp_vel[2][3];
+    uint32_t* sp_pid[2];
+    uint32_t* sp_cell[2];
+    float* fprm;          // kNFPrm x K relaxation parameters in FP32
     SimDyn* dyn;
 };
 
@@ -159,12 +165,15 @@ struct Launch {
     const int2* ctiles;   // (sim, first cell) tiles
     const int* nctiles;   // device scalar
     int nsims;
+    int dims;             // bit 0: some simulation is 1-D, bit 1: some is 2-D
     int grid_p, grid_c;   // persistent grid sizes
     cudaStream_t stream;
 };
 
 constexpr int kPTile = 2048;  // particles per tile
 constexpr int kCTile = 64;    // cells per tile
+constexpr int kSpillCap = 4096;  // spill entries per parity (fused pipeline)
+constexpr int kNFPrm = 16;       // u[3], theta, L[6], P_relax, nu, nu_ES, P_ne, valid, spare
 
 void launch_stream(const Launch& L, bool fp64);
 void launch_scan(const Launch& L);
@@ -175,6 +184,15 @@ void launch_params(const Launch& L);
 void launch_relax(const Launch& L, bool fp64);
 void launch_finish(const Launch& L);
 void launch_init(const Launch& L, bool fp64, const double* reg_theta, const double* reg_u, const int* cell_reg);
+void launch_assign(const Launch& L, bool fp64);
+// fused FP32 pipeline (usp_fused.cu); R = particles per lane held in registers
+void launch_fused_setup(const Launch& L);
+void launch_fused_relax_stream(const Launch& L, int R, bool flush_only);
+void launch_fused_inject(const Launch& L);
+void launch_fused_moments(const Launch& L, int R);
+void launch_fused_params(const Launch& L);
+void launch_fused_layout(const Launch& L);
+void launch_fused_finish(const Launch& L);
 cudaError_t debug_philox(int64_t n, const uint32_t* d_ctr, uint32_t k0, uint32_t k1, uint32_t* d_out, cudaStream_t st);
 
 }  // namespace usp

@@ -117,6 +117,7 @@ def lib(build_if_missing: bool = True):
         "usp_batch_info": (c_int, [c_void_p, P(c_int), P(c_size_t)]),
         "usp_batch_destroy": (c_int, [c_void_p]),
         "usp_batch_run_stage": (c_int, [c_void_p, c_int]),
+        "usp_fused_supported": (c_int, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -129,8 +130,9 @@ def lib(build_if_missing: bool = True):
 _STAGES = {
     "plain": [(0, "k_stream"), (2, "k_scan+k_scatter"), (3, "k_moments"), (4, "k_params"), (5, "k_relax"),
               (6, "k_finish")],
+    "fused": [(10, "k_g2"), (12, "k_g1"), (13, "k_params_f"), (14, "k_layout"), (15, "k_finish_f")],
 }
-_LAUNCHES = {"plain": 7}
+_LAUNCHES = {"plain": 7, "fused": 5}
 
 
 def fused_available() -> bool:

@@ -1,0 +1,197 @@
+"""GPU tests of the fused FP32 pipeline (FP32 particles, FP64 per-cell sums).
+
+FP32 storage rounds every particle, so the FP32 path is compared with the
+FP64 oracle statistically: time-averaged fields within 1e-3 relative or a few
+standard errors (batch means), plus exact invariants that hold at any size:
+no particle lost or duplicated, cells consistent with positions, total
+momentum and energy of a periodic box conserved to FP32 rounding.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1808_03801_gb300 import workloads as W
+from tests._util import KB_M_AR
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def usp():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1808_03801_gb300 import usp as U
+    U.lib()
+    assert U.fused_available()
+    return U
+
+
+def _fused(w):
+    w = W.with_precision(w, "fp32")
+    w["params"]["pipeline"] = "fused"
+    return w
+
+
+def _blocks(sim_step, sample, nburn, nblocks, blen):
+    sim_step(nburn)
+    out = []
+    for _ in range(nblocks):
+        acc = 0
+        for _ in range(blen):
+            sim_step(1)
+            acc = acc + sample()
+        out.append(acc / blen)
+    a = np.array(out)
+    return a.mean(0), a.std(0, ddof=1) / math.sqrt(nblocks)
+
+
+def _z(ga, gs, oa, os_):
+    return (ga - oa) / np.sqrt(gs ** 2 + os_ ** 2 + 1e-300)
+
+
+def test_fused_particles_conserved_and_cells_consistent(usp):
+    w = _fused(W.cavity(n=30, ppc=60, Kn=0.01))
+    g = usp.Simulation(w).init_particles()
+    n0 = g.info()["n_particles"]
+    g.step(25)
+    inf = g.info()
+    assert inf["counters"][5] == 0          # no bucket / spill overflow
+    P = g.particles()
+    assert len(P["pid"]) == n0
+    assert np.array_equal(np.sort(P["pid"]), np.arange(n0, dtype=np.uint32))
+    lo = np.float32(0.0)
+    d = np.float32(1e-4 / 30)
+    x = P["pos"][:, 0].astype(np.float32)
+    y = P["pos"][:, 1].astype(np.float32)
+    ix = np.clip(np.floor((x - lo) / d), 0, 29).astype(int)
+    iy = np.clip(np.floor((y - lo) / d), 0, 29).astype(int)
+    assert np.array_equal(iy * 30 + ix, P["cell"])
+    assert np.array_equal(np.bincount(P["cell"], minlength=900), g.sample()[15].astype(int))
+
+
+def test_fused_periodic_box_conserves_momentum_energy(usp):
+    n = 200_000
+    w = _fused(W.homogeneous_box(ppc=n, dt_over_tauc=2.0))
+    w["grid"]["ny"] = 8               # eight periodic cells
+    w["params"]["ppc_ref"] = n // 8
+    pos, vel, pid = W.bimaxwellian(n, seed=2, u=(40.0, -20.0, 5.0))
+    g = usp.Simulation(w).set_particles(pos, vel, pid)
+    g.step(20)
+    P = g.particles()
+    v = P["vel"]
+    assert len(v) == n
+    m0, m1 = vel.sum(0), v.sum(0)
+    e0, e1 = (vel ** 2).sum(), (v ** 2).sum()
+    sc = np.abs(vel).sum()
+    assert np.all(np.abs(m1 - m0) < 2e-6 * sc)
+    assert abs(e1 - e0) < 2e-6 * e0
+    assert g.info()["counters"][4] > 0      # relaxations happened
+
+
+@pytest.mark.parametrize("mode", ["usp", "sp"])
+def test_fused_homogeneous_relaxation_closed_form(usp, mode):
+    """The expectation of one relaxation step (derived from Eqs. 8b, 29-33)
+    holds for the FP32 sampler: sigma' = sigma [e^-a + (1 - e^-a)(1 - 1/Pr) kappa]."""
+    n = 1_000_000
+    w = _fused(W.homogeneous_box(ppc=n, dt_over_tauc=5.0, mode=mode))
+    pos, vel, pid = W.bimaxwellian(n, seed=21)
+    g = usp.Simulation(w).set_particles(pos, vel, pid)
+    g.step(1)                    # moments and parameters of the initial state
+    prm_dt = g.info()["dt"]
+    F = g.sample()
+    g.step(1)                    # applies the relaxation, then samples again
+    F2 = g.sample()
+    o = oracle.OracleSim(W.homogeneous_box(ppc=n, dt_over_tauc=5.0, mode=mode)).set_particles(pos, vel, pid)
+    o.step(1)
+    po = o.params()[0]
+    nu, nu_es = po[11], po[12]
+    a = nu_es * prm_dt
+    if mode == "usp":
+        kappa = 1.0 / (1.0 + 0.5 * nu * prm_dt)
+        f1, f2 = 1.0 + 0.5 * prm_dt * nu, 1.0 + 0.5 * prm_dt * nu  # sampled stress is sigma* (Eq. 33)
+    else:
+        d = (nu_es - nu) * prm_dt
+        kappa = a * math.expm1(d) / (d * math.expm1(a))
+        f1 = f2 = 1.0
+    r = math.exp(-a) + (1 - math.exp(-a)) * (1 - 1 / W.PR_MONO) * kappa
+    rho = F[0, 0] * W.M_AR
+    p = rho * KB_M_AR * F[4, 0]
+    sig0 = (F[5, 0] - p) * f1
+    sig1 = (F2[5, 0] - rho * KB_M_AR * F2[4, 0]) * f2
+    se = p * math.sqrt(2.0 / n)
+    assert abs(sig1 - r * sig0) < 5 * se, (sig1, r * sig0, se)
+
+
+def test_fused_couette_matches_oracle_statistically(usp):
+    base = W.couette(ny=20, ppc=200, Kn=0.1, dt_over_tauc=0.5)
+    g = usp.Simulation(_fused(base)).init_particles()
+    o = oracle.OracleSim(base).init_particles()
+    sel = [1, 4, 8]   # u_x, T, p_xy
+    ga, gs = _blocks(g.step, lambda: g.sample()[sel], 200, 12, 40)
+    oa, os_ = _blocks(o.step, lambda: o.fields()[sel], 200, 12, 40)
+    z = _z(ga, gs, oa, os_)
+    assert np.abs(z).max() < 4.5, np.abs(z).max()
+    assert (z ** 2).mean() < 2.5
+    # temperature to 1e-3 relative where the noise allows
+    assert np.all(np.abs(ga[1] - oa[1]) < np.maximum(1e-3 * oa[1], 4.5 * np.sqrt(gs[1] ** 2 + os_[1] ** 2)))
+
+
+def test_fused_sod_matches_plain_fp64(usp):
+    """Fused FP32 against the plain FP64 GPU path (itself at 1e-12 of the oracle)
+    on a coarse Sod tube: density, velocity, temperature profiles averaged over
+    eight seeds agree within their standard errors."""
+    prof_f, prof_p = [], []
+    for seed in range(1, 9):
+        wf = _fused(W.sod(ny=100, ppc_left=160, seed=seed))
+        wp = W.sod(ny=100, ppc_left=160, seed=seed, precision="fp64")
+        gf = usp.Simulation(wf).init_particles()
+        gp = usp.Simulation(wp).init_particles()
+        gf.step(40)
+        gp.step(40)
+        prof_f.append(gf.sample()[[0, 2, 4]])
+        prof_p.append(gp.sample()[[0, 2, 4]])
+    pf, pp = np.array(prof_f), np.array(prof_p)
+    z = (pf.mean(0) - pp.mean(0)) / np.sqrt(pf.var(0, ddof=1) / 8 + pp.var(0, ddof=1) / 8 + 1e-300)
+    assert np.abs(z).max() < 5.0
+    assert (z ** 2).mean() < 2.5
+
+
+def test_fused_slit_particle_balance(usp):
+    """Reservoir refill and outflow: the fused run keeps the same particle count
+    as the FP64 oracle within the statistical spread, and nothing overflows."""
+    base = W.slit(nx=40, ny=20, ppc=30)
+    g = usp.Simulation(_fused(base)).init_particles()
+    o = oracle.OracleSim(W.with_precision(base, "fp64")).init_particles()
+    ng, no = [], []
+    for _ in range(30):
+        g.step(2)
+        o.step(2)
+        ng.append(g.info()["n_particles"])
+        no.append(o.n)
+    assert g.info()["counters"][5] == 0
+    ng, no = np.array(ng[10:]), np.array(no[10:])
+    assert abs(ng.mean() - no.mean()) < 0.01 * no.mean()
+    P = g.particles()
+    assert len(np.unique(P["pid"])) == len(P["pid"])
+
+
+def test_fused_batch_equals_alone_statistically(usp):
+    """The same simulation alone and inside a batch of uneven neighbours gives
+    the same time-averaged fields within their standard errors."""
+    base = _fused(W.couette(ny=16, ppc=150, Kn=0.1))
+    alone = usp.Simulation(base).init_particles()
+    mixed = usp.Simulation(base).init_particles()
+    others = [usp.Simulation(_fused(W.cavity(n=12, ppc=40, Kn=0.05, seed=5))).init_particles(),
+              usp.Simulation(_fused(W.sod(ny=50, ppc_left=80, seed=9))).init_particles()]
+    B = usp.Batch(hbm_budget=8 << 30)
+    for s in [mixed] + others:
+        assert B.admit(s) == 0
+    sel = [1, 4, 8]
+    ga, gs = _blocks(alone.step, lambda: alone.sample()[sel], 100, 10, 30)
+    ma, ms = _blocks(B.step, lambda: mixed.sample()[sel], 100, 10, 30)
+    z = _z(ga, gs, ma, ms)
+    assert np.abs(z).max() < 4.5
+    B.retire(mixed)
+    assert mixed.info()["step"] == 100 + 300
