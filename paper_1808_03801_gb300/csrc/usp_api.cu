@@ -769,7 +769,8 @@ static int get_particles_fused(usp_handle* h, double* pos, double* vel, uint32_t
     for (int c = 0; c < K; ++c) n += cnt[c];
     if (n_out) *n_out = n;
     if (n > cap) return fail(h, USP_ERR_CAPACITY, "output arrays too small");
-    const int64_t slots = lay[K];
+    const int64_t slots = std::min<int64_t>(lay[K], s.cap);
+    for (int c = 0; c <= K; ++c) lay[c] = (uint32_t)std::min<int64_t>(lay[c], s.cap);
     std::vector<float> P[5];
     const int planes[5][2] = {{0, 0}, {0, 1}, {1, 0}, {1, 1}, {1, 2}};
     for (int k = 0; k < 5; ++k) {

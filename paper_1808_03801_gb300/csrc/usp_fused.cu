@@ -155,7 +155,8 @@ __device__ __forceinline__ void emit(const SimDev& s, int b, uint32_t key, float
     base = __shfl_sync(grp, base, leader);
     const uint32_t rank = base + (uint32_t)__popc(grp & lanemask_lt());
     const uint32_t lo = s.lay[b][key];
-    const uint32_t capd = s.lay[b][key + 1] - lo;
+    const uint32_t hi = min(s.lay[b][key + 1], (uint32_t)s.cap);
+    const uint32_t capd = hi > lo ? hi - lo : 0u;
     if (rank < capd) {
         const uint32_t i = lo + rank;
         if (DIM == 2) ((float*)s.pos[b][0])[i] = x;
@@ -208,7 +209,8 @@ __device__ __forceinline__ void es_draw_f(const SimDev& s, const FCell& f, const
 template <int R, int DIM, bool FLUSH>
 __device__ void g2_cell(const SimDev& s, int cell, int p, uint32_t step, bool pending, uint32_t* spl, int lane) {
     const uint32_t base = s.lay[p][cell];
-    const uint32_t capc = s.lay[p][cell + 1] - base;
+    const uint32_t top = min(s.lay[p][cell + 1], (uint32_t)s.cap);
+    const uint32_t capc = top > base ? top - base : 0u;
     const uint32_t arrived = s.cnt[p][cell];
     const uint32_t nb = min(arrived, capc);
     uint32_t nsp = 0;
@@ -383,7 +385,8 @@ __global__ void __launch_bounds__(256) k_g1(const SimDev* __restrict__ sims, con
             const int cell = tile.y + cc;
             if (cell >= K) break;
             const uint32_t base = s.lay[q][cell];
-            const uint32_t capc = s.lay[q][cell + 1] - base;
+            const uint32_t top = min(s.lay[q][cell + 1], (uint32_t)s.cap);
+            const uint32_t capc = top > base ? top - base : 0u;
             const uint32_t arrived = s.cnt[q][cell];
             const uint32_t nb = min(arrived, capc);
             uint32_t nsp = 0;
