@@ -64,6 +64,7 @@ struct usp_handle {
     std::vector<uint32_t> inj_count_host;
     int batch_refs = 0;
     int fused_R = 8;                  // particles per lane held in registers by the fused kernels
+    cudaStream_t batch_stream = nullptr;   // stream of the batch the handle is admitted to
 };
 
 struct usp_batch {
@@ -719,8 +720,16 @@ extern "C" int usp_run_stage(usp_handle* h, int stage) {
 // ---------------------------------------------------------------------------
 // read-back
 // ---------------------------------------------------------------------------
-static int read_dyn(usp_handle* h, SimDyn* d) {
+// wait for everything queued for this handle (its own stream and, while it is
+// admitted, the stream of its batch)
+static int sync_handle(usp_handle* h) {
     CK(cudaStreamSynchronize(h->stream));
+    if (h->batch_stream) CK(cudaStreamSynchronize(h->batch_stream));
+    return USP_OK;
+}
+
+static int read_dyn(usp_handle* h, SimDyn* d) {
+    if (int rc = sync_handle(h)) return rc;
     CK(cudaMemcpy(d, h->d_dyn, sizeof(SimDyn), cudaMemcpyDeviceToHost));
     if (d->counters[kCntOverflow]) return fail(h, USP_ERR_CAPACITY, "particle slots overflowed during a step");
     return USP_OK;
@@ -737,7 +746,7 @@ extern "C" int usp_sample_macro(usp_handle* h, int which, double* out, size_t ou
     const size_t need = (size_t)kNFields * h->host.K;
     if (out_len < need) return fail(h, USP_ERR_INVALID_ARG, "output too small");
     if (which != USP_SAMPLE_INSTANT && which != USP_SAMPLE_AVERAGED) return fail(h, USP_ERR_INVALID_ARG, "bad field set");
-    CK(cudaStreamSynchronize(h->stream));
+    if (int rc = sync_handle(h)) return rc;
     const double* src = which == USP_SAMPLE_INSTANT ? h->host.inst : h->host.avg;
     CK(cudaMemcpy(out, src, need * sizeof(double), out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
     return USP_OK;
@@ -874,7 +883,7 @@ extern "C" int usp_get_params(usp_handle* h, double* out, size_t out_len) {
     if (!h || !out) return USP_ERR_INVALID_ARG;
     const int K = h->host.K;
     if (out_len < (size_t)kNPrm * K) return fail(h, USP_ERR_INVALID_ARG, "output too small");
-    CK(cudaStreamSynchronize(h->stream));
+    if (int rc = sync_handle(h)) return rc;
     std::vector<double> t((size_t)kNPrm * K);
     CK(cudaMemcpy(t.data(), h->host.prm, sizeof(double) * t.size(), cudaMemcpyDeviceToHost));
     for (int c = 0; c < K; ++c)
@@ -1011,6 +1020,7 @@ extern "C" int usp_batch_admit(usp_batch* b, usp_handle* h) {
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return bfail(b, USP_ERR_CUDA, "handle stream error");
     b->members.push_back(h);
     h->batch_refs++;
+    h->batch_stream = b->stream;
     b->dirty = true;
     return USP_OK;
 }
@@ -1022,6 +1032,7 @@ extern "C" int usp_batch_retire(usp_batch* b, usp_handle* h) {
         if (cudaStreamSynchronize(b->stream) != cudaSuccess) return bfail(b, USP_ERR_CUDA, "batch stream error");
         b->members.erase(b->members.begin() + i);
         h->batch_refs--;
+        h->batch_stream = nullptr;
         h->sorted = true;
         b->dirty = true;
         return USP_OK;
@@ -1143,7 +1154,10 @@ extern "C" int usp_batch_step(usp_batch* b, int nsteps) {
 extern "C" int usp_batch_destroy(usp_batch* b) {
     if (!b) return USP_ERR_INVALID_ARG;
     if (b->stream) cudaStreamSynchronize(b->stream);
-    for (auto* h : b->members) h->batch_refs--;
+    for (auto* h : b->members) {
+        h->batch_refs--;
+        h->batch_stream = nullptr;
+    }
     b->members.clear();
     destroy_graphs(b->graphs);
     cudaFree(b->d_sims);

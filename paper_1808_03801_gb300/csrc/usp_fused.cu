@@ -350,10 +350,14 @@ __global__ void __launch_bounds__(256, 1) k_g2(const SimDev* __restrict__ sims, 
                                             const int* __restrict__ ntiles) {
     __shared__ uint32_t spl_all[8][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __shared__ SimDev sim_sh;
     const int nt = *ntiles;
     for (int t = blockIdx.x; t < nt; t += gridDim.x) {
         const int2 tile = tiles[t];
-        const SimDev& s = sims[tile.x];
+        __syncthreads();
+        load_sim(sim_sh, sims[tile.x]);
+        __syncthreads();
+        const SimDev& s = sim_sh;
         if (s.dim != DIM) continue;
         const int p = s.dyn->cur;
         const uint32_t step = s.dyn->step;
@@ -375,10 +379,14 @@ __global__ void __launch_bounds__(256) k_g1(const SimDev* __restrict__ sims, con
                                             const int* __restrict__ ntiles) {
     __shared__ uint32_t spl_all[8][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __shared__ SimDev sim_sh;
     const int nt = *ntiles;
     for (int t = blockIdx.x; t < nt; t += gridDim.x) {
         const int2 tile = tiles[t];
-        const SimDev& s = sims[tile.x];
+        __syncthreads();
+        load_sim(sim_sh, sims[tile.x]);
+        __syncthreads();
+        const SimDev& s = sim_sh;
         const int K = s.K;
         const int q = s.dyn->cur ^ 1;
         for (int cc = warp; cc < kCTile; cc += 8) {
@@ -507,10 +515,14 @@ __device__ __forceinline__ void local_f(const SimDev& s, int cell, LocalF& L, do
 
 __global__ void __launch_bounds__(128) k_params_f(const SimDev* __restrict__ sims, const int2* __restrict__ tiles,
                                                   const int* __restrict__ ntiles) {
+    __shared__ SimDev sim_sh;
     const int nt = *ntiles;
     for (int t = blockIdx.x; t < nt; t += gridDim.x) {
         const int2 tile = tiles[t];
-        const SimDev& s = sims[tile.x];
+        __syncthreads();
+        load_sim(sim_sh, sims[tile.x]);
+        __syncthreads();
+        const SimDev& s = sim_sh;
         const int K = s.K;
         for (int cc = threadIdx.x; cc < kCTile; cc += blockDim.x) {
             const int cell = tile.y + cc;
@@ -646,11 +658,15 @@ __global__ void __launch_bounds__(128) k_params_f(const SimDev* __restrict__ sim
 template <int DIM>
 __global__ void __launch_bounds__(256) k_inject_f(const SimDev* __restrict__ sims, const int2* __restrict__ tiles,
                                                   const int* __restrict__ ntiles) {
+    __shared__ SimDev sim_sh;
     const int nt = *ntiles;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int t = blockIdx.x; t < nt; t += gridDim.x) {
         const int2 tile = tiles[t];
-        const SimDev& s = sims[tile.x];
+        __syncthreads();
+        load_sim(sim_sh, sims[tile.x]);
+        __syncthreads();
+        const SimDev& s = sim_sh;
         if (!s.has_reservoir || s.dim != DIM) continue;
         const uint32_t step = s.dyn->step, next_pid = s.dyn->next_pid;
         const int q = s.dyn->cur ^ 1;

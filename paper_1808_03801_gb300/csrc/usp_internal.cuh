@@ -51,8 +51,9 @@ struct SimDyn {
 };
 
 // Everything a kernel needs to know about one simulation.  Lives in device
-// memory (one entry per simulation of a batch).
-struct SimDev {
+// memory (one entry per simulation of a batch); kernels stage it in shared
+// memory so that its fields stay cheap to read next to global stores.
+struct alignas(16) SimDev {
     int dim, nx, ny, K;
     double lo[2], hi[2], dx, dy;
     FaceDev face[4];
@@ -93,6 +94,13 @@ struct SimDev {
     float* fprm;          // kNFPrm x K relaxation parameters in FP32
     SimDyn* dyn;
 };
+
+// copy one simulation descriptor into shared memory (whole block)
+__device__ __forceinline__ void load_sim(SimDev& dst, const SimDev& src) {
+    const int4* a = reinterpret_cast<const int4*>(&src);
+    int4* b = reinterpret_cast<int4*>(&dst);
+    for (int i = threadIdx.x; i < (int)(sizeof(SimDev) / 16); i += blockDim.x) b[i] = a[i];
+}
 
 // -------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds, each two

@@ -24,10 +24,14 @@ namespace usp {
 template <class T>
 __global__ void __launch_bounds__(256) k_stream(const SimDev* __restrict__ sims, const int2* __restrict__ tiles,
                                                 const int* __restrict__ ntiles) {
+    __shared__ SimDev sim_sh;
     const int nt = *ntiles;
     for (int t = blockIdx.x; t < nt; t += gridDim.x) {
         const int2 tile = tiles[t];
-        const SimDev& s = sims[tile.x];
+        __syncthreads();
+        load_sim(sim_sh, sims[tile.x]);
+        __syncthreads();
+        const SimDev& s = sim_sh;
         const uint32_t n = s.dyn->n;
         const uint32_t step = s.dyn->step;
         const int cur = s.dyn->cur;
@@ -63,10 +67,14 @@ __global__ void __launch_bounds__(256) k_stream(const SimDev* __restrict__ sims,
 template <class T>
 __global__ void __launch_bounds__(256) k_assign(const SimDev* __restrict__ sims, const int2* __restrict__ tiles,
                                                 const int* __restrict__ ntiles) {
+    __shared__ SimDev sim_sh;
     const int nt = *ntiles;
     for (int t = blockIdx.x; t < nt; t += gridDim.x) {
         const int2 tile = tiles[t];
-        const SimDev& s = sims[tile.x];
+        __syncthreads();
+        load_sim(sim_sh, sims[tile.x]);
+        __syncthreads();
+        const SimDev& s = sim_sh;
         const uint32_t n = s.dyn->n;
         PView<T> P = view<T>(s, s.dyn->cur);
         for (int j = threadIdx.x; j < kPTile; j += blockDim.x) {
@@ -135,10 +143,14 @@ __global__ void __launch_bounds__(1024) k_scan(const SimDev* __restrict__ sims, 
 template <class T>
 __global__ void __launch_bounds__(256) k_scatter(const SimDev* __restrict__ sims, const int2* __restrict__ tiles,
                                                  const int* __restrict__ ntiles) {
+    __shared__ SimDev sim_sh;
     const int nt = *ntiles;
     for (int t = blockIdx.x; t < nt; t += gridDim.x) {
         const int2 tile = tiles[t];
-        const SimDev& s = sims[tile.x];
+        __syncthreads();
+        load_sim(sim_sh, sims[tile.x]);
+        __syncthreads();
+        const SimDev& s = sim_sh;
         const uint32_t n = s.dyn->n;
         const int cur = s.dyn->cur;
         PView<T> A = view<T>(s, cur), B = view<T>(s, cur ^ 1);
@@ -168,11 +180,15 @@ __global__ void __launch_bounds__(256) k_scatter(const SimDev* __restrict__ sims
 template <class T>
 __global__ void __launch_bounds__(256) k_inject(const SimDev* __restrict__ sims, const int2* __restrict__ tiles,
                                                 const int* __restrict__ ntiles) {
+    __shared__ SimDev sim_sh;
     const int nt = *ntiles;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     for (int t = blockIdx.x; t < nt; t += gridDim.x) {
         const int2 tile = tiles[t];
-        const SimDev& s = sims[tile.x];
+        __syncthreads();
+        load_sim(sim_sh, sims[tile.x]);
+        __syncthreads();
+        const SimDev& s = sim_sh;
         if (!s.has_reservoir) continue;
         const uint32_t step = s.dyn->step, next_pid = s.dyn->next_pid;
         PView<T> B = view<T>(s, s.dyn->cur ^ 1);
@@ -210,11 +226,15 @@ __global__ void __launch_bounds__(256) k_inject(const SimDev* __restrict__ sims,
 template <class T>
 __global__ void __launch_bounds__(256) k_moments(const SimDev* __restrict__ sims, const int2* __restrict__ tiles,
                                                  const int* __restrict__ ntiles) {
+    __shared__ SimDev sim_sh;
     const int nt = *ntiles;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     for (int t = blockIdx.x; t < nt; t += gridDim.x) {
         const int2 tile = tiles[t];
-        const SimDev& s = sims[tile.x];
+        __syncthreads();
+        load_sim(sim_sh, sims[tile.x]);
+        __syncthreads();
+        const SimDev& s = sim_sh;
         const int K = s.K;
         PView<T> B = view<T>(s, s.dyn->cur ^ 1);
         if (tile.y == 0 && threadIdx.x == 0) s.fill[K] = 0;
@@ -252,10 +272,14 @@ __global__ void __launch_bounds__(256) k_moments(const SimDev* __restrict__ sims
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(128) k_params(const SimDev* __restrict__ sims, const int2* __restrict__ tiles,
                                                 const int* __restrict__ ntiles) {
+    __shared__ SimDev sim_sh;
     const int nt = *ntiles;
     for (int t = blockIdx.x; t < nt; t += gridDim.x) {
         const int2 tile = tiles[t];
-        const SimDev& s = sims[tile.x];
+        __syncthreads();
+        load_sim(sim_sh, sims[tile.x]);
+        __syncthreads();
+        const SimDev& s = sim_sh;
         const int K = s.K;
         for (int cc = threadIdx.x; cc < kCTile; cc += blockDim.x) {
             const int cell = tile.y + cc;
@@ -381,11 +405,15 @@ __global__ void __launch_bounds__(128) k_params(const SimDev* __restrict__ sims,
 template <class T>
 __global__ void __launch_bounds__(256) k_relax(const SimDev* __restrict__ sims, const int2* __restrict__ tiles,
                                                const int* __restrict__ ntiles) {
+    __shared__ SimDev sim_sh;
     const int nt = *ntiles;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     for (int t = blockIdx.x; t < nt; t += gridDim.x) {
         const int2 tile = tiles[t];
-        const SimDev& s = sims[tile.x];
+        __syncthreads();
+        load_sim(sim_sh, sims[tile.x]);
+        __syncthreads();
+        const SimDev& s = sim_sh;
         const int K = s.K;
         const uint32_t step = s.dyn->step;
         PView<T> B = view<T>(s, s.dyn->cur ^ 1);
@@ -489,11 +517,15 @@ template <class T>
 __global__ void __launch_bounds__(256) k_init_fill(const SimDev* __restrict__ sims, const int2* __restrict__ tiles,
                                                    const int* __restrict__ ntiles, const double* __restrict__ reg_theta,
                                                    const double* __restrict__ reg_u, const int* __restrict__ cell_reg) {
+    __shared__ SimDev sim_sh;
     const int nt = *ntiles;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     for (int t = blockIdx.x; t < nt; t += gridDim.x) {
         const int2 tile = tiles[t];
-        const SimDev& s = sims[tile.x];
+        __syncthreads();
+        load_sim(sim_sh, sims[tile.x]);
+        __syncthreads();
+        const SimDev& s = sim_sh;
         PView<T> A = view<T>(s, 0);
         for (int cc = warp; cc < kCTile; cc += nwarps) {
             const int cell = tile.y + cc;
