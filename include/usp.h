@@ -164,8 +164,10 @@ typedef struct {
     int32_t precision, pipeline;
     uint32_t step;        /* completed steps */
     double dt, mu_ref;    /* derived time step and reference viscosity */
-    int64_t counters[8];  /* 0 Cholesky fallbacks, 1 bounce-cap clamps, 2 removed,
-                             3 injected, 4 relaxed (last step), 5-7 reserved */
+    int64_t counters[8];  /* cumulative: 0 Cholesky fallbacks, 1 bounce-cap clamps,
+                             2 removed, 3 injected, 4 relaxed, 5 particles lost to
+                             slot overflow (must stay 0), 6 particles spilled past
+                             a full bucket (fused pipeline), 7 reserved */
     size_t device_bytes;  /* device memory held by the handle */
 } usp_info;
 

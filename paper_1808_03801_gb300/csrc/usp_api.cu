@@ -247,6 +247,7 @@ extern "C" int usp_create(const usp_gas* gas, const usp_grid* grid, const usp_bc
         if (segs[g].kind == USP_BC_DIFFUSE && !(segs[g].T > 0)) return USP_ERR_INVALID_ARG;
     }
 
+    if (prm->pipeline == USP_PIPE_FUSED) fused_prepare_attributes();
     usp_handle* h = new usp_handle();
     h->precision = prm->precision;
     h->pipeline = prm->pipeline;

@@ -114,34 +114,6 @@ __device__ __forceinline__ void store_velocity(const SimDev& s, int b, uint32_t 
     }
 }
 
-// FP32 advection: straight flight when the path stays strictly inside the
-// domain and crosses no plate, otherwise the full time-of-flight treatment.
-template <int DIM>
-__device__ __forceinline__ bool advect_fast(const SimDev& s, uint32_t step, uint32_t pid, float& x, float& y,
-                                            float* c) {
-    const float tau = (float)s.dt;
-    const float yn = y + c[1] * tau;
-    bool inside = yn > (float)s.lo[1] && yn < (float)s.hi[1];
-    float xn = x;
-    if (DIM == 2) {
-        xn = x + c[0] * tau;
-        inside = inside && xn > (float)s.lo[0] && xn < (float)s.hi[0];
-        for (int g = 0; g < s.nseg; ++g) {
-            const float ps = (float)s.seg[g].pos;
-            if ((x - ps) * (xn - ps) <= 0.0f) inside = false;
-        }
-    }
-    if (inside) {
-        y = yn;
-        if (DIM == 2) x = xn;
-        c[0] += (float)s.body[0] * tau;
-        c[1] += (float)s.body[1] * tau;
-        c[2] += (float)s.body[2] * tau;
-        return true;
-    }
-    return advect<float>(s, step, pid, x, y, c);
-}
-
 // append one particle to the bucket of its cell in buffer b (all 32 lanes
 // call this together; key == kNoCell for lanes with nothing to write)
 template <int DIM>
@@ -167,6 +139,7 @@ __device__ __forceinline__ void emit(const SimDev& s, int b, uint32_t key, float
         s.pid[b][i] = id;
     } else {
         const uint32_t k = atomicAdd(&s.dyn->sp_n[b], 1u);
+        atomicAdd(&s.dyn->counters[kCntSpilled], 1ull);
         if (k < (uint32_t)kSpillCap) {
             if (DIM == 2) s.sp_pos[b][0][k] = x;
             s.sp_pos[b][1][k] = y;
@@ -205,9 +178,71 @@ __device__ __forceinline__ void es_draw_f(const SimDev& s, const FCell& f, const
 
 // ---------------------------------------------------------------------------
 // k_g2: pending relaxation + advection + bucket scatter (FLUSH: relaxation only)
+//
+// One warp per cell.  The cell's particles are staged in a per-warp shared
+// memory area of CAP entries and every pass walks them with a rolled loop, so
+// that the per-particle code (two Philox draws, the ES sample, advection)
+// appears once in the binary.  Cells above CAP particles are processed in
+// chunks: the conservation sums in a first sweep, the update in a second
+// sweep that redraws the same counter-based random numbers.
 // ---------------------------------------------------------------------------
-template <int R, int DIM, bool FLUSH>
-__device__ void g2_cell(const SimDev& s, int cell, int p, uint32_t step, bool pending, uint32_t* spl, int lane) {
+__device__ __noinline__ bool advect_slow(const SimDev& s, uint32_t step, uint32_t pid, float& x, float& y, float* c) {
+    return advect<float>(s, step, pid, x, y, c);
+}
+
+template <int DIM>
+__device__ __forceinline__ bool advect_fast(const SimDev& s, float tau, uint32_t step, uint32_t pid, float& x,
+                                            float& y, float* c) {
+    const float yn = y + c[1] * tau;
+    bool inside = yn > (float)s.lo[1] && yn < (float)s.hi[1];
+    float xn = x;
+    if (DIM == 2) {
+        xn = x + c[0] * tau;
+        inside = inside && xn > (float)s.lo[0] && xn < (float)s.hi[0];
+        for (int g = 0; g < s.nseg; ++g) {
+            const float ps = (float)s.seg[g].pos;
+            if ((x - ps) * (xn - ps) <= 0.0f) inside = false;
+        }
+    }
+    if (inside) {
+        y = yn;
+        if (DIM == 2) x = xn;
+        c[0] += (float)s.body[0] * tau;
+        c[1] += (float)s.body[1] * tau;
+        c[2] += (float)s.body[2] * tau;
+        return true;
+    }
+    return advect_slow(s, step, pid, x, y, c);
+}
+
+// per-warp staging area
+struct Stage {
+    float* x;
+    float* y;
+    float* v0;
+    float* v1;
+    float* v2;
+    uint32_t* id;
+    unsigned char* sel;
+};
+
+template <int CAP>
+__device__ __forceinline__ Stage stage_of(unsigned char* base, int warp) {
+    unsigned char* w = base + (size_t)warp * CAP * 25;
+    Stage S;
+    S.x = (float*)w;
+    S.y = S.x + CAP;
+    S.v0 = S.y + CAP;
+    S.v1 = S.v0 + CAP;
+    S.v2 = S.v1 + CAP;
+    S.id = (uint32_t*)(S.v2 + CAP);
+    S.sel = (unsigned char*)(S.id + CAP);
+    return S;
+}
+
+template <int CAP, int DIM, bool FLUSH>
+__device__ void g2_cell(const SimDev& s, int cell, int p, uint32_t step, bool pending, uint32_t* spl, const Stage& S,
+                        int lane) {
     const uint32_t base = s.lay[p][cell];
     const uint32_t top = min(s.lay[p][cell + 1], (uint32_t)s.cap);
     const uint32_t capc = top > base ? top - base : 0u;
@@ -228,42 +263,55 @@ __device__ void g2_cell(const SimDev& s, int cell, int p, uint32_t step, bool pe
     td.ema = __expf(-td.a);
     td.inv_nues = 1.0f / f.nues;
     const int q = p ^ 1;
-    const uint32_t CH = 32u * R;
-    const uint32_t nch = (n + CH - 1) / CH;
+    const uint32_t nch = (n + CAP - 1) / CAP;
 
-    // a relaxed particle's new peculiar velocity replaces its old velocity in
-    // v0..v2 once the old one has entered the conservation sums (bit r of sel)
-    float x[R], y[R], v0[R], v1[R], v2[R];
-    uint32_t id[R];
-    unsigned sel = 0;
-    // relaxed-subset sums relative to the cell mean: so, eo (old), sn, en (new)
+    // stage chunk ch; if `draw_new`, relaxed particles get their new peculiar
+    // velocity in v0..v2 (flag in sel); if `sums`, accumulate the conservation sums
     float a0 = 0, a1 = 0, a2 = 0, ae = 0, b0 = 0, b1 = 0, b2 = 0, be = 0, nr = 0;
-    for (uint32_t ch = 0; ch < nch; ++ch) {
-        sel = 0;
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const uint32_t j = ch * CH + r * 32 + lane;
-            x[r] = 0.0f;
-            if (j < n) load_particle<DIM>(s, p, base, nb, spl, j, x[r], y[r], v0[r], v1[r], v2[r], id[r]);
-            if (relax && j < n) {
-                const uint4 w = draw(s, id[r], step, kRelax, 0);
+    auto stage_chunk = [&](uint32_t ch, bool sums) -> uint32_t {
+        const uint32_t off = ch * CAP;
+        const uint32_t m = min((uint32_t)CAP, n - off);
+        __syncwarp();
+#pragma unroll 1
+        for (uint32_t j = lane; j < m; j += 32) {
+            float x = 0.0f, y, v0, v1, v2;
+            uint32_t id;
+            load_particle<DIM>(s, p, base, nb, spl, off + j, x, y, v0, v1, v2, id);
+            unsigned char sl = 0;
+            if (relax) {
+                const uint4 w = draw(s, id, step, kRelax, 0);
                 if (u01<float>(w.x) < f.pr) {
-                    sel |= 1u << r;
+                    sl = 1;
                     float C[3];
-                    es_draw_f(s, f, td, id[r], step, w, C);
-                    const float o0 = v0[r] - f.u[0], o1 = v1[r] - f.u[1], o2 = v2[r] - f.u[2];
-                    a0 += o0; a1 += o1; a2 += o2;
-                    ae += o0 * o0 + o1 * o1 + o2 * o2;
-                    b0 += C[0]; b1 += C[1]; b2 += C[2];
-                    be += C[0] * C[0] + C[1] * C[1] + C[2] * C[2];
-                    nr += 1.0f;
-                    v0[r] = C[0];
-                    v1[r] = C[1];
-                    v2[r] = C[2];
+                    es_draw_f(s, f, td, id, step, w, C);
+                    if (sums) {
+                        const float o0 = v0 - f.u[0], o1 = v1 - f.u[1], o2 = v2 - f.u[2];
+                        a0 += o0; a1 += o1; a2 += o2;
+                        ae += o0 * o0 + o1 * o1 + o2 * o2;
+                        b0 += C[0]; b1 += C[1]; b2 += C[2];
+                        be += C[0] * C[0] + C[1] * C[1] + C[2] * C[2];
+                        nr += 1.0f;
+                    }
+                    v0 = C[0];
+                    v1 = C[1];
+                    v2 = C[2];
                 }
             }
+            if (DIM == 2) S.x[j] = x;
+            S.y[j] = y;
+            S.v0[j] = v0;
+            S.v1[j] = v1;
+            S.v2[j] = v2;
+            S.id[j] = id;
+            S.sel[j] = sl;
         }
-    }
+        __syncwarp();
+        return m;
+    };
+
+    uint32_t m_last = 0;
+    for (uint32_t ch = 0; ch < nch; ++ch) m_last = stage_chunk(ch, true);
+
     // conservation factors of the cell (FP64 once per cell)
     bool apply = false;
     float uo0 = 0, uo1 = 0, uo2 = 0, mn0 = 0, mn1 = 0, mn2 = 0, alpha = 1;
@@ -288,69 +336,60 @@ __device__ void g2_cell(const SimDev& s, int cell, int p, uint32_t step, bool pe
         }
         if (lane == 0 && apply) atomicAdd(&s.dyn->counters[kCntRelaxed], (unsigned long long)nr);
     }
+
+    const float tau = (float)s.dt;
     for (uint32_t ch = 0; ch < nch; ++ch) {
-        if (nch > 1) {
-            sel = 0;
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const uint32_t j = ch * CH + r * 32 + lane;
-                x[r] = 0.0f;
-                if (j < n) load_particle<DIM>(s, p, base, nb, spl, j, x[r], y[r], v0[r], v1[r], v2[r], id[r]);
-                if (relax && j < n) {
-                    const uint4 w = draw(s, id[r], step, kRelax, 0);
-                    if (u01<float>(w.x) < f.pr) {
-                        sel |= 1u << r;
-                        float C[3];
-                        es_draw_f(s, f, td, id[r], step, w, C);
-                        v0[r] = C[0];
-                        v1[r] = C[1];
-                        v2[r] = C[2];
+        const uint32_t m = nch > 1 ? stage_chunk(ch, false) : m_last;
+        const uint32_t off = ch * CAP;
+#pragma unroll 1
+        for (uint32_t b = 0; b < m; b += 32) {
+            const uint32_t j = b + lane;
+            const bool valid = j < m;
+            float x = 0.0f, y = 0.0f, c[3] = {0.0f, 0.0f, 0.0f};
+            uint32_t id = 0;
+            if (valid) {
+                if (DIM == 2) x = S.x[j];
+                y = S.y[j];
+                c[0] = S.v0[j];
+                c[1] = S.v1[j];
+                c[2] = S.v2[j];
+                id = S.id[j];
+                if (S.sel[j]) {
+                    if (apply) {
+                        c[0] = uo0 + alpha * (c[0] - mn0);
+                        c[1] = uo1 + alpha * (c[1] - mn1);
+                        c[2] = uo2 + alpha * (c[2] - mn2);
+                    } else {   // a lone relaxed particle keeps its old velocity
+                        float ox, oy;
+                        uint32_t oid;
+                        load_particle<DIM>(s, p, base, nb, spl, off + j, ox, oy, c[0], c[1], c[2], oid);
                     }
                 }
             }
-        }
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const uint32_t j = ch * CH + r * 32 + lane;
-            if ((sel >> r) & 1u) {
-                if (apply) {
-                    v0[r] = uo0 + alpha * (v0[r] - mn0);
-                    v1[r] = uo1 + alpha * (v1[r] - mn1);
-                    v2[r] = uo2 + alpha * (v2[r] - mn2);
-                } else {   // a lone relaxed particle keeps its old velocity
-                    float ox, oy, ov0, ov1, ov2;
-                    uint32_t oid;
-                    load_particle<DIM>(s, p, base, nb, spl, j, ox, oy, ov0, ov1, ov2, oid);
-                    v0[r] = ov0;
-                    v1[r] = ov1;
-                    v2[r] = ov2;
-                }
-            }
             if (FLUSH) {
-                if (j < n && apply && ((sel >> r) & 1u))
-                    store_velocity<DIM>(s, p, base, nb, spl, j, v0[r], v1[r], v2[r]);
+                if (valid && S.sel[j] && apply) store_velocity<DIM>(s, p, base, nb, spl, off + j, c[0], c[1], c[2]);
                 continue;
             }
             uint32_t key = kNoCell;
-            float cv[3] = {v0[r], v1[r], v2[r]};
-            if (j < n) {
-                if (advect_fast<DIM>(s, step, id[r], x[r], y[r], cv)) {
-                    const int dc = cell_index<float>(s, x[r], y[r]);
-                    if (!in_buffer(s, dc)) key = (uint32_t)dc;
-                    else atomicAdd(&s.dyn->counters[kCntRemoved], 1ull);
-                }
+            if (valid && advect_fast<DIM>(s, tau, step, id, x, y, c)) {
+                const int dc = cell_index<float>(s, x, y);
+                if (!in_buffer(s, dc)) key = (uint32_t)dc;
+                else atomicAdd(&s.dyn->counters[kCntRemoved], 1ull);
             }
-            emit<DIM>(s, q, key, x[r], y[r], cv[0], cv[1], cv[2], id[r], lane);
+            emit<DIM>(s, q, key, x, y, c[0], c[1], c[2], id, lane);
         }
     }
+    __syncwarp();
 }
 
-template <int R, int DIM, bool FLUSH>
-__global__ void __launch_bounds__(256, 1) k_g2(const SimDev* __restrict__ sims, const int2* __restrict__ tiles,
+template <int CAP, int DIM, bool FLUSH>
+__global__ void __launch_bounds__(128, 4) k_g2(const SimDev* __restrict__ sims, const int2* __restrict__ tiles,
                                             const int* __restrict__ ntiles) {
-    __shared__ uint32_t spl_all[8][32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    extern __shared__ __align__(16) unsigned char g2_smem[];
     __shared__ SimDev sim_sh;
+    __shared__ uint32_t spl_all[4][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const Stage S = stage_of<CAP>(g2_smem, warp);
     const int nt = *ntiles;
     for (int t = blockIdx.x; t < nt; t += gridDim.x) {
         const int2 tile = tiles[t];
@@ -363,10 +402,10 @@ __global__ void __launch_bounds__(256, 1) k_g2(const SimDev* __restrict__ sims, 
         const uint32_t step = s.dyn->step;
         const bool pending = s.dyn->relax_pending != 0;
         if (FLUSH && !pending) continue;
-        for (int cc = warp; cc < kCTile; cc += 8) {
+        for (int cc = warp; cc < kCTile; cc += 4) {
             const int cell = tile.y + cc;
             if (cell >= s.K) break;
-            g2_cell<R, DIM, FLUSH>(s, cell, p, step, pending, spl_all[warp], lane);
+            g2_cell<CAP, DIM, FLUSH>(s, cell, p, step, pending, spl_all[warp], S, lane);
         }
     }
 }
@@ -816,27 +855,59 @@ __global__ void k_finish_f(const SimDev* __restrict__ sims, int nsims, int mode)
     }
 }
 
-template <int R, bool FLUSH>
+template <int CAP, int DIM, bool FLUSH>
+void launch_g2_one(const Launch& L) {
+    const int smem = 4 * CAP * 25;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_g2<CAP, DIM, FLUSH>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        attr = true;
+    }
+    k_g2<CAP, DIM, FLUSH><<<L.grid_c, 128, smem, L.stream>>>(L.sims, L.ctiles, L.nctiles);
+}
+
+template <int CAP, bool FLUSH>
 void launch_g2(const Launch& L) {
-    if (L.dims & 1) k_g2<R, 1, FLUSH><<<L.grid_c, 256, 0, L.stream>>>(L.sims, L.ctiles, L.nctiles);
-    if (L.dims & 2) k_g2<R, 2, FLUSH><<<L.grid_c, 256, 0, L.stream>>>(L.sims, L.ctiles, L.nctiles);
+    if (L.dims & 1) launch_g2_one<CAP, 1, FLUSH>(L);
+    if (L.dims & 2) launch_g2_one<CAP, 2, FLUSH>(L);
 }
 
 }  // namespace
 
 void launch_fused_setup(const Launch& L) { k_layout<true><<<L.nsims, 1024, 0, L.stream>>>(L.sims, L.nsims); }
 
+// R: particles per lane of the largest expected cell (staging area of 32 R)
 void launch_fused_relax_stream(const Launch& L, int R, bool flush_only) {
     if (flush_only) {
-        if (R <= 4) launch_g2<4, true>(L);
-        else if (R <= 8) launch_g2<8, true>(L);
-        else launch_g2<12, true>(L);
+        if (R <= 4) launch_g2<128, true>(L);
+        else if (R <= 8) launch_g2<256, true>(L);
+        else launch_g2<512, true>(L);
         k_finish_f<<<(L.nsims + 127) / 128, 128, 0, L.stream>>>(L.sims, L.nsims, 1);
         return;
     }
-    if (R <= 4) launch_g2<4, false>(L);
-    else if (R <= 8) launch_g2<8, false>(L);
-    else launch_g2<12, false>(L);
+    if (R <= 4) launch_g2<128, false>(L);
+    else if (R <= 8) launch_g2<256, false>(L);
+    else launch_g2<512, false>(L);
+}
+
+// set the shared-memory limits of the staged kernels once, outside any capture
+void fused_prepare_attributes() {
+    static bool done = false;
+    if (done) return;
+    done = true;
+    cudaFuncSetAttribute(k_g2<128, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 128 * 25);
+    cudaFuncSetAttribute(k_g2<128, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 128 * 25);
+    cudaFuncSetAttribute(k_g2<256, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 256 * 25);
+    cudaFuncSetAttribute(k_g2<256, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 256 * 25);
+    cudaFuncSetAttribute(k_g2<512, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 512 * 25);
+    cudaFuncSetAttribute(k_g2<512, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 512 * 25);
+    cudaFuncSetAttribute(k_g2<128, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 128 * 25);
+    cudaFuncSetAttribute(k_g2<128, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 128 * 25);
+    cudaFuncSetAttribute(k_g2<256, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 256 * 25);
+    cudaFuncSetAttribute(k_g2<256, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 256 * 25);
+    cudaFuncSetAttribute(k_g2<512, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 512 * 25);
+    cudaFuncSetAttribute(k_g2<512, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 512 * 25);
+    cudaGetLastError();
 }
 
 void launch_fused_inject(const Launch& L) {

@@ -22,7 +22,8 @@ enum { kBcDiffuse = 0, kBcSpecular = 1, kBcPeriodic = 2, kBcReservoir = 3 };
 enum { kModeUSP = 0, kModeSP = 1, kModeFixed = 2 };
 
 // counters (u64, device)
-enum { kCntChol = 0, kCntClamp = 1, kCntRemoved = 2, kCntInjected = 3, kCntRelaxed = 4, kCntOverflow = 5 };
+enum { kCntChol = 0, kCntClamp = 1, kCntRemoved = 2, kCntInjected = 3, kCntRelaxed = 4, kCntOverflow = 5,
+       kCntSpilled = 6 };
 
 struct FaceDev {
     int kind;
@@ -201,6 +202,7 @@ void launch_fused_moments(const Launch& L, int R);
 void launch_fused_params(const Launch& L);
 void launch_fused_layout(const Launch& L);
 void launch_fused_finish(const Launch& L);
+void fused_prepare_attributes();
 cudaError_t debug_philox(int64_t n, const uint32_t* d_ctr, uint32_t k0, uint32_t k1, uint32_t* d_out, cudaStream_t st);
 
 }  // namespace usp
