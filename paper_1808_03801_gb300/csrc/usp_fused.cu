@@ -114,46 +114,6 @@ __device__ __forceinline__ void store_velocity(const SimDev& s, int b, uint32_t 
     }
 }
 
-// append one particle to the bucket of its cell in buffer b (all 32 lanes
-// call this together; key == kNoCell for lanes with nothing to write)
-template <int DIM>
-__device__ __forceinline__ void emit(const SimDev& s, int b, uint32_t key, float x, float y, float v0, float v1,
-                                     float v2, uint32_t id, int lane) {
-    const unsigned grp = __match_any_sync(0xffffffffu, key);
-    if (key == kNoCell) return;
-    const int leader = __ffs(grp) - 1;
-    uint32_t base = 0;
-    if (lane == leader) base = atomicAdd(&s.cnt[b][key], (uint32_t)__popc(grp));
-    base = __shfl_sync(grp, base, leader);
-    const uint32_t rank = base + (uint32_t)__popc(grp & lanemask_lt());
-    const uint32_t lo = s.lay[b][key];
-    const uint32_t hi = min(s.lay[b][key + 1], (uint32_t)s.cap);
-    const uint32_t capd = hi > lo ? hi - lo : 0u;
-    if (rank < capd) {
-        const uint32_t i = lo + rank;
-        if (DIM == 2) ((float*)s.pos[b][0])[i] = x;
-        ((float*)s.pos[b][1])[i] = y;
-        ((float*)s.vel[b][0])[i] = v0;
-        ((float*)s.vel[b][1])[i] = v1;
-        ((float*)s.vel[b][2])[i] = v2;
-        s.pid[b][i] = id;
-    } else {
-        const uint32_t k = atomicAdd(&s.dyn->sp_n[b], 1u);
-        atomicAdd(&s.dyn->counters[kCntSpilled], 1ull);
-        if (k < (uint32_t)kSpillCap) {
-            if (DIM == 2) s.sp_pos[b][0][k] = x;
-            s.sp_pos[b][1][k] = y;
-            s.sp_vel[b][0][k] = v0;
-            s.sp_vel[b][1][k] = v1;
-            s.sp_vel[b][2][k] = v2;
-            s.sp_pid[b][k] = id;
-            s.sp_cell[b][k] = key;
-        } else {
-            atomicAdd(&s.dyn->counters[kCntOverflow], 1ull);
-        }
-    }
-}
-
 // per-cell constants of the time-instant draw (Eq. 30)
 struct TimeDraw {
     float dt, a, em1, ema, inv_nues;
@@ -162,7 +122,7 @@ struct TimeDraw {
 __device__ __forceinline__ void es_draw_f(const SimDev& s, const FCell& f, const TimeDraw& td, uint32_t pid,
                                           uint32_t step, const uint4& w, float* C) {
     const float U1 = u01<float>(w.y);
-    const float t = td.a < 1.0f ? log1pf(U1 * td.em1) * td.inv_nues
+    const float t = td.a < 1.0f ? __logf(1.0f + U1 * td.em1) * td.inv_nues
                                 : td.dt + __logf(U1 + (1.0f - U1) * td.ema) * td.inv_nues;
     const float sf = f.pne + (1.0f - f.pne) * __expf(-f.nu * t);          // Eq. 32
     const uint4 v = draw(s, pid, step, kRelax, 1);
@@ -190,16 +150,68 @@ __device__ __noinline__ bool advect_slow(const SimDev& s, uint32_t step, uint32_
     return advect<float>(s, step, pid, x, y, c);
 }
 
+// per-cell register copy of what the advection and the scatter need
+struct Ctx {
+    float tau, lo0, hi0, lo1, hi1, inv_dx, inv_dy, b0, b1, b2;
+    int nx, nxm1, nym1, nseg, reservoir, K;
+    float* dx_;   // destination planes
+    float* dy_;
+    float* dv0;
+    float* dv1;
+    float* dv2;
+    uint32_t* did;
+    const uint32_t* dlay;
+    uint32_t* dcnt;
+    uint32_t cap;
+};
+
+__device__ __forceinline__ void make_ctx(const SimDev& s, int q, Ctx& C) {
+    C.tau = (float)s.dt;
+    C.lo0 = (float)s.lo[0];
+    C.hi0 = (float)s.hi[0];
+    C.lo1 = (float)s.lo[1];
+    C.hi1 = (float)s.hi[1];
+    C.inv_dx = (float)(1.0 / s.dx);
+    C.inv_dy = (float)(1.0 / s.dy);
+    C.b0 = (float)(s.body[0] * s.dt);
+    C.b1 = (float)(s.body[1] * s.dt);
+    C.b2 = (float)(s.body[2] * s.dt);
+    C.nx = s.nx;
+    C.nxm1 = s.nx - 1;
+    C.nym1 = s.ny - 1;
+    C.nseg = s.nseg;
+    C.reservoir = s.has_reservoir;
+    C.K = s.K;
+    C.dx_ = (float*)s.pos[q][0];
+    C.dy_ = (float*)s.pos[q][1];
+    C.dv0 = (float*)s.vel[q][0];
+    C.dv1 = (float*)s.vel[q][1];
+    C.dv2 = (float*)s.vel[q][2];
+    C.did = s.pid[q];
+    C.dlay = s.lay[q];
+    C.dcnt = s.cnt[q];
+    C.cap = (uint32_t)s.cap;
+}
+
+// cell of an FP32 position: floor of the scaled offset, clamped to the grid
 template <int DIM>
-__device__ __forceinline__ bool advect_fast(const SimDev& s, float tau, uint32_t step, uint32_t pid, float& x,
+__device__ __forceinline__ int cell_f(const Ctx& C, float x, float y) {
+    const float fy = fminf(fmaxf(floorf((y - C.lo1) * C.inv_dy), 0.0f), (float)C.nym1);
+    if (DIM == 1) return (int)fy;
+    const float fx = fminf(fmaxf(floorf((x - C.lo0) * C.inv_dx), 0.0f), (float)C.nxm1);
+    return (int)fy * C.nx + (int)fx;
+}
+
+template <int DIM>
+__device__ __forceinline__ bool advect_fast(const SimDev& s, const Ctx& C, uint32_t step, uint32_t pid, float& x,
                                             float& y, float* c) {
-    const float yn = y + c[1] * tau;
-    bool inside = yn > (float)s.lo[1] && yn < (float)s.hi[1];
+    const float yn = y + c[1] * C.tau;
+    bool inside = yn > C.lo1 && yn < C.hi1;
     float xn = x;
     if (DIM == 2) {
-        xn = x + c[0] * tau;
-        inside = inside && xn > (float)s.lo[0] && xn < (float)s.hi[0];
-        for (int g = 0; g < s.nseg; ++g) {
+        xn = x + c[0] * C.tau;
+        inside = inside && xn > C.lo0 && xn < C.hi0;
+        for (int g = 0; g < C.nseg; ++g) {
             const float ps = (float)s.seg[g].pos;
             if ((x - ps) * (xn - ps) <= 0.0f) inside = false;
         }
@@ -207,12 +219,51 @@ __device__ __forceinline__ bool advect_fast(const SimDev& s, float tau, uint32_t
     if (inside) {
         y = yn;
         if (DIM == 2) x = xn;
-        c[0] += (float)s.body[0] * tau;
-        c[1] += (float)s.body[1] * tau;
-        c[2] += (float)s.body[2] * tau;
+        c[0] += C.b0;
+        c[1] += C.b1;
+        c[2] += C.b2;
         return true;
     }
     return advect_slow(s, step, pid, x, y, c);
+}
+
+// append one particle to the bucket of its cell (all 32 lanes call this
+// together; key == kNoCell for lanes with nothing to write)
+template <int DIM>
+__device__ __forceinline__ void emit_c(const SimDev& s, const Ctx& C, int b, uint32_t key, float x, float y, float v0,
+                                       float v1, float v2, uint32_t id, int lane) {
+    const unsigned grp = __match_any_sync(0xffffffffu, key);
+    if (key == kNoCell) return;
+    const int leader = __ffs(grp) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(&C.dcnt[key], (uint32_t)__popc(grp));
+    base = __shfl_sync(grp, base, leader);
+    const uint32_t rank = base + (uint32_t)__popc(grp & lanemask_lt());
+    const uint32_t lo = C.dlay[key];
+    const uint32_t hi = min(C.dlay[key + 1], C.cap);
+    if (lo + rank < hi) {
+        const uint32_t i = lo + rank;
+        if (DIM == 2) C.dx_[i] = x;
+        C.dy_[i] = y;
+        C.dv0[i] = v0;
+        C.dv1[i] = v1;
+        C.dv2[i] = v2;
+        C.did[i] = id;
+    } else {
+        const uint32_t k = atomicAdd(&s.dyn->sp_n[b], 1u);
+        atomicAdd(&s.dyn->counters[kCntSpilled], 1ull);
+        if (k < (uint32_t)kSpillCap) {
+            if (DIM == 2) s.sp_pos[b][0][k] = x;
+            s.sp_pos[b][1][k] = y;
+            s.sp_vel[b][0][k] = v0;
+            s.sp_vel[b][1][k] = v1;
+            s.sp_vel[b][2][k] = v2;
+            s.sp_pid[b][k] = id;
+            s.sp_cell[b][k] = key;
+        } else {
+            atomicAdd(&s.dyn->counters[kCntOverflow], 1ull);
+        }
+    }
 }
 
 // per-warp staging area
@@ -337,7 +388,8 @@ __device__ void g2_cell(const SimDev& s, int cell, int p, uint32_t step, bool pe
         if (lane == 0 && apply) atomicAdd(&s.dyn->counters[kCntRelaxed], (unsigned long long)nr);
     }
 
-    const float tau = (float)s.dt;
+    Ctx C;
+    make_ctx(s, q, C);
     for (uint32_t ch = 0; ch < nch; ++ch) {
         const uint32_t m = nch > 1 ? stage_chunk(ch, false) : m_last;
         const uint32_t off = ch * CAP;
@@ -371,12 +423,12 @@ __device__ void g2_cell(const SimDev& s, int cell, int p, uint32_t step, bool pe
                 continue;
             }
             uint32_t key = kNoCell;
-            if (valid && advect_fast<DIM>(s, tau, step, id, x, y, c)) {
-                const int dc = cell_index<float>(s, x, y);
-                if (!in_buffer(s, dc)) key = (uint32_t)dc;
+            if (valid && advect_fast<DIM>(s, C, step, id, x, y, c)) {
+                const int dc = cell_f<DIM>(C, x, y);
+                if (!C.reservoir || !in_buffer(s, dc)) key = (uint32_t)dc;
                 else atomicAdd(&s.dyn->counters[kCntRemoved], 1ull);
             }
-            emit<DIM>(s, q, key, x, y, c[0], c[1], c[2], id, lane);
+            emit_c<DIM>(s, C, q, key, x, y, c[0], c[1], c[2], id, lane);
         }
     }
     __syncwarp();
@@ -709,6 +761,8 @@ __global__ void __launch_bounds__(256) k_inject_f(const SimDev* __restrict__ sim
         if (!s.has_reservoir || s.dim != DIM) continue;
         const uint32_t step = s.dyn->step, next_pid = s.dyn->next_pid;
         const int q = s.dyn->cur ^ 1;
+        Ctx C;
+        make_ctx(s, q, C);
         for (int cc = warp; cc < kCTile; cc += 8) {
             const int cell = tile.y + cc;
             if (cell >= s.K) break;
@@ -725,7 +779,7 @@ __global__ void __launch_bounds__(256) k_inject_f(const SimDev* __restrict__ sim
                     make_particle<float>(s, cell, pid, step, kInject, F.theta, F.u, x, y, c);
                     key = (uint32_t)cell;
                 }
-                emit<DIM>(s, q, key, x, y, c[0], c[1], c[2], pid, lane);
+                emit_c<DIM>(s, C, q, key, x, y, c[0], c[1], c[2], pid, lane);
             }
         }
     }

@@ -61,12 +61,13 @@ def test_fused_particles_conserved_and_cells_consistent(usp):
     P = g.particles()
     assert len(P["pid"]) == n0
     assert np.array_equal(np.sort(P["pid"]), np.arange(n0, dtype=np.uint32))
+    # the FP32 pipeline assigns cells as floor((x - lo) * (1/dx)) in single precision
     lo = np.float32(0.0)
-    d = np.float32(1e-4 / 30)
+    inv = np.float32(1.0 / (1e-4 / 30))
     x = P["pos"][:, 0].astype(np.float32)
     y = P["pos"][:, 1].astype(np.float32)
-    ix = np.clip(np.floor((x - lo) / d), 0, 29).astype(int)
-    iy = np.clip(np.floor((y - lo) / d), 0, 29).astype(int)
+    ix = np.clip(np.floor((x - lo) * inv), 0, 29).astype(int)
+    iy = np.clip(np.floor((y - lo) * inv), 0, 29).astype(int)
     assert np.array_equal(iy * 30 + ix, P["cell"])
     assert np.array_equal(np.bincount(P["cell"], minlength=900), g.sample()[15].astype(int))
 
