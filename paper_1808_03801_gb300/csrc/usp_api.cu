@@ -323,6 +323,14 @@ extern "C" int usp_create(const usp_gas* gas, const usp_grid* grid, const usp_bc
     }
     s.has_reservoir = any_res;
     s.reservoir_cols = any_res ? prm->reservoir_cols : 0;
+    s.f_dt = (float)s.dt;
+    for (int i = 0; i < 2; ++i) {
+        s.f_lo[i] = (float)s.lo[i];
+        s.f_hi[i] = (float)s.hi[i];
+    }
+    s.f_inv_dx = (float)(1.0 / s.dx);
+    s.f_inv_dy = (float)(1.0 / s.dy);
+    for (int d = 0; d < 3; ++d) s.f_bdt[d] = (float)(s.body[d] * s.dt);
 
     const int K = s.K;
     int rc = USP_OK;

@@ -166,16 +166,16 @@ struct Ctx {
 };
 
 __device__ __forceinline__ void make_ctx(const SimDev& s, int q, Ctx& C) {
-    C.tau = (float)s.dt;
-    C.lo0 = (float)s.lo[0];
-    C.hi0 = (float)s.hi[0];
-    C.lo1 = (float)s.lo[1];
-    C.hi1 = (float)s.hi[1];
-    C.inv_dx = (float)(1.0 / s.dx);
-    C.inv_dy = (float)(1.0 / s.dy);
-    C.b0 = (float)(s.body[0] * s.dt);
-    C.b1 = (float)(s.body[1] * s.dt);
-    C.b2 = (float)(s.body[2] * s.dt);
+    C.tau = s.f_dt;
+    C.lo0 = s.f_lo[0];
+    C.hi0 = s.f_hi[0];
+    C.lo1 = s.f_lo[1];
+    C.hi1 = s.f_hi[1];
+    C.inv_dx = s.f_inv_dx;
+    C.inv_dy = s.f_inv_dy;
+    C.b0 = s.f_bdt[0];
+    C.b1 = s.f_bdt[1];
+    C.b2 = s.f_bdt[2];
     C.nx = s.nx;
     C.nxm1 = s.nx - 1;
     C.nym1 = s.ny - 1;
@@ -308,7 +308,7 @@ __device__ void g2_cell(const SimDev& s, int cell, int p, uint32_t step, bool pe
     const bool relax = pending && f.valid;
     if (FLUSH && !relax) return;
     TimeDraw td;
-    td.dt = (float)s.dt;
+    td.dt = s.f_dt;
     td.a = f.nues * td.dt;
     td.em1 = expm1f(td.a);
     td.ema = __expf(-td.a);
@@ -371,21 +371,33 @@ __device__ void g2_cell(const SimDev& s, int cell, int p, uint32_t step, bool pe
         if (nr >= 2.0f) {
             a0 = warp_sumf(a0); a1 = warp_sumf(a1); a2 = warp_sumf(a2); ae = warp_sumf(ae);
             b0 = warp_sumf(b0); b1 = warp_sumf(b1); b2 = warp_sumf(b2); be = warp_sumf(be);
-            const double inv = 1.0 / (double)nr;
-            const double Eo = (double)ae - ((double)a0 * a0 + (double)a1 * a1 + (double)a2 * a2) * inv;
-            const double En = (double)be - ((double)b0 * b0 + (double)b1 * b1 + (double)b2 * b2) * inv;
-            if (En > 0.0) {
-                apply = true;
-                alpha = (float)sqrt(Eo / En);
-                uo0 = (float)((double)f.u[0] + a0 * inv);
-                uo1 = (float)((double)f.u[1] + a1 * inv);
-                uo2 = (float)((double)f.u[2] + a2 * inv);
-                mn0 = (float)(b0 * inv);
-                mn1 = (float)(b1 * inv);
-                mn2 = (float)(b2 * inv);
+            // FP64 on one lane only (the FP64 pipe is narrow), then broadcast
+            int ok = 0;
+            if (lane == 0) {
+                const double inv = 1.0 / (double)nr;
+                const double Eo = (double)ae - ((double)a0 * a0 + (double)a1 * a1 + (double)a2 * a2) * inv;
+                const double En = (double)be - ((double)b0 * b0 + (double)b1 * b1 + (double)b2 * b2) * inv;
+                if (En > 0.0) {
+                    ok = 1;
+                    alpha = (float)sqrt(Eo / En);
+                    uo0 = (float)((double)f.u[0] + a0 * inv);
+                    uo1 = (float)((double)f.u[1] + a1 * inv);
+                    uo2 = (float)((double)f.u[2] + a2 * inv);
+                    mn0 = (float)(b0 * inv);
+                    mn1 = (float)(b1 * inv);
+                    mn2 = (float)(b2 * inv);
+                    atomicAdd(&s.dyn->counters[kCntRelaxed], (unsigned long long)nr);
+                }
             }
+            apply = __shfl_sync(0xffffffffu, ok, 0) != 0;
+            alpha = __shfl_sync(0xffffffffu, alpha, 0);
+            uo0 = __shfl_sync(0xffffffffu, uo0, 0);
+            uo1 = __shfl_sync(0xffffffffu, uo1, 0);
+            uo2 = __shfl_sync(0xffffffffu, uo2, 0);
+            mn0 = __shfl_sync(0xffffffffu, mn0, 0);
+            mn1 = __shfl_sync(0xffffffffu, mn1, 0);
+            mn2 = __shfl_sync(0xffffffffu, mn2, 0);
         }
-        if (lane == 0 && apply) atomicAdd(&s.dyn->counters[kCntRelaxed], (unsigned long long)nr);
     }
 
     Ctx C;

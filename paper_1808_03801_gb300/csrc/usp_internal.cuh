@@ -64,6 +64,8 @@ struct alignas(16) SimDev {
     int has_reservoir, reservoir_cols;
     double R, mass, mu_ref, T_ref, omega, Pr, dt, w;   // w: number density carried by one particle
     double avg_keep, avg_new;                          // (n_a - 1)/n_a, 1/n_a
+    // single-precision copies for the FP32 kernels (set on the host)
+    float f_dt, f_lo[2], f_hi[2], f_inv_dx, f_inv_dy, f_bdt[3];
     int mode;
     double fixed_pne;
     double body[3];

@@ -180,7 +180,9 @@ def test_fused_slit_particle_balance(usp):
 
 def test_fused_batch_equals_alone_statistically(usp):
     """The same simulation alone and inside a batch of uneven neighbours gives
-    the same time-averaged fields within their standard errors."""
+    the same time-averaged bulk shear stress, velocity and temperature within
+    their standard errors (the FP32 path is not bit-reproducible: bucket order
+    follows atomic arrival order)."""
     base = _fused(W.couette(ny=16, ppc=150, Kn=0.1))
     alone = usp.Simulation(base).init_particles()
     mixed = usp.Simulation(base).init_particles()
@@ -189,10 +191,14 @@ def test_fused_batch_equals_alone_statistically(usp):
     B = usp.Batch(hbm_budget=8 << 30)
     for s in [mixed] + others:
         assert B.admit(s) == 0
-    sel = [1, 4, 8]
-    ga, gs = _blocks(alone.step, lambda: alone.sample()[sel], 100, 10, 30)
-    ma, ms = _blocks(B.step, lambda: mixed.sample()[sel], 100, 10, 30)
+
+    def bulk(F):
+        # gap-averaged |u_x| antisymmetric part, temperature and shear stress
+        return np.array([(F[1, 8:] - F[1, :8][::-1]).mean(), F[4].mean(), F[8].mean()])
+
+    ga, gs = _blocks(alone.step, lambda: bulk(alone.sample()), 200, 16, 40)
+    ma, ms = _blocks(B.step, lambda: bulk(mixed.sample()), 200, 16, 40)
     z = _z(ga, gs, ma, ms)
-    assert np.abs(z).max() < 4.5
+    assert np.abs(z).max() < 4.0, z
     B.retire(mixed)
-    assert mixed.info()["step"] == 100 + 300
+    assert mixed.info()["step"] == 200 + 16 * 40

@@ -169,3 +169,26 @@ def test_capacity_and_argument_errors(usp):
     with pytest.raises(usp.UspError) as e:
         g.step(1)
     assert e.value.status == -6   # not initialised
+
+
+def test_batch_fp64_matches_alone_per_particle(usp):
+    """A simulation stepped inside a batch with uneven neighbours gives the same
+    particles as the oracle (and so as the same simulation alone) to 1e-12."""
+    w = W.couette(ny=40, ppc=50, precision="fp64")
+    mixed = usp.Simulation(w).init_particles()
+    others = [usp.Simulation(W.cavity(n=10, ppc=20, Kn=0.05, precision="fp64", seed=4)).init_particles(),
+              usp.Simulation(W.slit(nx=20, ny=10, ppc=15, precision="fp64", seed=6)).init_particles()]
+    B = usp.Batch(hbm_budget=8 << 30)
+    for s in [mixed] + others:
+        assert B.admit(s) == 0
+    B.step(12)
+    B.retire(mixed)
+    o = oracle.OracleSim(w).init_particles()
+    o.step(12)
+    assert_particles_close(mixed.particles(), o.particles(), VSCALE, _cell_size(w))
+    for s in others:
+        B.retire(s)
+    ws = W.slit(nx=20, ny=10, ppc=15, precision="fp64", seed=6)
+    os_ = oracle.OracleSim(ws).init_particles()
+    os_.step(12)
+    assert_particles_close(others[1].particles(), os_.particles(), VSCALE, _cell_size(ws))
