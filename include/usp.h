@@ -249,6 +249,40 @@ int usp_batch_info(usp_batch* b, int* n_sims, size_t* bytes_in_use);
  * simulation; a full step is the stages in order. */
 int usp_batch_run_stage(usp_batch* b, int stage);
 
+/* ---------------------------------------------------------------------- */
+/* Cell sort that allocates nothing.  The paper has no counterpart: this   */
+/* is a library service for callers that cannot allocate device memory at  */
+/* the point of the call (code inside host callbacks or custom allocators,  */
+/* plug-ins whose host owns every device allocation or enforces a memory   */
+/* budget, paths that must not trigger the implicit synchronisation of     */
+/* cudaMalloc / cudaFree).                                                  */
+/* ---------------------------------------------------------------------- */
+#define USP_STATIC_MAX_CELLS (1 << 18)
+
+/* Counting sort of n particles by cell of `grid` (same cell rule as the
+ * FP64 step: floor((y - lo) / dy), and in 2-D floor((x - lo) / dx), clamped
+ * to the grid).  pos: DEVICE array [n][2] of FP64 (x, y; x ignored in 1-D).
+ * Outputs, DEVICE arrays owned by the caller: cell_start[K + 1] (exclusive
+ * offsets, cell_start[K] = n) and perm[n] (particle indices grouped by cell;
+ * the order inside a cell is the order in which atomics landed, so it can
+ * differ between calls).  Work is queued on `stream` (a cudaStream_t, NULL
+ * for the legacy default stream) and the call does not wait for it.
+ *   - Histogram and cursors live in one file-scope device array of
+ *     2 * (USP_STATIC_MAX_CELLS + 1) 32-bit words (2 MB) that every GPU
+ *     loading the library holds until the process exits; the call clears
+ *     it on the GPU before use and calls no cudaMalloc, cudaFree or other
+ *     allocating routine.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call shares the array: calls whose work overlaps on the GPU
+ *     (different streams without ordering, several host threads) race and
+ *     give wrong results; order them on one stream.
+ * Errors: INVALID_ARG (null pointers, bad grid), CAPACITY when the grid has
+ * more than USP_STATIC_MAX_CELLS cells or n > 2^31 - 1, CUDA. */
+int usp_cell_sort_static(const usp_grid* grid, int64_t n, const double* pos, uint32_t* cell_start,
+                         uint32_t* perm, void* stream);
+
 /* 1 when the library carries the fused FP32 pipeline (USP_PIPE_FUSED).  Its
  * stages for usp_run_stage / usp_batch_run_stage are 10 relaxation of the
  * previous step + advection + bucket scatter, 11 reservoir refill, 12

@@ -118,6 +118,7 @@ def lib(build_if_missing: bool = True):
         "usp_batch_destroy": (c_int, [c_void_p]),
         "usp_batch_run_stage": (c_int, [c_void_p, c_int]),
         "usp_fused_supported": (c_int, []),
+        "usp_cell_sort_static": (c_int, [P(Grid), c_int64, c_void_p, c_void_p, c_void_p, c_void_p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
