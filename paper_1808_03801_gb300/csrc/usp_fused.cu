@@ -266,14 +266,7 @@ __device__ __forceinline__ void emit_c(const SimDev& s, const Ctx& C, int b, uin
     }
 }
 
-// per-warp staging area: CAP particles and a window of kWin destination cells
-constexpr int kWin = 32;
-
-template <int CAP, int DIM>
-__host__ __device__ constexpr int stage_bytes() {
-    return CAP * 4 * (DIM == 2 ? 8 : 7) + 4 * 4 * kWin;
-}
-
+// per-warp staging area
 struct Stage {
     float* x;
     float* y;
@@ -281,63 +274,21 @@ struct Stage {
     float* v1;
     float* v2;
     uint32_t* id;
-    uint32_t* key;    // relaxation flag in the relax pass, destination cell afterwards
-    uint32_t* rank;   // rank inside the window cell, or (bit 31) rank inside a far cell
-    uint32_t* whist;  // arrivals per window cell in this chunk
-    uint32_t* wbase;  // first rank of this chunk in the window cell
-    uint32_t* wlo;    // bucket start of the window cell
-    uint32_t* whi;    // bucket end of the window cell
+    unsigned char* sel;
 };
 
-template <int CAP, int DIM>
+template <int CAP>
 __device__ __forceinline__ Stage stage_of(unsigned char* base, int warp) {
-    float* f = (float*)(base + (size_t)warp * stage_bytes<CAP, DIM>());
+    unsigned char* w = base + (size_t)warp * CAP * 25;
     Stage S;
-    S.x = nullptr;
-    if (DIM == 2) {
-        S.x = f;
-        f += CAP;
-    }
-    S.y = f; f += CAP;
-    S.v0 = f; f += CAP;
-    S.v1 = f; f += CAP;
-    S.v2 = f; f += CAP;
-    uint32_t* u = (uint32_t*)f;
-    S.id = u; u += CAP;
-    S.key = u; u += CAP;
-    S.rank = u; u += CAP;
-    S.whist = u; u += kWin;
-    S.wbase = u; u += kWin;
-    S.wlo = u; u += kWin;
-    S.whi = u;
+    S.x = (float*)w;
+    S.y = S.x + CAP;
+    S.v0 = S.y + CAP;
+    S.v1 = S.v0 + CAP;
+    S.v2 = S.v1 + CAP;
+    S.id = (uint32_t*)(S.v2 + CAP);
+    S.sel = (unsigned char*)(S.id + CAP);
     return S;
-}
-
-// window slot of destination cell d around source cell c (1-D: c-15..c+16,
-// 2-D: the 5 x 5 block around c), or -1
-template <int DIM>
-__device__ __forceinline__ int wslot(int c, int d, int nx) {
-    if (DIM == 1) {
-        const int o = d - c + 15;
-        return (o >= 0 && o < kWin) ? o : -1;
-    }
-    const int cx = c % nx, cy = c / nx;
-    const int dx = d % nx - cx, dy = d / nx - cy;
-    if (dx < -2 || dx > 2 || dy < -2 || dy > 2) return -1;
-    return (dy + 2) * 5 + (dx + 2);
-}
-
-template <int DIM>
-__device__ __forceinline__ int wcell(int c, int w, int nx, int K) {
-    if (DIM == 1) {
-        const int d = c + w - 15;
-        return (d >= 0 && d < K) ? d : -1;
-    }
-    if (w >= 25) return -1;
-    const int x = c % nx + w % 5 - 2, y = c / nx + w / 5 - 2;
-    if (x < 0 || x >= nx || y < 0) return -1;
-    const int d = y * nx + x;
-    return d < K ? d : -1;
 }
 
 template <int CAP, int DIM, bool FLUSH>
@@ -364,63 +315,55 @@ __device__ void g2_cell(const SimDev& s, int cell, int p, uint32_t step, bool pe
     td.inv_nues = 1.0f / f.nues;
     const int q = p ^ 1;
     const uint32_t nch = (n + CAP - 1) / CAP;
-    float a0 = 0, a1 = 0, a2 = 0, ae = 0, b0 = 0, b1 = 0, b2 = 0, be = 0, nr = 0;
 
-    // global -> shared, several loads in flight per lane
-    auto load_chunk = [&](uint32_t ch) -> uint32_t {
+    // stage chunk ch; if `draw_new`, relaxed particles get their new peculiar
+    // velocity in v0..v2 (flag in sel); if `sums`, accumulate the conservation sums
+    float a0 = 0, a1 = 0, a2 = 0, ae = 0, b0 = 0, b1 = 0, b2 = 0, be = 0, nr = 0;
+    auto stage_chunk = [&](uint32_t ch, bool sums) -> uint32_t {
         const uint32_t off = ch * CAP;
         const uint32_t m = min((uint32_t)CAP, n - off);
         __syncwarp();
-#pragma unroll 4
+#pragma unroll 1
         for (uint32_t j = lane; j < m; j += 32) {
             float x = 0.0f, y, v0, v1, v2;
             uint32_t id;
             load_particle<DIM>(s, p, base, nb, spl, off + j, x, y, v0, v1, v2, id);
+            unsigned char sl = 0;
+            if (relax) {
+                const uint4 w = draw(s, id, step, kRelax, 0);
+                if (u01<float>(w.x) < f.pr) {
+                    sl = 1;
+                    float C[3];
+                    es_draw_f(s, f, td, id, step, w, C);
+                    if (sums) {
+                        const float o0 = v0 - f.u[0], o1 = v1 - f.u[1], o2 = v2 - f.u[2];
+                        a0 += o0; a1 += o1; a2 += o2;
+                        ae += o0 * o0 + o1 * o1 + o2 * o2;
+                        b0 += C[0]; b1 += C[1]; b2 += C[2];
+                        be += C[0] * C[0] + C[1] * C[1] + C[2] * C[2];
+                        nr += 1.0f;
+                    }
+                    v0 = C[0];
+                    v1 = C[1];
+                    v2 = C[2];
+                }
+            }
             if (DIM == 2) S.x[j] = x;
             S.y[j] = y;
             S.v0[j] = v0;
             S.v1[j] = v1;
             S.v2[j] = v2;
             S.id[j] = id;
+            S.sel[j] = sl;
         }
         __syncwarp();
         return m;
     };
-    // draw the new peculiar velocities (flag in key[]), optionally with the sums
-    auto relax_chunk = [&](uint32_t m, bool sums) {
-#pragma unroll 1
-        for (uint32_t j = lane; j < m; j += 32) {
-            const uint32_t id = S.id[j];
-            const uint4 w = draw(s, id, step, kRelax, 0);
-            uint32_t sl = 0;
-            if (u01<float>(w.x) < f.pr) {
-                sl = 1;
-                float C[3];
-                es_draw_f(s, f, td, id, step, w, C);
-                if (sums) {
-                    const float o0 = S.v0[j] - f.u[0], o1 = S.v1[j] - f.u[1], o2 = S.v2[j] - f.u[2];
-                    a0 += o0; a1 += o1; a2 += o2;
-                    ae += o0 * o0 + o1 * o1 + o2 * o2;
-                    b0 += C[0]; b1 += C[1]; b2 += C[2];
-                    be += C[0] * C[0] + C[1] * C[1] + C[2] * C[2];
-                    nr += 1.0f;
-                }
-                S.v0[j] = C[0];
-                S.v1[j] = C[1];
-                S.v2[j] = C[2];
-            }
-            S.key[j] = sl;
-        }
-        __syncwarp();
-    };
 
     uint32_t m_last = 0;
-    for (uint32_t ch = 0; ch < nch; ++ch) {
-        m_last = load_chunk(ch);
-        if (relax) relax_chunk(m_last, true);
-    }
+    for (uint32_t ch = 0; ch < nch; ++ch) m_last = stage_chunk(ch, true);
 
-    // conservation factors of the cell (FP64 on one lane, then broadcast)
+    // conservation factors of the cell (FP64 once per cell)
     bool apply = false;
     float uo0 = 0, uo1 = 0, uo2 = 0, mn0 = 0, mn1 = 0, mn2 = 0, alpha = 1;
     if (relax) {
@@ -428,6 +371,7 @@ __device__ void g2_cell(const SimDev& s, int cell, int p, uint32_t step, bool pe
         if (nr >= 2.0f) {
             a0 = warp_sumf(a0); a1 = warp_sumf(a1); a2 = warp_sumf(a2); ae = warp_sumf(ae);
             b0 = warp_sumf(b0); b1 = warp_sumf(b1); b2 = warp_sumf(b2); be = warp_sumf(be);
+            // FP64 on one lane only (the FP64 pipe is narrow), then broadcast
             int ok = 0;
             if (lane == 0) {
                 const double inv = 1.0 / (double)nr;
@@ -459,111 +403,47 @@ __device__ void g2_cell(const SimDev& s, int cell, int p, uint32_t step, bool pe
     Ctx C;
     make_ctx(s, q, C);
     for (uint32_t ch = 0; ch < nch; ++ch) {
-        uint32_t m = m_last;
-        if (nch > 1) {
-            m = load_chunk(ch);
-            if (relax) relax_chunk(m, false);
-        }
+        const uint32_t m = nch > 1 ? stage_chunk(ch, false) : m_last;
         const uint32_t off = ch * CAP;
-        if (!FLUSH) S.whist[lane] = 0;
-        __syncwarp();
-        // correction, advection, destination cell, rank inside the chunk
 #pragma unroll 1
-        for (uint32_t j = lane; j < m; j += 32) {
-            float c[3] = {S.v0[j], S.v1[j], S.v2[j]};
-            const bool relaxed = relax && S.key[j] != 0;
-            if (relaxed) {
-                if (apply) {
-                    c[0] = uo0 + alpha * (c[0] - mn0);
-                    c[1] = uo1 + alpha * (c[1] - mn1);
-                    c[2] = uo2 + alpha * (c[2] - mn2);
-                } else {   // a lone relaxed particle keeps its old velocity
-                    float ox, oy;
-                    uint32_t oid;
-                    load_particle<DIM>(s, p, base, nb, spl, off + j, ox, oy, c[0], c[1], c[2], oid);
+        for (uint32_t b = 0; b < m; b += 32) {
+            const uint32_t j = b + lane;
+            const bool valid = j < m;
+            float x = 0.0f, y = 0.0f, c[3] = {0.0f, 0.0f, 0.0f};
+            uint32_t id = 0;
+            if (valid) {
+                if (DIM == 2) x = S.x[j];
+                y = S.y[j];
+                c[0] = S.v0[j];
+                c[1] = S.v1[j];
+                c[2] = S.v2[j];
+                id = S.id[j];
+                if (S.sel[j]) {
+                    if (apply) {
+                        c[0] = uo0 + alpha * (c[0] - mn0);
+                        c[1] = uo1 + alpha * (c[1] - mn1);
+                        c[2] = uo2 + alpha * (c[2] - mn2);
+                    } else {   // a lone relaxed particle keeps its old velocity
+                        float ox, oy;
+                        uint32_t oid;
+                        load_particle<DIM>(s, p, base, nb, spl, off + j, ox, oy, c[0], c[1], c[2], oid);
+                    }
                 }
             }
             if (FLUSH) {
-                if (relaxed && apply) store_velocity<DIM>(s, p, base, nb, spl, off + j, c[0], c[1], c[2]);
+                if (valid && S.sel[j] && apply) store_velocity<DIM>(s, p, base, nb, spl, off + j, c[0], c[1], c[2]);
                 continue;
             }
-            float x = DIM == 2 ? S.x[j] : 0.0f, y = S.y[j];
             uint32_t key = kNoCell;
-            if (advect_fast<DIM>(s, C, step, S.id[j], x, y, c)) {
+            if (valid && advect_fast<DIM>(s, C, step, id, x, y, c)) {
                 const int dc = cell_f<DIM>(C, x, y);
                 if (!C.reservoir || !in_buffer(s, dc)) key = (uint32_t)dc;
                 else atomicAdd(&s.dyn->counters[kCntRemoved], 1ull);
             }
-            if (DIM == 2) S.x[j] = x;
-            S.y[j] = y;
-            S.v0[j] = c[0];
-            S.v1[j] = c[1];
-            S.v2[j] = c[2];
-            S.key[j] = key;
-            if (key != kNoCell) {
-                const int w = wslot<DIM>(cell, (int)key, C.nx);
-                if (w >= 0) S.rank[j] = atomicAdd(&S.whist[w], 1u);
-                else S.rank[j] = atomicAdd(&C.dcnt[key], 1u) | 0x80000000u;   // far destination
-            }
+            emit_c<DIM>(s, C, q, key, x, y, c[0], c[1], c[2], id, lane);
         }
-        __syncwarp();
-        if (FLUSH) continue;
-        // one global atomic per window cell reserves this chunk's ranks
-        {
-            const uint32_t h = S.whist[lane];
-            const int d = wcell<DIM>(cell, lane, C.nx, C.K);
-            if (h > 0 && d >= 0) {
-                S.wbase[lane] = atomicAdd(&C.dcnt[d], h);
-                S.wlo[lane] = C.dlay[d];
-                S.whi[lane] = min(C.dlay[d + 1], C.cap);
-            }
-        }
-        __syncwarp();
-#pragma unroll 2
-        for (uint32_t j = lane; j < m; j += 32) {
-            const uint32_t key = S.key[j];
-            if (key == kNoCell) continue;
-            const uint32_t r = S.rank[j];
-            uint32_t lo, hi, rank;
-            if (r & 0x80000000u) {
-                rank = r & 0x7FFFFFFFu;
-                lo = C.dlay[key];
-                hi = min(C.dlay[key + 1], C.cap);
-            } else {
-                const int w = wslot<DIM>(cell, (int)key, C.nx);
-                rank = S.wbase[w] + r;
-                lo = S.wlo[w];
-                hi = S.whi[w];
-            }
-            const float x = DIM == 2 ? S.x[j] : 0.0f, y = S.y[j];
-            const float v0 = S.v0[j], v1 = S.v1[j], v2 = S.v2[j];
-            const uint32_t id = S.id[j];
-            if (lo + rank < hi) {
-                const uint32_t i = lo + rank;
-                if (DIM == 2) C.dx_[i] = x;
-                C.dy_[i] = y;
-                C.dv0[i] = v0;
-                C.dv1[i] = v1;
-                C.dv2[i] = v2;
-                C.did[i] = id;
-            } else {
-                const uint32_t k = atomicAdd(&s.dyn->sp_n[q], 1u);
-                atomicAdd(&s.dyn->counters[kCntSpilled], 1ull);
-                if (k < (uint32_t)kSpillCap) {
-                    if (DIM == 2) s.sp_pos[q][0][k] = x;
-                    s.sp_pos[q][1][k] = y;
-                    s.sp_vel[q][0][k] = v0;
-                    s.sp_vel[q][1][k] = v1;
-                    s.sp_vel[q][2][k] = v2;
-                    s.sp_pid[q][k] = id;
-                    s.sp_cell[q][k] = key;
-                } else {
-                    atomicAdd(&s.dyn->counters[kCntOverflow], 1ull);
-                }
-            }
-        }
-        __syncwarp();
     }
+    __syncwarp();
 }
 
 template <int CAP, int DIM, bool FLUSH>
@@ -573,7 +453,7 @@ __global__ void __launch_bounds__(128, 4) k_g2(const SimDev* __restrict__ sims, 
     __shared__ SimDev sim_sh;
     __shared__ uint32_t spl_all[4][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const Stage S = stage_of<CAP, DIM>(g2_smem, warp);
+    const Stage S = stage_of<CAP>(g2_smem, warp);
     const int nt = *ntiles;
     for (int t = blockIdx.x; t < nt; t += gridDim.x) {
         const int2 tile = tiles[t];
@@ -1043,7 +923,7 @@ __global__ void k_finish_f(const SimDev* __restrict__ sims, int nsims, int mode)
 
 template <int CAP, int DIM, bool FLUSH>
 void launch_g2_one(const Launch& L) {
-    const int smem = 4 * stage_bytes<CAP, DIM>();
+    const int smem = 4 * CAP * 25;
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_g2<CAP, DIM, FLUSH>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -1081,18 +961,18 @@ void fused_prepare_attributes() {
     static bool done = false;
     if (done) return;
     done = true;
-    cudaFuncSetAttribute(k_g2<128, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<128, 1>());
-    cudaFuncSetAttribute(k_g2<128, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<128, 2>());
-    cudaFuncSetAttribute(k_g2<256, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<256, 1>());
-    cudaFuncSetAttribute(k_g2<256, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<256, 2>());
-    cudaFuncSetAttribute(k_g2<512, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<512, 1>());
-    cudaFuncSetAttribute(k_g2<512, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<512, 2>());
-    cudaFuncSetAttribute(k_g2<128, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<128, 1>());
-    cudaFuncSetAttribute(k_g2<128, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<128, 2>());
-    cudaFuncSetAttribute(k_g2<256, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<256, 1>());
-    cudaFuncSetAttribute(k_g2<256, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<256, 2>());
-    cudaFuncSetAttribute(k_g2<512, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<512, 1>());
-    cudaFuncSetAttribute(k_g2<512, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<512, 2>());
+    cudaFuncSetAttribute(k_g2<128, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 128 * 25);
+    cudaFuncSetAttribute(k_g2<128, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 128 * 25);
+    cudaFuncSetAttribute(k_g2<256, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 256 * 25);
+    cudaFuncSetAttribute(k_g2<256, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 256 * 25);
+    cudaFuncSetAttribute(k_g2<512, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 512 * 25);
+    cudaFuncSetAttribute(k_g2<512, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 512 * 25);
+    cudaFuncSetAttribute(k_g2<128, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 128 * 25);
+    cudaFuncSetAttribute(k_g2<128, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 128 * 25);
+    cudaFuncSetAttribute(k_g2<256, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 256 * 25);
+    cudaFuncSetAttribute(k_g2<256, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 256 * 25);
+    cudaFuncSetAttribute(k_g2<512, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 512 * 25);
+    cudaFuncSetAttribute(k_g2<512, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 512 * 25);
     cudaGetLastError();
 }
 
