@@ -41,6 +41,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparator", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--serve-requests", type=int, default=48,
+                    help="requests of the serving leg (0: skip); --serve-full uses the full request mix")
+    ap.add_argument("--serve-full", action="store_true")
     return ap.parse_args()
 
 
@@ -231,6 +234,26 @@ def e2e_rate(U, W, torch, batch, pipeline, steps, stream):
     return n * steps / el, h2d / steps, d2h / steps
 
 
+def serving_leg(W, args, capacity):
+    """Continuous batching of independent solves arriving as a Poisson stream at
+    80% of the measured batched capacity; p50 / p99 time to solution."""
+    from paper_1808_03801_gb300.serve import serve_requests
+    if args.serve_full:
+        reqs = W.serving_requests(n=256)
+    else:
+        reqs = W.serving_requests(n=args.serve_requests, n_min=1e4, n_max=4e5, steps_min=100, steps_max=400)
+    work = []
+    for w in reqs:
+        g = w["grid"]
+        cells = (g["nx"] if g["dim"] == 2 else 1) * g["ny"]
+        work.append(cells * w["params"]["ppc_ref"] * w["steps"])
+    rate = 0.8 * capacity / (sum(work) / len(work))
+    rep, _ = serve_requests(reqs, rate=rate, hbm_budget=64 << 30, pipeline="fused", precision="fp32")
+    rep.update({"arrival_rate_per_s": rate, "mix": "couette/poiseuille/cavity, FP32 fused, log-uniform N, Kn",
+                "full_mix": bool(args.serve_full)})
+    return rep
+
+
 def run_gpu(args):
     import torch
     rank, world, dist = dist_setup(args.gpus)
@@ -316,6 +339,8 @@ def run_gpu(args):
                 s.close()
             result["plain_fp64_per_sim"] = {"value": statistics.mean(cmp_rates), "unit": METRIC,
                                             "ratio": value / statistics.mean(cmp_rates)}
+        if args.serve_requests > 0:
+            result["serving"] = serving_leg(W, args, value)
         if not args.no_cpu_baseline:
             rate, n, done, elc = oracle_rate(args.cpu_seconds)
             result["cpu_baseline"] = {"value": rate, "unit": METRIC, "cores": 1, "kind": "oracle",

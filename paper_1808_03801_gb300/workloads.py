@@ -182,6 +182,7 @@ def serving_requests(n=256, seed=12345, n_min=1e4, n_max=4e6, steps_min=500, ste
             ny = max(4, int(round(npart / 100.0)))
             w = poiseuille(ny=ny, ppc=100, Kn=Kn, precision="fp32", steps=steps, seed=i + 1)
         w["name"] = f"req{i}:{kind}"
+        w["steps"] = steps
         out.append(w)
     return out
 
