@@ -40,6 +40,7 @@ def parse():
     ap.add_argument("--pipeline", default="auto", choices=["auto", "plain", "fused"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparator", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="skip the launch autotuner")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--serve-requests", type=int, default=48,
                     help="requests of the serving leg (0: skip); --serve-full uses the full request mix")
@@ -160,12 +161,14 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------------- GPU
-def make_batch(U, W, torch, batch, pipeline, precision="fp32", seed0=1, stream=None):
+def make_batch(U, W, torch, batch, pipeline, precision="fp32", seed0=1, stream=None, tuning=None):
     sims = []
     for i in range(batch):
         w = W.sod(precision=precision, seed=seed0 + i)
         w["params"]["pipeline"] = pipeline
         sims.append(U.Simulation(w, stream=stream).init_particles())
+        if tuning:
+            sims[-1].set_tuning(tuning["fused_R"], tuning["grid_per_sm"])
     B = U.Batch(hbm_budget=200 << 30, max_sims=max(batch, 1), stream=stream)
     for s in sims:
         rc = B.admit(s)
@@ -269,7 +272,16 @@ def run_gpu(args):
     if pipeline == "auto":
         pipeline = "fused" if U.fused_available() else "plain"
     stream = torch.cuda.Stream()
-    sims, B = make_batch(U, W, torch, args.batch, pipeline, stream=stream)
+    tuning = None
+    if not args.no_tune:
+        from paper_1808_03801_gb300 import autotune
+        tw = []
+        for i in range(min(16, args.batch)):
+            w = W.sod(precision="fp32", seed=100 + i)
+            w["params"]["pipeline"] = pipeline
+            tw.append(w)
+        tuning = autotune.tune_batch(tw, use_cache=False)
+    sims, B = make_batch(U, W, torch, args.batch, pipeline, stream=stream, tuning=tuning)
     n_total = sum(s.info()["n_particles"] for s in sims)
     B.step(max(args.warmup, 3))
     torch.cuda.synchronize()
@@ -307,7 +319,9 @@ def run_gpu(args):
     result = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
               "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
               "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-              "config": workload_cfg(args.batch, pipeline), "clocks": clocks.summary(), "roofline": roof,
+              "config": dict(workload_cfg(args.batch, pipeline),
+                             tuning={k: v for k, v in (tuning or {}).items() if k != "tried"}),
+              "clocks": clocks.summary(), "roofline": roof,
               "gpu_launches": launches}
     B.close()
     for s in sims:

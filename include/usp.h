@@ -283,6 +283,15 @@ int usp_batch_run_stage(usp_batch* b, int stage);
 int usp_cell_sort_static(const usp_grid* grid, int64_t n, const double* pos, uint32_t* cell_start,
                          uint32_t* perm, void* stream);
 
+/* Launch tuning (set by the autotuner, paper_1808_03801_gb300/autotune.py):
+ * fused_R in {4, 8, 12} sets the fused kernels' staging capacity to 32 R
+ * particles per cell pass (larger cells take two sweeps); grid_per_sm in
+ * 1..32 sets the persistent blocks per SM of the tiled kernels; 0 keeps a
+ * value.  A batch uses the largest values of its members.  STATE while the
+ * handle is admitted to a batch. */
+int usp_set_tuning(usp_handle* h, int fused_R, int grid_per_sm);
+int usp_get_tuning(usp_handle* h, int* fused_R, int* grid_per_sm);
+
 /* 1 when the library carries the fused FP32 pipeline (USP_PIPE_FUSED).  Its
  * stages for usp_run_stage / usp_batch_run_stage are 10 relaxation of the
  * previous step + advection + bucket scatter, 11 reservoir refill, 12

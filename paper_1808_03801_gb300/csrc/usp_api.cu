@@ -63,7 +63,8 @@ struct usp_handle {
     std::string err;
     std::vector<uint32_t> inj_count_host;
     int batch_refs = 0;
-    int fused_R = 8;                  // particles per lane held in registers by the fused kernels
+    int fused_R = 8;                  // staging capacity of the fused kernels: 32 R particles per cell pass
+    int grid_per_sm = 8;              // persistent blocks per SM of the tiled kernels
     cudaStream_t batch_stream = nullptr;   // stream of the batch the handle is admitted to
 };
 
@@ -148,8 +149,8 @@ static Launch make_launch(usp_handle* h) {
     L.nctiles = h->d_ntiles + 1;
     L.nsims = 1;
     L.dims = h->host.dim == 1 ? 1 : 2;
-    L.grid_p = persistent_grid(h->nptiles, 8);
-    L.grid_c = persistent_grid(h->nctiles, 8);
+    L.grid_p = persistent_grid(h->nptiles, h->grid_per_sm);
+    L.grid_c = persistent_grid(h->nctiles, h->grid_per_sm);
     L.stream = h->stream;
     return L;
 }
@@ -1110,8 +1111,10 @@ static Launch batch_launch(usp_batch* b) {
     for (auto* h : b->members) L.dims |= h->host.dim == 1 ? 1 : 2;
     // fixed persistent grids: the tile counts are read on the device, so the
     // captured graph stays valid while simulations come and go
-    L.grid_p = persistent_grid(1 << 30, 8);
-    L.grid_c = persistent_grid(1 << 30, 8);
+    int per_sm = 1;
+    for (auto* h : b->members) per_sm = std::max(per_sm, h->grid_per_sm);
+    L.grid_p = persistent_grid(1 << 30, per_sm);
+    L.grid_c = persistent_grid(1 << 30, per_sm);
     L.stream = b->stream;
     return L;
 }
@@ -1200,3 +1203,24 @@ extern "C" int usp_batch_run_stage(usp_batch* b, int stage) {
 }
 
 extern "C" int usp_fused_supported(void) { return 1; }
+
+// Tuning knobs chosen by the autotuner: fused staging capacity (R = 4, 8 or
+// 12, i.e. 128, 256 or 512 particles per cell pass; 0 keeps the current) and
+// persistent blocks per SM (1..32; 0 keeps).  Captured graphs are rebuilt.
+extern "C" int usp_set_tuning(usp_handle* h, int fused_R, int grid_per_sm) {
+    if (!h) return USP_ERR_INVALID_ARG;
+    if (h->batch_refs) return fail(h, USP_ERR_STATE, "handle is admitted to a batch");
+    if (fused_R != 0 && fused_R != 4 && fused_R != 8 && fused_R != 12) return fail(h, USP_ERR_INVALID_ARG, "R");
+    if (grid_per_sm < 0 || grid_per_sm > 32) return fail(h, USP_ERR_INVALID_ARG, "grid_per_sm");
+    if (fused_R) h->fused_R = fused_R;
+    if (grid_per_sm) h->grid_per_sm = grid_per_sm;
+    destroy_graphs(h->graphs);
+    return USP_OK;
+}
+
+extern "C" int usp_get_tuning(usp_handle* h, int* fused_R, int* grid_per_sm) {
+    if (!h) return USP_ERR_INVALID_ARG;
+    if (fused_R) *fused_R = h->fused_R;
+    if (grid_per_sm) *grid_per_sm = h->grid_per_sm;
+    return USP_OK;
+}

@@ -118,6 +118,8 @@ def lib(build_if_missing: bool = True):
         "usp_batch_destroy": (c_int, [c_void_p]),
         "usp_batch_run_stage": (c_int, [c_void_p, c_int]),
         "usp_fused_supported": (c_int, []),
+        "usp_set_tuning": (c_int, [c_void_p, c_int, c_int]),
+        "usp_get_tuning": (c_int, [c_void_p, P(c_int), P(c_int)]),
         "usp_cell_sort_static": (c_int, [P(Grid), c_int64, c_void_p, c_void_p, c_void_p, c_void_p]),
     }
     for name, (res, args) in sig.items():
@@ -324,6 +326,15 @@ class Simulation:
         self._check(rc, "usp_get_particles")
         m = n.value
         return {"pos": pos[:m], "vel": vel[:m], "pid": pid[:m], "cell": cell[:m]}
+
+    def set_tuning(self, fused_R=0, grid_per_sm=0):
+        self._check(lib().usp_set_tuning(self._h, int(fused_R), int(grid_per_sm)), "usp_set_tuning")
+        return self
+
+    def tuning(self):
+        r, g = c_int(), c_int()
+        self._check(lib().usp_get_tuning(self._h, ctypes.byref(r), ctypes.byref(g)), "usp_get_tuning")
+        return {"fused_R": r.value, "grid_per_sm": g.value}
 
     def params(self):
         out = np.zeros((self.K, NPRM))
