@@ -276,7 +276,7 @@ def run_gpu(args):
     if not args.no_tune:
         from paper_1808_03801_gb300 import autotune
         tw = []
-        for i in range(min(16, args.batch)):
+        for i in range(args.batch):
             w = W.sod(precision="fp32", seed=100 + i)
             w["params"]["pipeline"] = pipeline
             tw.append(w)
