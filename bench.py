@@ -113,6 +113,19 @@ class Clocks:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
+def reduce_max(value, dist, device="cpu"):
+    """Max of a per-rank number over all ranks (the timed region's length)."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(particles_per_rank, world, steps, elapsed_max):
+    """Updates of all ranks divided by the slowest rank's time (weak scaling)."""
+    return particles_per_rank * world * steps / elapsed_max
+
+
 def dist_setup(n_gpus):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -294,11 +307,9 @@ def run_gpu(args):
     el = time_batch_steps(torch, B, args.steps)
     torch.cuda.synchronize()
     if dist:
-        t = torch.tensor([el], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        el = float(t.item())
+        el = reduce_max(el, dist, "cuda")
     clocks.stop()
-    value = n_total * world * args.steps / el
+    value = whole_job_rate(n_total, world, args.steps, el)
     ms = 1e3 * el / args.steps
 
     # dominant kernel: per-stage times outside the graph, on the same stream
