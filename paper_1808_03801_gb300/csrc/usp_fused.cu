@@ -848,8 +848,16 @@ __global__ void __launch_bounds__(1024) k_layout(const SimDev* __restrict__ sims
             lf += bucket_size(s, C, c);
             le += C[c];
         }
-        atomicAdd(&tot_full, lf);
-        atomicAdd(&tot_exact, le);
+        // warp sums first: one shared atomic per warp instead of per thread
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lf += __shfl_xor_sync(0xffffffffu, lf, o);
+            le += __shfl_xor_sync(0xffffffffu, le, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(&tot_full, lf);
+            atomicAdd(&tot_exact, le);
+        }
         __syncthreads();
         // bucket sizes with slack when they fit, else the exact demand plus an even share of what is left
         const unsigned long long demand = tot_exact + (s.has_reservoir ? s.inj_total : 0u);

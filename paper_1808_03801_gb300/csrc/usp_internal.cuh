@@ -135,7 +135,8 @@ template <> __device__ __forceinline__ double u01<double>(uint32_t x) {
     return fma((double)x, 2.3283064365386963e-10, 1.1641532182693481e-10);
 }
 template <> __device__ __forceinline__ float u01<float>(uint32_t x) {
-    return (float)(((x >> 9) << 1) | 1u) * 5.9604644775390625e-08f;
+    // 1 + k 2^-23 built from the bits, minus (1 - 2^-24): exactly k 2^-23 + 2^-24
+    return __uint_as_float(0x3F800000u | (x >> 9)) - 0.99999994039535522f;
 }
 
 // Box-Muller pair from two words.
