@@ -324,37 +324,54 @@ __device__ void g2_cell(const SimDev& s, int cell, int p, uint32_t step, bool pe
         const uint32_t m = min((uint32_t)CAP, n - off);
         __syncwarp();
 #pragma unroll 1
-        for (uint32_t j = lane; j < m; j += 32) {
-            float x = 0.0f, y, v0, v1, v2;
-            uint32_t id;
-            load_particle<DIM>(s, p, base, nb, spl, off + j, x, y, v0, v1, v2, id);
-            unsigned char sl = 0;
+        for (uint32_t j0 = lane; j0 < m; j0 += 64) {
+            const uint32_t j1 = j0 + 32;
+            const bool has1 = j1 < m;
+            float x0 = 0.0f, y0, p0, q0, r0;
+            float x1 = 0.0f, y1 = 0.0f, p1 = 0.0f, q1 = 0.0f, r1 = 0.0f;
+            uint32_t id0, id1 = 0;
+            load_particle<DIM>(s, p, base, nb, spl, off + j0, x0, y0, p0, q0, r0, id0);
+            if (has1) load_particle<DIM>(s, p, base, nb, spl, off + j1, x1, y1, p1, q1, r1, id1);
+            unsigned char s0 = 0, s1 = 0;
             if (relax) {
-                const uint4 w = draw(s, id, step, kRelax, 0);
-                if (u01<float>(w.x) < f.pr) {
-                    sl = 1;
-                    float C[3];
-                    es_draw_f(s, f, td, id, step, w, C);
-                    if (sums) {
-                        const float o0 = v0 - f.u[0], o1 = v1 - f.u[1], o2 = v2 - f.u[2];
-                        a0 += o0; a1 += o1; a2 += o2;
-                        ae += o0 * o0 + o1 * o1 + o2 * o2;
-                        b0 += C[0]; b1 += C[1]; b2 += C[2];
-                        be += C[0] * C[0] + C[1] * C[1] + C[2] * C[2];
-                        nr += 1.0f;
+                const uint4 w0 = draw(s, id0, step, kRelax, 0);
+                const uint4 w1 = draw(s, id1, step, kRelax, 0);
+                s0 = u01<float>(w0.x) < f.pr;
+                s1 = has1 && u01<float>(w1.x) < f.pr;
+                if (s0 | s1) {
+                    float C0[3], C1[3];
+                    es_draw_f(s, f, td, id0, step, w0, C0);
+                    es_draw_f(s, f, td, id1, step, w1, C1);
+                    if (s0) {
+                        if (sums) {
+                            const float o0 = p0 - f.u[0], o1 = q0 - f.u[1], o2 = r0 - f.u[2];
+                            a0 += o0; a1 += o1; a2 += o2;
+                            ae += o0 * o0 + o1 * o1 + o2 * o2;
+                            b0 += C0[0]; b1 += C0[1]; b2 += C0[2];
+                            be += C0[0] * C0[0] + C0[1] * C0[1] + C0[2] * C0[2];
+                            nr += 1.0f;
+                        }
+                        p0 = C0[0]; q0 = C0[1]; r0 = C0[2];
                     }
-                    v0 = C[0];
-                    v1 = C[1];
-                    v2 = C[2];
+                    if (s1) {
+                        if (sums) {
+                            const float o0 = p1 - f.u[0], o1 = q1 - f.u[1], o2 = r1 - f.u[2];
+                            a0 += o0; a1 += o1; a2 += o2;
+                            ae += o0 * o0 + o1 * o1 + o2 * o2;
+                            b0 += C1[0]; b1 += C1[1]; b2 += C1[2];
+                            be += C1[0] * C1[0] + C1[1] * C1[1] + C1[2] * C1[2];
+                            nr += 1.0f;
+                        }
+                        p1 = C1[0]; q1 = C1[1]; r1 = C1[2];
+                    }
                 }
             }
-            if (DIM == 2) S.x[j] = x;
-            S.y[j] = y;
-            S.v0[j] = v0;
-            S.v1[j] = v1;
-            S.v2[j] = v2;
-            S.id[j] = id;
-            S.sel[j] = sl;
+            if (DIM == 2) S.x[j0] = x0;
+            S.y[j0] = y0; S.v0[j0] = p0; S.v1[j0] = q0; S.v2[j0] = r0; S.id[j0] = id0; S.sel[j0] = s0;
+            if (has1) {
+                if (DIM == 2) S.x[j1] = x1;
+                S.y[j1] = y1; S.v0[j1] = p1; S.v1[j1] = q1; S.v2[j1] = r1; S.id[j1] = id1; S.sel[j1] = s1;
+            }
         }
         __syncwarp();
         return m;
