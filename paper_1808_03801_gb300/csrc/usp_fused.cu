@@ -1012,7 +1012,7 @@ void launch_fused_moments(const Launch& L, int R) {
     else k_g1<12><<<L.grid_c, 256, 0, L.stream>>>(L.sims, L.ctiles, L.nctiles);
 }
 
-void launch_fused_params(const Launch& L) { k_params_f<<<L.grid_c, 64, 0, L.stream>>>(L.sims, L.ctiles, L.nctiles); }
+void launch_fused_params(const Launch& L) { k_params_f<<<L.grid_c, 32, 0, L.stream>>>(L.sims, L.ctiles, L.nctiles); }
 
 void launch_fused_layout(const Launch& L) { k_layout<false><<<L.nsims, 1024, 0, L.stream>>>(L.sims, L.nsims); }
 

@@ -582,7 +582,7 @@ void launch_moments(const Launch& L, bool fp64) {
     if (fp64) k_moments<double><<<L.grid_c, 256, 0, L.stream>>>(L.sims, L.ctiles, L.nctiles);
     else k_moments<float><<<L.grid_c, 256, 0, L.stream>>>(L.sims, L.ctiles, L.nctiles);
 }
-void launch_params(const Launch& L) { k_params<<<L.grid_c, 64, 0, L.stream>>>(L.sims, L.ctiles, L.nctiles); }
+void launch_params(const Launch& L) { k_params<<<L.grid_c, 32, 0, L.stream>>>(L.sims, L.ctiles, L.nctiles); }
 void launch_relax(const Launch& L, bool fp64) {
     if (fp64) k_relax<double><<<L.grid_c, 256, 0, L.stream>>>(L.sims, L.ctiles, L.nctiles);
     else k_relax<float><<<L.grid_c, 256, 0, L.stream>>>(L.sims, L.ctiles, L.nctiles);
