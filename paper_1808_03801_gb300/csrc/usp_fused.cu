@@ -114,18 +114,56 @@ __device__ __forceinline__ void store_velocity(const SimDev& s, int b, uint32_t 
     }
 }
 
+// register copy of the source buffer's planes for the particles of one cell
+struct Src {
+    const float* x;
+    const float* y;
+    const float* v0;
+    const float* v1;
+    const float* v2;
+    const uint32_t* id;
+};
+
+__device__ __forceinline__ Src src_of(const SimDev& s, int b) {
+    Src P;
+    P.x = (const float*)s.pos[b][0];
+    P.y = (const float*)s.pos[b][1];
+    P.v0 = (const float*)s.vel[b][0];
+    P.v1 = (const float*)s.vel[b][1];
+    P.v2 = (const float*)s.vel[b][2];
+    P.id = s.pid[b];
+    return P;
+}
+
+template <int DIM>
+__device__ __forceinline__ void load_src(const Src& P, const SimDev& s, int b, uint32_t base, uint32_t nb,
+                                         const uint32_t* spl, uint32_t j, float& x, float& y, float& v0, float& v1,
+                                         float& v2, uint32_t& id) {
+    if (j < nb) {
+        const uint32_t i = base + j;
+        if (DIM == 2) x = P.x[i];
+        y = P.y[i];
+        v0 = P.v0[i];
+        v1 = P.v1[i];
+        v2 = P.v2[i];
+        id = P.id[i];
+    } else {
+        load_particle<DIM>(s, b, base, nb, spl, j, x, y, v0, v1, v2, id);
+    }
+}
+
 // per-cell constants of the time-instant draw (Eq. 30)
 struct TimeDraw {
     float dt, a, em1, ema, inv_nues;
 };
 
-__device__ __forceinline__ void es_draw_f(const SimDev& s, const FCell& f, const TimeDraw& td, uint32_t pid,
+__device__ __forceinline__ void es_draw_f(const uint2 key, const FCell& f, const TimeDraw& td, uint32_t pid,
                                           uint32_t step, const uint4& w, float* C) {
     const float U1 = u01<float>(w.y);
     const float t = td.a < 1.0f ? __logf(1.0f + U1 * td.em1) * td.inv_nues
                                 : td.dt + __logf(U1 + (1.0f - U1) * td.ema) * td.inv_nues;
     const float sf = f.pne + (1.0f - f.pne) * __expf(-f.nu * t);          // Eq. 32
-    const uint4 v = draw(s, pid, step, kRelax, 1);
+    const uint4 v = philox(make_uint4(pid, step, kRelax, 1), key);
     float z0, z1, z2, z3, z4, z5;
     box_muller<float>(w.z, w.w, z0, z1);
     box_muller<float>(v.x, v.y, z2, z3);
@@ -315,6 +353,8 @@ __device__ void g2_cell(const SimDev& s, int cell, int p, uint32_t step, bool pe
     td.inv_nues = 1.0f / f.nues;
     const int q = p ^ 1;
     const uint32_t nch = (n + CAP - 1) / CAP;
+    const Src P = src_of(s, p);
+    const uint2 key = make_uint2(s.key0, s.key1);
 
     // stage chunk ch; if `draw_new`, relaxed particles get their new peculiar
     // velocity in v0..v2 (flag in sel); if `sums`, accumulate the conservation sums
@@ -330,18 +370,18 @@ __device__ void g2_cell(const SimDev& s, int cell, int p, uint32_t step, bool pe
             float x0 = 0.0f, y0, p0, q0, r0;
             float x1 = 0.0f, y1 = 0.0f, p1 = 0.0f, q1 = 0.0f, r1 = 0.0f;
             uint32_t id0, id1 = 0;
-            load_particle<DIM>(s, p, base, nb, spl, off + j0, x0, y0, p0, q0, r0, id0);
-            if (has1) load_particle<DIM>(s, p, base, nb, spl, off + j1, x1, y1, p1, q1, r1, id1);
+            load_src<DIM>(P, s, p, base, nb, spl, off + j0, x0, y0, p0, q0, r0, id0);
+            if (has1) load_src<DIM>(P, s, p, base, nb, spl, off + j1, x1, y1, p1, q1, r1, id1);
             unsigned char s0 = 0, s1 = 0;
             if (relax) {
-                const uint4 w0 = draw(s, id0, step, kRelax, 0);
-                const uint4 w1 = draw(s, id1, step, kRelax, 0);
+                const uint4 w0 = philox(make_uint4(id0, step, kRelax, 0), key);
+                const uint4 w1 = philox(make_uint4(id1, step, kRelax, 0), key);
                 s0 = u01<float>(w0.x) < f.pr;
                 s1 = has1 && u01<float>(w1.x) < f.pr;
                 if (s0 | s1) {
                     float C0[3], C1[3];
-                    es_draw_f(s, f, td, id0, step, w0, C0);
-                    es_draw_f(s, f, td, id1, step, w1, C1);
+                    es_draw_f(key, f, td, id0, step, w0, C0);
+                    es_draw_f(key, f, td, id1, step, w1, C1);
                     if (s0) {
                         if (sums) {
                             const float o0 = p0 - f.u[0], o1 = q0 - f.u[1], o2 = r0 - f.u[2];
