@@ -28,6 +28,7 @@ sys.path.insert(0, ROOT)
 METRIC = "particle-updates/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM = 6800.0
+KG2_DRAM_BYTES_PER_PARTICLE = 38.91   # profiles/k_g2_k_g1_sod_batch32_fused.md
 
 
 def parse():
@@ -41,6 +42,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparator", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch autotuner")
+    ap.add_argument("--prof-tubes", type=int, default=0,
+                    help="profiling case for ncu: N tubes, 3 steps, then the stages of one step; no timing")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--serve-requests", type=int, default=48,
                     help="requests of the serving leg (0: skip); --serve-full uses the full request mix")
@@ -321,8 +324,11 @@ def run_gpu(args):
     rec = 20                         # FP32 1-D record: y, c0, c1, c2 (4 B each), pid (4 B)
     alg = 2 * rec * n_total          # read and write each particle once per step
     achieved = alg / st[top] / 1e9
+    # DRAM bytes per particle of k_g2 from the ncu capture in profiles/ (32-tube
+    # case, scaled by particles); recorded for the current k_g2
+    traffic = KG2_DRAM_BYTES_PER_PARTICLE * n_total if names[top] == "k_g2" else None
     roof = {"bound": "hbm", "kernel": names[top], "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": None, "peak_source": f"{src} hbm_gbs (copy, burst)",
+            "frac": achieved / hbm, "traffic": traffic, "peak_source": f"{src} hbm_gbs (copy, burst)",
             "stage_ms": {names[k]: 1e3 * v for k, v in st.items()},
             "step_frac": alg / (el / args.steps) / 1e9 / hbm}
     launches = U.launches_per_step(pipeline, reservoir=False) * args.steps
@@ -376,8 +382,32 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_profile_case(args):
+    """Small case of the bench workload for kernel captures: N Sod tubes in one
+    batch, three warm-up steps, then the five stages of one step."""
+    import torch
+    from paper_1808_03801_gb300 import usp as U, workloads as W
+    sims = []
+    for i in range(args.prof_tubes):
+        w = W.sod(precision="fp32", seed=1 + i)
+        w["params"]["pipeline"] = "fused"
+        sims.append(U.Simulation(w).init_particles())
+    B = U.Batch(hbm_budget=64 << 30, max_sims=len(sims))
+    for sim in sims:
+        assert B.admit(sim) == 0
+    B.step(3)
+    torch.cuda.synchronize()
+    for k, _ in U.stage_list("fused"):
+        B.run_stage(k)
+    torch.cuda.synchronize()
+    print("profile case done:", sum(sim.info()["n_particles"] for sim in sims), "particles")
+
+
 def main():
     args = parse()
+    if args.prof_tubes:
+        run_profile_case(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
