@@ -157,13 +157,14 @@ struct TimeDraw {
     float dt, a, em1, ema, inv_nues;
 };
 
+// v: the second counter's words (drawn here unless the caller has them)
 __device__ __forceinline__ void es_draw_f(const uint2 key, const FCell& f, const TimeDraw& td, uint32_t pid,
-                                          uint32_t step, const uint4& w, float* C) {
+                                          uint32_t step, const uint4& w, float* C, const uint4* v_in = nullptr) {
     const float U1 = u01<float>(w.y);
     const float t = td.a < 1.0f ? __logf(1.0f + U1 * td.em1) * td.inv_nues
                                 : td.dt + __logf(U1 + (1.0f - U1) * td.ema) * td.inv_nues;
     const float sf = f.pne + (1.0f - f.pne) * __expf(-f.nu * t);          // Eq. 32
-    const uint4 v = philox(make_uint4(pid, step, kRelax, 1), key);
+    const uint4 v = v_in ? *v_in : philox(make_uint4(pid, step, kRelax, 1), key);
     float z0, z1, z2, z3, z4, z5;
     box_muller<float>(w.z, w.w, z0, z1);
     box_muller<float>(v.x, v.y, z2, z3);
@@ -355,6 +356,7 @@ __device__ void g2_cell(const SimDev& s, int cell, int p, uint32_t step, bool pe
     const uint32_t nch = (n + CAP - 1) / CAP;
     const Src P = src_of(s, p);
     const uint2 key = make_uint2(s.key0, s.key1);
+    const bool eager = f.pr > 0.5f;
 
     // stage chunk ch; if `draw_new`, relaxed particles get their new peculiar
     // velocity in v0..v2 (flag in sel); if `sums`, accumulate the conservation sums
@@ -376,12 +378,19 @@ __device__ void g2_cell(const SimDev& s, int cell, int p, uint32_t step, bool pe
             if (relax) {
                 const uint4 w0 = philox(make_uint4(id0, step, kRelax, 0), key);
                 const uint4 w1 = philox(make_uint4(id1, step, kRelax, 0), key);
+                // when most particles relax, draw the second counter of both up
+                // front: four independent Philox chains in flight
+                uint4 u0 = make_uint4(0, 0, 0, 0), u1 = u0;
+                if (eager) {
+                    u0 = philox(make_uint4(id0, step, kRelax, 1), key);
+                    u1 = philox(make_uint4(id1, step, kRelax, 1), key);
+                }
                 s0 = u01<float>(w0.x) < f.pr;
                 s1 = has1 && u01<float>(w1.x) < f.pr;
                 if (s0 | s1) {
                     float C0[3], C1[3];
-                    es_draw_f(key, f, td, id0, step, w0, C0);
-                    es_draw_f(key, f, td, id1, step, w1, C1);
+                    es_draw_f(key, f, td, id0, step, w0, C0, eager ? &u0 : nullptr);
+                    es_draw_f(key, f, td, id1, step, w1, C1, eager ? &u1 : nullptr);
                     if (s0) {
                         if (sums) {
                             const float o0 = p0 - f.u[0], o1 = q0 - f.u[1], o2 = r0 - f.u[2];
