@@ -332,6 +332,8 @@ extern "C" int usp_create(const usp_gas* gas, const usp_grid* grid, const usp_bc
     s.f_inv_dx = (float)(1.0 / s.dx);
     s.f_inv_dy = (float)(1.0 / s.dy);
     for (int d = 0; d < 3; ++d) s.f_bdt[d] = (float)(s.body[d] * s.dt);
+    s.f_w = (float)s.w;
+    s.f_inv_R = (float)(1.0 / s.R);
 
     const int K = s.K;
     int rc = USP_OK;
@@ -354,6 +356,8 @@ extern "C" int usp_create(const usp_gas* gas, const usp_grid* grid, const usp_bc
     CALLOC(inj_pidoff, uint32_t, K);
     CALLOC(fprm, float, (size_t)kNFPrm * K);
     if (prm->pipeline == USP_PIPE_FUSED) {
+        CALLOC(momf, float, 16 * (size_t)K);
+        CALLOC(floc, float, 4 * (size_t)K);
         for (int b = 0; b < 2; ++b) {
             CALLOC(lay[b], uint32_t, K + 1);
             CALLOC(cnt[b], uint32_t, K);

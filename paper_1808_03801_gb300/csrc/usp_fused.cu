@@ -9,16 +9,21 @@
 //             bucket sizes come from the previous histogram plus slack).
 //   k_inject  reservoir buffer cells refilled into buffer q.
 //   k_g1      per cell (one warp): two-pass moments of Eq. 1 from the
-//             particles held in registers (mean, then central sums).
+//             particles held in registers (mean, then central sums), and the
+//             cell's n, T, |u| for its neighbours' Kn_GLL.
 //   k_params  per cell: Kn_GLL and P_ne (Eqs. 16-18), sigma* and q* (Eq. 33),
 //             the Cholesky factor of the ES covariance (Eq. 6c) in FP64, the
 //             fields and the average of Eq. 34.
 //   k_layout  per simulation: histogram -> bucket sizes -> exclusive scan,
 //             the layout that the next step writes with.
 //   k_finish  swap buffers, advance the step.
-// Per particle all arithmetic is FP32; FP64 is used once per cell (sums
-// after the warp reduction, the stress tensor, the Cholesky factor, the
-// conservation factors), because FP64 issue rate is scarce on GB300.
+// Per particle all arithmetic is FP32.  FP64 is used per cell in k_params_f
+// (one cell per thread): the promotion of the moment sums, the stress
+// tensor, Eq. 33 and the Cholesky factor.  FP64 issue rate is scarce on
+// GB300 and an FP64 instruction costs about as much for one lane as for a
+// whole warp, so the warp-per-cell kernels keep their per-cell arithmetic
+// in FP32: moments are two-pass sums about the cell mean and the
+// conservation factors use sums about the cell mean, so neither cancels.
 // Each particle is read once and written once by k_g2 and its velocity is
 // read once more by k_g1.
 #include "usp_device.cuh"
@@ -437,22 +442,23 @@ __device__ void g2_cell(const SimDev& s, int cell, int p, uint32_t step, bool pe
         if (nr >= 2.0f) {
             a0 = warp_sumf(a0); a1 = warp_sumf(a1); a2 = warp_sumf(a2); ae = warp_sumf(ae);
             b0 = warp_sumf(b0); b1 = warp_sumf(b1); b2 = warp_sumf(b2); be = warp_sumf(be);
-            // FP64 on one lane only (the FP64 pipe is narrow), then broadcast
+            // FP32: the sums are taken about the cell mean, so the differences
+            // below do not cancel; an FP64 instruction would cost a whole warp
             int ok = 0;
             if (lane == 0) {
-                const double inv = 1.0 / (double)nr;
-                const double Eo = (double)ae - ((double)a0 * a0 + (double)a1 * a1 + (double)a2 * a2) * inv;
-                const double En = (double)be - ((double)b0 * b0 + (double)b1 * b1 + (double)b2 * b2) * inv;
-                if (En > 0.0) {
+                const float inv = 1.0f / nr;
+                const float Eo = ae - (a0 * a0 + a1 * a1 + a2 * a2) * inv;
+                const float En = be - (b0 * b0 + b1 * b1 + b2 * b2) * inv;
+                if (En > 0.0f && Eo >= 0.0f) {
                     ok = 1;
-                    alpha = (float)sqrt(Eo / En);
-                    uo0 = (float)((double)f.u[0] + a0 * inv);
-                    uo1 = (float)((double)f.u[1] + a1 * inv);
-                    uo2 = (float)((double)f.u[2] + a2 * inv);
-                    mn0 = (float)(b0 * inv);
-                    mn1 = (float)(b1 * inv);
-                    mn2 = (float)(b2 * inv);
-                    atomicAdd(&s.dyn->counters[kCntRelaxed], (unsigned long long)nr);
+                    alpha = sqrtf(Eo / En);
+                    uo0 = f.u[0] + a0 * inv;
+                    uo1 = f.u[1] + a1 * inv;
+                    uo2 = f.u[2] + a2 * inv;
+                    mn0 = b0 * inv;
+                    mn1 = b1 * inv;
+                    mn2 = b2 * inv;
+                    atomicAdd(&s.dyn->counters[kCntRelaxed], (unsigned long long)(unsigned)nr);
                 }
             }
             apply = __shfl_sync(0xffffffffu, ok, 0) != 0;
@@ -629,13 +635,37 @@ __global__ void __launch_bounds__(256) k_g1(const SimDev* __restrict__ sims, con
             }
 #pragma unroll
             for (int k = 0; k < 12; ++k) S[k] = warp_sumf(S[k]);
-            if (lane == 0) {
-                s.mom[cell] = (double)n;
+            // FP32 sums only: their promotion to FP64 happens in k_params_f, one
+            // cell per thread (an FP64 instruction costs the same for one lane)
+            if (lane < 16) {
+                float v;
+                if (lane == 0) v = (float)n;
+                else if (lane <= 12) v = S[0];
+                else v = lane == 13 ? u0 : (lane == 14 ? u1 : u2);
+                // lanes 1..12 need S[lane - 1]: select without dynamic indexing
 #pragma unroll
-                for (int k = 0; k < 12; ++k) s.mom[(size_t)(k + 1) * K + cell] = (double)S[k];
-                s.ushift[cell] = u0;
-                s.ushift[(size_t)K + cell] = u1;
-                s.ushift[(size_t)2 * K + cell] = u2;
+                for (int k = 1; k < 12; ++k)
+                    if (lane == k + 1) v = S[k];
+                s.momf[(size_t)lane * K + cell] = v;
+            }
+            if (lane == 31) {
+                // local state of the cell for its neighbours' Kn_GLL (FP32)
+                float nn = (float)n * s.f_w, T = 0.0f, um = 0.0f, valid = 0.0f;
+                if (n >= 2) {
+                    const float inv2 = 1.0f / (float)n;
+                    const float d0 = S[0] * inv2, d1 = S[1] * inv2, d2 = S[2] * inv2;
+                    const float th = ((S[3] + S[4] + S[5]) * inv2 - (d0 * d0 + d1 * d1 + d2 * d2)) * (1.0f / 3.0f);
+                    if (th > 0.0f) {
+                        valid = 1.0f;
+                        T = th * s.f_inv_R;
+                        const float w0 = u0 + d0, w1 = u1 + d1, w2 = u2 + d2;
+                        um = sqrtf(w0 * w0 + w1 * w1 + w2 * w2);
+                    }
+                }
+                s.floc[cell] = nn;
+                s.floc[(size_t)K + cell] = T;
+                s.floc[(size_t)2 * K + cell] = um;
+                s.floc[(size_t)3 * K + cell] = valid;
             }
         }
     }
@@ -652,7 +682,7 @@ struct LocalF {
 
 __device__ __forceinline__ void local_f(const SimDev& s, int cell, LocalF& L, double* u, double* P, double* theta) {
     const int K = s.K;
-    const double* M = s.mom;
+    const float* M = s.momf;
     const int N = (int)M[cell];
     L.N = N;
     L.valid = 0;
@@ -662,7 +692,7 @@ __device__ __forceinline__ void local_f(const SimDev& s, int cell, LocalF& L, do
     if (N < 1) return;
     const double inv = 1.0 / N;
     const double d0 = M[K + cell] * inv, d1 = M[2 * K + cell] * inv, d2 = M[3 * K + cell] * inv;
-    const double uu[3] = {s.ushift[cell] + d0, s.ushift[K + cell] + d1, s.ushift[2 * K + cell] + d2};
+    const double uu[3] = {M[13 * K + cell] + d0, M[14 * K + cell] + d1, M[15 * K + cell] + d2};
     const double p0 = M[4 * K + cell] * inv - d0 * d0, p1 = M[5 * K + cell] * inv - d1 * d1,
                  p2 = M[6 * K + cell] * inv - d2 * d2;
     const double th = (p0 + p1 + p2) / 3.0;
@@ -680,6 +710,16 @@ __device__ __forceinline__ void local_f(const SimDev& s, int cell, LocalF& L, do
     if (!L.valid) return;
     L.T = (float)(th / s.R);
     L.umag = sqrtf((float)(uu[0] * uu[0] + uu[1] * uu[1] + uu[2] * uu[2]));
+}
+
+// neighbour state for the Kn_GLL stencil, written in FP32 by k_g1
+__device__ __forceinline__ void local_nb(const SimDev& s, int cell, LocalF& L) {
+    const int K = s.K;
+    L.n = s.floc[cell];
+    L.T = s.floc[(size_t)K + cell];
+    L.umag = s.floc[(size_t)2 * K + cell];
+    L.valid = s.floc[(size_t)3 * K + cell] != 0.0f;
+    L.N = 0;
 }
 
 __global__ void __launch_bounds__(128) k_params_f(const SimDev* __restrict__ sims, const int2* __restrict__ tiles,
@@ -728,11 +768,11 @@ __global__ void __launch_bounds__(128) k_params_f(const SimDev* __restrict__ sim
                         int m = neighbor(s, cell, axis, -1), p = neighbor(s, cell, axis, +1);
                         LocalF Lm, Lp;
                         if (m >= 0) {
-                            local_f(s, m, Lm, nullptr, nullptr, nullptr);
+                            local_nb(s, m, Lm);
                             if (!Lm.valid) m = -1;
                         }
                         if (p >= 0) {
-                            local_f(s, p, Lp, nullptr, nullptr, nullptr);
+                            local_nb(s, p, Lp);
                             if (!Lp.valid) p = -1;
                         }
                         const float Qm[3] = {Lm.n, Lm.T, Lm.umag}, Qp[3] = {Lp.n, Lp.T, Lp.umag};
@@ -756,20 +796,23 @@ __global__ void __launch_bounds__(128) k_params_f(const SimDev* __restrict__ sim
                 const double b = 1.0 - 1.0 / s.Pr;                                              // Eq. 6c
                 const double A00 = th + b * sig[0], A11 = th + b * sig[1], A22 = th + b * sig[2];
                 const double A10 = b * sig[3], A20 = b * sig[4], A21 = b * sig[5];
+                // Cholesky factor with reciprocal square roots (no FP64 divisions)
                 double l00 = 0, l10 = 0, l11 = 0, l20 = 0, l21 = 0, l22 = 0;
                 bool ok = A00 > 0.0;
                 if (ok) {
-                    l00 = sqrt(A00);
-                    l10 = A10 / l00;
-                    l20 = A20 / l00;
+                    const double r0 = rsqrt(A00);
+                    l00 = A00 * r0;
+                    l10 = A10 * r0;
+                    l20 = A20 * r0;
                     const double d1 = A11 - l10 * l10;
                     ok = d1 > 0.0;
                     if (ok) {
-                        l11 = sqrt(d1);
-                        l21 = (A21 - l20 * l10) / l11;
+                        const double r1 = rsqrt(d1);
+                        l11 = d1 * r1;
+                        l21 = (A21 - l20 * l10) * r1;
                         const double d2 = A22 - l20 * l20 - l21 * l21;
                         ok = d2 > 0.0;
-                        if (ok) l22 = sqrt(d2);
+                        if (ok) l22 = d2 * rsqrt(d2);
                     }
                 }
                 if (!ok) {
@@ -787,7 +830,7 @@ __global__ void __launch_bounds__(128) k_params_f(const SimDev* __restrict__ sim
                 pr[13] = pne;
                 pr[14] = 1.0f;
                 // heat flux from the third central moment of the shifted sums
-                const double* M = s.mom;
+                const float* M = s.momf;
                 const double inv = 1.0 / L.N;
                 const double d0 = M[K + cell] * inv, d1 = M[2 * K + cell] * inv, d2 = M[3 * K + cell] * inv;
                 const double m00 = M[4 * K + cell] * inv, m11 = M[5 * K + cell] * inv, m22 = M[6 * K + cell] * inv;
