@@ -321,12 +321,22 @@ struct Stage {
     unsigned char* sel;
 };
 
-template <int CAP>
+// bytes per staged particle: (x,) y, v0, v1, v2, id, relaxation flag
+template <int CAP, int DIM>
+__host__ __device__ constexpr int stage_bytes() {
+    return CAP * (DIM == 2 ? 25 : 21);
+}
+
+template <int CAP, int DIM>
 __device__ __forceinline__ Stage stage_of(unsigned char* base, int warp) {
-    unsigned char* w = base + (size_t)warp * CAP * 25;
+    float* f = (float*)(base + (size_t)warp * stage_bytes<CAP, DIM>());
     Stage S;
-    S.x = (float*)w;
-    S.y = S.x + CAP;
+    S.x = nullptr;
+    if (DIM == 2) {
+        S.x = f;
+        f += CAP;
+    }
+    S.y = f;
     S.v0 = S.y + CAP;
     S.v1 = S.v0 + CAP;
     S.v2 = S.v1 + CAP;
@@ -525,7 +535,7 @@ __global__ void __launch_bounds__(128, 4) k_g2(const SimDev* __restrict__ sims, 
     __shared__ SimDev sim_sh;
     __shared__ uint32_t spl_all[4][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const Stage S = stage_of<CAP>(g2_smem, warp);
+    const Stage S = stage_of<CAP, DIM>(g2_smem, warp);
     const int nt = *ntiles;
     for (int t = blockIdx.x; t < nt; t += gridDim.x) {
         const int2 tile = tiles[t];
@@ -598,6 +608,7 @@ __global__ void __launch_bounds__(256) k_g1(const SimDev* __restrict__ sims, con
             for (uint32_t ch = 0; ch < nch; ++ch) {
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
+                    if (ch * CH + r * 32 >= n) break;   // warp-uniform: no idle slots issued
                     const uint32_t j = ch * CH + r * 32 + lane;
                     v0[r] = v1[r] = v2[r] = 0.0f;
                     if (j < n) load(j, v0[r], v1[r], v2[r]);
@@ -618,6 +629,7 @@ __global__ void __launch_bounds__(256) k_g1(const SimDev* __restrict__ sims, con
             for (uint32_t ch = 0; ch < nch; ++ch) {
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
+                    if (ch * CH + r * 32 >= n) break;
                     const uint32_t j = ch * CH + r * 32 + lane;
                     if (nch > 1) {
                         v0[r] = v1[r] = v2[r] = 0.0f;
@@ -1040,7 +1052,7 @@ __global__ void k_finish_f(const SimDev* __restrict__ sims, int nsims, int mode)
 
 template <int CAP, int DIM, bool FLUSH>
 void launch_g2_one(const Launch& L) {
-    const int smem = 4 * CAP * 25;
+    const int smem = 4 * stage_bytes<CAP, DIM>();
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_g2<CAP, DIM, FLUSH>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -1078,18 +1090,18 @@ void fused_prepare_attributes() {
     static bool done = false;
     if (done) return;
     done = true;
-    cudaFuncSetAttribute(k_g2<128, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 128 * 25);
-    cudaFuncSetAttribute(k_g2<128, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 128 * 25);
-    cudaFuncSetAttribute(k_g2<256, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 256 * 25);
-    cudaFuncSetAttribute(k_g2<256, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 256 * 25);
-    cudaFuncSetAttribute(k_g2<512, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 512 * 25);
-    cudaFuncSetAttribute(k_g2<512, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 512 * 25);
-    cudaFuncSetAttribute(k_g2<128, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 128 * 25);
-    cudaFuncSetAttribute(k_g2<128, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 128 * 25);
-    cudaFuncSetAttribute(k_g2<256, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 256 * 25);
-    cudaFuncSetAttribute(k_g2<256, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 256 * 25);
-    cudaFuncSetAttribute(k_g2<512, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 512 * 25);
-    cudaFuncSetAttribute(k_g2<512, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 512 * 25);
+    cudaFuncSetAttribute(k_g2<128, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<128, 1>());
+    cudaFuncSetAttribute(k_g2<128, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<128, 2>());
+    cudaFuncSetAttribute(k_g2<256, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<256, 1>());
+    cudaFuncSetAttribute(k_g2<256, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<256, 2>());
+    cudaFuncSetAttribute(k_g2<512, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<512, 1>());
+    cudaFuncSetAttribute(k_g2<512, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<512, 2>());
+    cudaFuncSetAttribute(k_g2<128, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<128, 1>());
+    cudaFuncSetAttribute(k_g2<128, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<128, 2>());
+    cudaFuncSetAttribute(k_g2<256, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<256, 1>());
+    cudaFuncSetAttribute(k_g2<256, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<256, 2>());
+    cudaFuncSetAttribute(k_g2<512, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<512, 1>());
+    cudaFuncSetAttribute(k_g2<512, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<512, 2>());
     cudaGetLastError();
 }
 
