@@ -608,7 +608,6 @@ __global__ void __launch_bounds__(256) k_g1(const SimDev* __restrict__ sims, con
             for (uint32_t ch = 0; ch < nch; ++ch) {
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    if (ch * CH + r * 32 >= n) break;   // warp-uniform: no idle slots issued
                     const uint32_t j = ch * CH + r * 32 + lane;
                     v0[r] = v1[r] = v2[r] = 0.0f;
                     if (j < n) load(j, v0[r], v1[r], v2[r]);
@@ -629,7 +628,6 @@ __global__ void __launch_bounds__(256) k_g1(const SimDev* __restrict__ sims, con
             for (uint32_t ch = 0; ch < nch; ++ch) {
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    if (ch * CH + r * 32 >= n) break;
                     const uint32_t j = ch * CH + r * 32 + lane;
                     if (nch > 1) {
                         v0[r] = v1[r] = v2[r] = 0.0f;
