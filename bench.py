@@ -54,7 +54,7 @@ def parse():
 def workload_cfg(batch, pipeline):
     return {"workload": "sod_shock_tube_batch", "cells": 1000, "ppc_left": 360, "ppc_right": 45,
             "particles_per_tube": 202500, "global_batch": batch, "Kn": 1e-4, "dt_over_tauc": 10.0,
-            "storage": "fp32", "moments": "fp64", "pipeline": pipeline,
+            "storage": "fp32", "moments": "fp32 centred sums, fp64 per-cell parameters", "pipeline": pipeline,
             "l2": "state larger than L2 (no flush)", "parallelism": "replicas"}
 
 
