@@ -28,6 +28,7 @@
 // read once more by k_g1.
 #include "usp_device.cuh"
 
+
 namespace usp {
 
 namespace {
@@ -140,23 +141,6 @@ __device__ __forceinline__ Src src_of(const SimDev& s, int b) {
     return P;
 }
 
-template <int DIM>
-__device__ __forceinline__ void load_src(const Src& P, const SimDev& s, int b, uint32_t base, uint32_t nb,
-                                         const uint32_t* spl, uint32_t j, float& x, float& y, float& v0, float& v1,
-                                         float& v2, uint32_t& id) {
-    if (j < nb) {
-        const uint32_t i = base + j;
-        if (DIM == 2) x = P.x[i];
-        y = P.y[i];
-        v0 = P.v0[i];
-        v1 = P.v1[i];
-        v2 = P.v2[i];
-        id = P.id[i];
-    } else {
-        load_particle<DIM>(s, b, base, nb, spl, j, x, y, v0, v1, v2, id);
-    }
-}
-
 // per-cell constants of the time-instant draw (Eq. 30)
 struct TimeDraw {
     float dt, a, em1, ema, inv_nues;
@@ -183,12 +167,19 @@ __device__ __forceinline__ void es_draw_f(const uint2 key, const FCell& f, const
 // ---------------------------------------------------------------------------
 // k_g2: pending relaxation + advection + bucket scatter (FLUSH: relaxation only)
 //
-// One warp per cell.  The cell's particles are staged in a per-warp shared
-// memory area of CAP entries and every pass walks them with a rolled loop, so
-// that the per-particle code (two Philox draws, the ES sample, advection)
-// appears once in the binary.  Cells above CAP particles are processed in
-// chunks: the conservation sums in a first sweep, the update in a second
-// sweep that redraws the same counter-based random numbers.
+// One warp per cell.  The cell's particles are copied (cp.async, the whole
+// cell at once) into a per-warp shared memory area of CAP entries and every
+// pass walks them with a rolled loop, so that the per-particle code (two
+// Philox draws, the ES sample, advection) appears once in the binary:
+//   stage    relaxation draws, conservation sums;
+//   pass A   conservation, advection, destination cell, arrivals counted per
+//            slot of the cell's destination window;
+//   pass B   one atomic reservation per occupied slot in the destination
+//            buckets (a single round trip for the whole cell);
+//   pass C   rank within the slot, write.
+// Cells above CAP particles are processed in chunks: the conservation sums in
+// a first sweep, the update in a second sweep that redraws the same
+// counter-based random numbers.
 // ---------------------------------------------------------------------------
 __device__ __noinline__ bool advect_slow(const SimDev& s, uint32_t step, uint32_t pid, float& x, float& y, float* c) {
     return advect<float>(s, step, pid, x, y, c);
@@ -345,9 +336,43 @@ __device__ __forceinline__ Stage stage_of(unsigned char* base, int warp) {
     return S;
 }
 
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Destination window of a cell: the 64 cells that its particles can reach in
+// one step without leaving it (1-D: offsets -32..31; 2-D: an 8 x 8 block
+// around the cell).  The warp counts its arrivals per window slot in shared
+// memory, reserves each slot's range in the destination bucket with one
+// global atomic, then writes; particles that land outside the window reserve
+// their place one group at a time.
+constexpr int kWin = 64;
+constexpr unsigned char kSlotNone = 0xFF;   // removed, nothing to write
+constexpr unsigned char kSlotFar = 0xFE;    // outside the window
+
+template <int DIM>
+__device__ __forceinline__ int win_slot(int dc, int cell, int cx, int cy, int nx) {
+    if (DIM == 1) {
+        const int o = dc - cell + 32;
+        return (o >= 0 && o < kWin) ? o : -1;
+    }
+    const int iy = dc / nx, ix = dc - iy * nx;
+    const int oy = iy - cy + 4, ox = ix - cx + 4;
+    return (oy >= 0 && oy < 8 && ox >= 0 && ox < 8) ? oy * 8 + ox : -1;
+}
+
+template <int DIM>
+__device__ __forceinline__ int win_cell(int k, int cell, int cx, int cy, int nx) {
+    if (DIM == 1) return cell + k - 32;
+    return (cy + (k >> 3) - 4) * nx + (cx + (k & 7) - 4);
+}
+
 template <int CAP, int DIM, bool FLUSH>
 __device__ void g2_cell(const SimDev& s, int cell, int p, uint32_t step, bool pending, uint32_t* spl, const Stage& S,
-                        int lane) {
+                        uint32_t* win, int lane) {
     const uint32_t base = s.lay[p][cell];
     const uint32_t top = min(s.lay[p][cell + 1], (uint32_t)s.cap);
     const uint32_t capc = top > base ? top - base : 0u;
@@ -373,24 +398,50 @@ __device__ void g2_cell(const SimDev& s, int cell, int p, uint32_t step, bool pe
     const uint2 key = make_uint2(s.key0, s.key1);
     const bool eager = f.pr > 0.5f;
 
-    // stage chunk ch; if `draw_new`, relaxed particles get their new peculiar
-    // velocity in v0..v2 (flag in sel); if `sums`, accumulate the conservation sums
+    // stage chunk ch: the particles are copied into the staging planes
+    // (asynchronously from the bucket, directly from the spill list), then
+    // relaxed particles get their new peculiar velocity in v0..v2 and their
+    // flag in sel; if `sums`, the conservation sums are accumulated
     float a0 = 0, a1 = 0, a2 = 0, ae = 0, b0 = 0, b1 = 0, b2 = 0, be = 0, nr = 0;
     auto stage_chunk = [&](uint32_t ch, bool sums) -> uint32_t {
         const uint32_t off = ch * CAP;
         const uint32_t m = min((uint32_t)CAP, n - off);
+        const uint32_t mb = off < nb ? min(m, nb - off) : 0u;
+        __syncwarp();
+#pragma unroll 1
+        for (uint32_t j = lane; j < mb; j += 32) {
+            const uint32_t i = base + off + j;
+            if (DIM == 2) cp_async4(S.x + j, P.x + i);
+            cp_async4(S.y + j, P.y + i);
+            cp_async4(S.v0 + j, P.v0 + i);
+            cp_async4(S.v1 + j, P.v1 + i);
+            cp_async4(S.v2 + j, P.v2 + i);
+            cp_async4(S.id + j, P.id + i);
+        }
+#pragma unroll 1
+        for (uint32_t j = mb + lane; j < m; j += 32) {
+            float x = 0.0f, y, v0, v1, v2;
+            uint32_t id;
+            load_particle<DIM>(s, p, base, nb, spl, off + j, x, y, v0, v1, v2, id);
+            if (DIM == 2) S.x[j] = x;
+            S.y[j] = y; S.v0[j] = v0; S.v1[j] = v1; S.v2[j] = v2; S.id[j] = id;
+        }
+        cp_async_wait_all();
         __syncwarp();
 #pragma unroll 1
         for (uint32_t j0 = lane; j0 < m; j0 += 64) {
             const uint32_t j1 = j0 + 32;
             const bool has1 = j1 < m;
-            float x0 = 0.0f, y0, p0, q0, r0;
-            float x1 = 0.0f, y1 = 0.0f, p1 = 0.0f, q1 = 0.0f, r1 = 0.0f;
-            uint32_t id0, id1 = 0;
-            load_src<DIM>(P, s, p, base, nb, spl, off + j0, x0, y0, p0, q0, r0, id0);
-            if (has1) load_src<DIM>(P, s, p, base, nb, spl, off + j1, x1, y1, p1, q1, r1, id1);
             unsigned char s0 = 0, s1 = 0;
             if (relax) {
+                const float p0 = S.v0[j0], q0 = S.v1[j0], r0 = S.v2[j0];
+                const uint32_t id0 = S.id[j0];
+                float p1 = 0.0f, q1 = 0.0f, r1 = 0.0f;
+                uint32_t id1 = 0;
+                if (has1) {
+                    p1 = S.v0[j1]; q1 = S.v1[j1]; r1 = S.v2[j1];
+                    id1 = S.id[j1];
+                }
                 const uint4 w0 = philox(make_uint4(id0, step, kRelax, 0), key);
                 const uint4 w1 = philox(make_uint4(id1, step, kRelax, 0), key);
                 // when most particles relax, draw the second counter of both up
@@ -415,7 +466,7 @@ __device__ void g2_cell(const SimDev& s, int cell, int p, uint32_t step, bool pe
                             be += C0[0] * C0[0] + C0[1] * C0[1] + C0[2] * C0[2];
                             nr += 1.0f;
                         }
-                        p0 = C0[0]; q0 = C0[1]; r0 = C0[2];
+                        S.v0[j0] = C0[0]; S.v1[j0] = C0[1]; S.v2[j0] = C0[2];
                     }
                     if (s1) {
                         if (sums) {
@@ -426,16 +477,12 @@ __device__ void g2_cell(const SimDev& s, int cell, int p, uint32_t step, bool pe
                             be += C1[0] * C1[0] + C1[1] * C1[1] + C1[2] * C1[2];
                             nr += 1.0f;
                         }
-                        p1 = C1[0]; q1 = C1[1]; r1 = C1[2];
+                        S.v0[j1] = C1[0]; S.v1[j1] = C1[1]; S.v2[j1] = C1[2];
                     }
                 }
             }
-            if (DIM == 2) S.x[j0] = x0;
-            S.y[j0] = y0; S.v0[j0] = p0; S.v1[j0] = q0; S.v2[j0] = r0; S.id[j0] = id0; S.sel[j0] = s0;
-            if (has1) {
-                if (DIM == 2) S.x[j1] = x1;
-                S.y[j1] = y1; S.v0[j1] = p1; S.v1[j1] = q1; S.v2[j1] = r1; S.id[j1] = id1; S.sel[j1] = s1;
-            }
+            S.sel[j0] = s0;
+            if (has1) S.sel[j1] = s1;
         }
         __syncwarp();
         return m;
@@ -444,7 +491,7 @@ __device__ void g2_cell(const SimDev& s, int cell, int p, uint32_t step, bool pe
     uint32_t m_last = 0;
     for (uint32_t ch = 0; ch < nch; ++ch) m_last = stage_chunk(ch, true);
 
-    // conservation factors of the cell (FP64 once per cell)
+    // conservation factors of the cell
     bool apply = false;
     float uo0 = 0, uo1 = 0, uo2 = 0, mn0 = 0, mn1 = 0, mn2 = 0, alpha = 1;
     if (relax) {
@@ -482,47 +529,140 @@ __device__ void g2_cell(const SimDev& s, int cell, int p, uint32_t step, bool pe
         }
     }
 
+    // the relaxed velocity of staged particle j (conservation applied), or
+    // its old velocity when the cell had a single relaxed particle
+    auto final_velocity = [&](uint32_t off, uint32_t j, float* c) {
+        c[0] = S.v0[j];
+        c[1] = S.v1[j];
+        c[2] = S.v2[j];
+        if (S.sel[j]) {
+            if (apply) {
+                c[0] = uo0 + alpha * (c[0] - mn0);
+                c[1] = uo1 + alpha * (c[1] - mn1);
+                c[2] = uo2 + alpha * (c[2] - mn2);
+            } else {
+                float ox, oy;
+                uint32_t oid;
+                load_particle<DIM>(s, p, base, nb, spl, off + j, ox, oy, c[0], c[1], c[2], oid);
+            }
+        }
+    };
+
+    if (FLUSH) {
+        for (uint32_t ch = 0; ch < nch; ++ch) {
+            const uint32_t m = nch > 1 ? stage_chunk(ch, false) : m_last;
+            const uint32_t off = ch * CAP;
+#pragma unroll 1
+            for (uint32_t j = lane; j < m; j += 32) {
+                if (!(S.sel[j] && apply)) continue;
+                float c[3];
+                final_velocity(off, j, c);
+                store_velocity<DIM>(s, p, base, nb, spl, off + j, c[0], c[1], c[2]);
+            }
+        }
+        __syncwarp();
+        return;
+    }
+
     Ctx C;
     make_ctx(s, q, C);
+    const int cy = DIM == 2 ? cell / C.nx : 0;
+    const int cx = DIM == 2 ? cell - cy * C.nx : 0;
+    uint32_t* wcnt = win;          // arrivals per window slot, then the running rank
+    uint32_t* wbase = win + kWin;  // reserved start of each slot in its bucket
     for (uint32_t ch = 0; ch < nch; ++ch) {
         const uint32_t m = nch > 1 ? stage_chunk(ch, false) : m_last;
         const uint32_t off = ch * CAP;
+        for (int k = lane; k < kWin; k += 32) wcnt[k] = 0;
+        __syncwarp();
+        // pass A: conservation, advection, destination slot; count per slot
 #pragma unroll 1
         for (uint32_t b = 0; b < m; b += 32) {
             const uint32_t j = b + lane;
-            const bool valid = j < m;
-            float x = 0.0f, y = 0.0f, c[3] = {0.0f, 0.0f, 0.0f};
-            uint32_t id = 0;
-            if (valid) {
+            int slot = -2;   // -2: nothing to count
+            if (j < m) {
+                float x = DIM == 2 ? S.x[j] : 0.0f, y = S.y[j], c[3];
+                final_velocity(off, j, c);
+                unsigned char ws = kSlotNone;
+                if (advect_fast<DIM>(s, C, step, S.id[j], x, y, c)) {
+                    const int dc = cell_f<DIM>(C, x, y);
+                    if (!C.reservoir || !in_buffer(s, dc)) {
+                        slot = win_slot<DIM>(dc, cell, cx, cy, C.nx);
+                        ws = slot >= 0 ? (unsigned char)slot : kSlotFar;
+                    } else {
+                        atomicAdd(&s.dyn->counters[kCntRemoved], 1ull);
+                    }
+                }
+                if (DIM == 2) S.x[j] = x;
+                S.y[j] = y; S.v0[j] = c[0]; S.v1[j] = c[1]; S.v2[j] = c[2];
+                S.sel[j] = ws;
+            }
+            const unsigned grp = __match_any_sync(0xffffffffu, slot);
+            if (slot >= 0 && lane == __ffs(grp) - 1) wcnt[slot] += (uint32_t)__popc(grp);
+            __syncwarp();
+        }
+        // pass B: one reservation per occupied slot, all in flight together
+        for (int k = lane; k < kWin; k += 32) {
+            const uint32_t cnt = wcnt[k];
+            if (cnt) wbase[k] = atomicAdd(&C.dcnt[win_cell<DIM>(k, cell, cx, cy, C.nx)], cnt);
+            wcnt[k] = 0;
+        }
+        __syncwarp();
+        // pass C: rank within the slot, write into the destination bucket
+#pragma unroll 1
+        for (uint32_t b = 0; b < m; b += 32) {
+            const uint32_t j = b + lane;
+            const unsigned char ws = j < m ? S.sel[j] : kSlotNone;
+            float x = 0.0f, y = 0.0f;
+            int dc = -1;
+            if (ws != kSlotNone) {
                 if (DIM == 2) x = S.x[j];
                 y = S.y[j];
-                c[0] = S.v0[j];
-                c[1] = S.v1[j];
-                c[2] = S.v2[j];
-                id = S.id[j];
-                if (S.sel[j]) {
-                    if (apply) {
-                        c[0] = uo0 + alpha * (c[0] - mn0);
-                        c[1] = uo1 + alpha * (c[1] - mn1);
-                        c[2] = uo2 + alpha * (c[2] - mn2);
-                    } else {   // a lone relaxed particle keeps its old velocity
-                        float ox, oy;
-                        uint32_t oid;
-                        load_particle<DIM>(s, p, base, nb, spl, off + j, ox, oy, c[0], c[1], c[2], oid);
+                dc = cell_f<DIM>(C, x, y);
+            }
+            const int gkey = ws == kSlotNone ? -1 : (ws == kSlotFar ? dc : (int)(0x40000000 | ws));
+            const unsigned grp = __match_any_sync(0xffffffffu, gkey);
+            if (gkey >= 0) {
+                const int leader = __ffs(grp) - 1;
+                uint32_t r0 = 0;
+                if (lane == leader) {
+                    if (ws != kSlotFar) {
+                        r0 = wbase[ws] + wcnt[ws];
+                        wcnt[ws] += (uint32_t)__popc(grp);
+                    } else {
+                        r0 = atomicAdd(&C.dcnt[dc], (uint32_t)__popc(grp));
+                    }
+                }
+                const uint32_t rank = __shfl_sync(grp, r0, leader) + (uint32_t)__popc(grp & lanemask_lt());
+                const uint32_t lo = C.dlay[dc];
+                const uint32_t hi = min(C.dlay[dc + 1], C.cap);
+                const float v0 = S.v0[j], v1 = S.v1[j], v2 = S.v2[j];
+                const uint32_t id = S.id[j];
+                if (lo + rank < hi) {
+                    const uint32_t i = lo + rank;
+                    if (DIM == 2) C.dx_[i] = x;
+                    C.dy_[i] = y;
+                    C.dv0[i] = v0;
+                    C.dv1[i] = v1;
+                    C.dv2[i] = v2;
+                    C.did[i] = id;
+                } else {
+                    const uint32_t k = atomicAdd(&s.dyn->sp_n[q], 1u);
+                    atomicAdd(&s.dyn->counters[kCntSpilled], 1ull);
+                    if (k < (uint32_t)kSpillCap) {
+                        if (DIM == 2) s.sp_pos[q][0][k] = x;
+                        s.sp_pos[q][1][k] = y;
+                        s.sp_vel[q][0][k] = v0;
+                        s.sp_vel[q][1][k] = v1;
+                        s.sp_vel[q][2][k] = v2;
+                        s.sp_pid[q][k] = id;
+                        s.sp_cell[q][k] = (uint32_t)dc;
+                    } else {
+                        atomicAdd(&s.dyn->counters[kCntOverflow], 1ull);
                     }
                 }
             }
-            if (FLUSH) {
-                if (valid && S.sel[j] && apply) store_velocity<DIM>(s, p, base, nb, spl, off + j, c[0], c[1], c[2]);
-                continue;
-            }
-            uint32_t key = kNoCell;
-            if (valid && advect_fast<DIM>(s, C, step, id, x, y, c)) {
-                const int dc = cell_f<DIM>(C, x, y);
-                if (!C.reservoir || !in_buffer(s, dc)) key = (uint32_t)dc;
-                else atomicAdd(&s.dyn->counters[kCntRemoved], 1ull);
-            }
-            emit_c<DIM>(s, C, q, key, x, y, c[0], c[1], c[2], id, lane);
+            __syncwarp();
         }
     }
     __syncwarp();
@@ -534,6 +674,7 @@ __global__ void __launch_bounds__(128, 4) k_g2(const SimDev* __restrict__ sims, 
     extern __shared__ __align__(16) unsigned char g2_smem[];
     __shared__ SimDev sim_sh;
     __shared__ uint32_t spl_all[4][32];
+    __shared__ uint32_t win_all[4][2 * kWin];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const Stage S = stage_of<CAP, DIM>(g2_smem, warp);
     const int nt = *ntiles;
@@ -551,7 +692,7 @@ __global__ void __launch_bounds__(128, 4) k_g2(const SimDev* __restrict__ sims, 
         for (int cc = warp; cc < kCTile; cc += 4) {
             const int cell = tile.y + cc;
             if (cell >= s.K) break;
-            g2_cell<CAP, DIM, FLUSH>(s, cell, p, step, pending, spl_all[warp], S, lane);
+            g2_cell<CAP, DIM, FLUSH>(s, cell, p, step, pending, spl_all[warp], S, win_all[warp], lane);
         }
     }
 }
