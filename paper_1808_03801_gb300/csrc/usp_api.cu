@@ -54,7 +54,7 @@ struct usp_handle {
     size_t cell_bytes = 0, part_bytes = 0;
     int2* d_ptiles = nullptr;
     int2* d_ctiles = nullptr;
-    int* d_ntiles = nullptr;          // [0] particle tiles, [1] cell tiles
+    int* d_ntiles = nullptr;          // [0] particle tiles, [1] cell tiles, [2..3] k_g2 work queue
     int nptiles = 0, nctiles = 0;
     Graphs graphs;
     bool initialised = false;
@@ -147,6 +147,7 @@ static Launch make_launch(usp_handle* h) {
     L.nptiles = h->d_ntiles;
     L.ctiles = h->d_ctiles;
     L.nctiles = h->d_ntiles + 1;
+    L.wq = (uint32_t*)(h->d_ntiles + 2);
     L.nsims = 1;
     L.dims = h->host.dim == 1 ? 1 : 2;
     L.grid_p = persistent_grid(h->nptiles, h->grid_per_sm);
@@ -374,7 +375,7 @@ extern "C" int usp_create(const usp_gas* gas, const usp_grid* grid, const usp_bc
     if ((rc = cell_alloc(h, sizeof(SimDyn), &p)) != 0) { usp_destroy(h); return rc; }
     h->d_dyn = (SimDyn*)p;
     s.dyn = h->d_dyn;
-    if ((rc = cell_alloc(h, 2 * sizeof(int), &p)) != 0) { usp_destroy(h); return rc; }
+    if ((rc = cell_alloc(h, 4 * sizeof(int), &p)) != 0) { usp_destroy(h); return rc; }
     h->d_ntiles = (int*)p;
     h->nctiles = (K + kCTile - 1) / kCTile;
     if ((rc = cell_alloc(h, sizeof(int2) * (size_t)h->nctiles, &p)) != 0) { usp_destroy(h); return rc; }
@@ -399,7 +400,7 @@ extern "C" int usp_create(const usp_gas* gas, const usp_grid* grid, const usp_bc
     s.inj_total = total;
     std::vector<int2> ct(h->nctiles);
     for (int t = 0; t < h->nctiles; ++t) ct[t] = make_int2(0, t * kCTile);
-    int nt[2] = {0, h->nctiles};
+    int nt[4] = {0, h->nctiles, 0, 0};
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = cudaMemcpyAsync(s.inj_count, h->inj_count_host.data(), sizeof(uint32_t) * K, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(s.inj_pidoff, off.data(), sizeof(uint32_t) * K, cudaMemcpyHostToDevice, h->stream);
@@ -993,9 +994,11 @@ extern "C" int usp_batch_create(size_t hbm_budget, int max_sims, void* stream, u
         b->own_stream = true;
     }
     if (cudaMalloc(&b->d_sims, sizeof(SimDev) * max_sims) != cudaSuccess ||
-        cudaMalloc(&b->d_ntiles, 2 * sizeof(int)) != cudaSuccess) {
+        cudaMalloc(&b->d_ntiles, 4 * sizeof(int)) != cudaSuccess ||
+        cudaMemsetAsync(b->d_ntiles, 0, 4 * sizeof(int), b->stream) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(b->d_sims);
+        cudaFree(b->d_ntiles);
         if (b->own_stream) cudaStreamDestroy(b->stream);
         delete b;
         return USP_ERR_OOM;
@@ -1110,6 +1113,7 @@ static Launch batch_launch(usp_batch* b) {
     L.nptiles = b->d_ntiles;
     L.ctiles = b->d_ctiles;
     L.nctiles = b->d_ntiles + 1;
+    L.wq = (uint32_t*)(b->d_ntiles + 2);
     L.nsims = (int)b->members.size();
     L.dims = 0;
     for (auto* h : b->members) L.dims |= h->host.dim == 1 ? 1 : 2;

@@ -668,31 +668,58 @@ __device__ void g2_cell(const SimDev& s, int cell, int p, uint32_t step, bool pe
     __syncwarp();
 }
 
+// copy one simulation descriptor into shared memory (one warp)
+__device__ __forceinline__ void load_sim_warp(SimDev& dst, const SimDev& src, int lane) {
+    const int4* a = reinterpret_cast<const int4*>(&src);
+    int4* b = reinterpret_cast<int4*>(&dst);
+    for (int i = lane; i < (int)(sizeof(SimDev) / 16); i += 32) b[i] = a[i];
+}
+
+// Cells are handed out one at a time from a queue (wq[0]: next cell of the
+// batch's cell-tile list, wq[1]: warps that found it empty), so that a few
+// dense cells at the end of the list do not leave the other SMs idle.  The
+// last warp to leave resets the queue for the next launch.
 template <int CAP, int DIM, bool FLUSH>
 __global__ void __launch_bounds__(128, 4) k_g2(const SimDev* __restrict__ sims, const int2* __restrict__ tiles,
-                                            const int* __restrict__ ntiles) {
+                                            const int* __restrict__ ntiles, uint32_t* __restrict__ wq) {
     extern __shared__ __align__(16) unsigned char g2_smem[];
-    __shared__ SimDev sim_sh;
+    __shared__ SimDev sim_w[4];
     __shared__ uint32_t spl_all[4][32];
     __shared__ uint32_t win_all[4][2 * kWin];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const Stage S = stage_of<CAP, DIM>(g2_smem, warp);
-    const int nt = *ntiles;
-    for (int t = blockIdx.x; t < nt; t += gridDim.x) {
-        const int2 tile = tiles[t];
-        __syncthreads();
-        load_sim(sim_sh, sims[tile.x]);
-        __syncthreads();
-        const SimDev& s = sim_sh;
-        if (s.dim != DIM) continue;
-        const int p = s.dyn->cur;
-        const uint32_t step = s.dyn->step;
-        const bool pending = s.dyn->relax_pending != 0;
-        if (FLUSH && !pending) continue;
-        for (int cc = warp; cc < kCTile; cc += 4) {
-            const int cell = tile.y + cc;
-            if (cell >= s.K) break;
-            g2_cell<CAP, DIM, FLUSH>(s, cell, p, step, pending, spl_all[warp], S, win_all[warp], lane);
+    const uint32_t total = (uint32_t)*ntiles * kCTile;
+    SimDev& s = sim_w[warp];
+    int cur_sim = -1;
+    uint32_t g = 0;
+    if (lane == 0) g = atomicAdd(&wq[0], 1u);
+    g = __shfl_sync(0xffffffffu, g, 0);
+    while (g < total) {
+        uint32_t gn = 0;   // the next cell, requested while this one is processed
+        if (lane == 0) gn = atomicAdd(&wq[0], 1u);
+        const int2 tile = tiles[g / kCTile];
+        const int cell = tile.y + (int)(g % kCTile);
+        if (tile.x != cur_sim) {
+            __syncwarp();
+            load_sim_warp(s, sims[tile.x], lane);
+            __syncwarp();
+            cur_sim = tile.x;
+        }
+        if (s.dim == DIM && cell < s.K) {
+            const int p = s.dyn->cur;
+            const uint32_t step = s.dyn->step;
+            const bool pending = s.dyn->relax_pending != 0;
+            if (!FLUSH || pending)
+                g2_cell<CAP, DIM, FLUSH>(s, cell, p, step, pending, spl_all[warp], S, win_all[warp], lane);
+        }
+        g = __shfl_sync(0xffffffffu, gn, 0);
+    }
+    if (lane == 0) {
+        __threadfence();
+        const uint32_t done = atomicAdd(&wq[1], 1u);
+        if (done == gridDim.x * (blockDim.x / 32) - 1) {
+            wq[0] = 0;
+            wq[1] = 0;
         }
     }
 }
@@ -1197,7 +1224,7 @@ void launch_g2_one(const Launch& L) {
         cudaFuncSetAttribute(k_g2<CAP, DIM, FLUSH>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         attr = true;
     }
-    k_g2<CAP, DIM, FLUSH><<<L.grid_c, 128, smem, L.stream>>>(L.sims, L.ctiles, L.nctiles);
+    k_g2<CAP, DIM, FLUSH><<<L.grid_c, 128, smem, L.stream>>>(L.sims, L.ctiles, L.nctiles, L.wq);
 }
 
 template <int CAP, bool FLUSH>
