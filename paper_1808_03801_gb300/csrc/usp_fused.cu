@@ -40,21 +40,6 @@ struct FCell {
     int valid;
 };
 
-__device__ __forceinline__ void load_fcell(const SimDev& s, int c, FCell& f) {
-    const float* P = s.fprm;
-    const int K = s.K;
-#pragma unroll
-    for (int d = 0; d < 3; ++d) f.u[d] = P[(size_t)d * K + c];
-    f.th = P[(size_t)3 * K + c];
-#pragma unroll
-    for (int d = 0; d < 6; ++d) f.L[d] = P[(size_t)(4 + d) * K + c];
-    f.pr = P[(size_t)10 * K + c];
-    f.nu = P[(size_t)11 * K + c];
-    f.nues = P[(size_t)12 * K + c];
-    f.pne = P[(size_t)13 * K + c];
-    f.valid = P[(size_t)14 * K + c] != 0.0f;
-}
-
 __device__ __forceinline__ float warp_sumf(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -370,20 +355,48 @@ __device__ __forceinline__ int win_cell(int k, int cell, int cx, int cy, int nx)
     return (cy + (k >> 3) - 4) * nx + (cx + (k & 7) - 4);
 }
 
+// Per-warp copy of the header of one cell: bucket bounds, arrivals and the
+// FP32 relaxation parameters, fetched with one round of cp.async (one word
+// per lane) instead of two dependent rounds of loads.
+constexpr int kHdrPrm = 15;   // u[3], theta, L[6], P_relax, nu, nu_ES, P_ne, valid
+
+struct Hdr {
+    uint32_t lay[2];
+    uint32_t cnt;
+    float prm[kHdrPrm];
+};
+
+__device__ __forceinline__ void fetch_hdr(const SimDev& s, int p, int cell, Hdr& H, int lane) {
+    if (lane < 2) cp_async4(&H.lay[lane], s.lay[p] + cell + lane);
+    else if (lane == 2) cp_async4(&H.cnt, s.cnt[p] + cell);
+    else if (lane < 3 + kHdrPrm) cp_async4(&H.prm[lane - 3], s.fprm + (size_t)(lane - 3) * s.K + cell);
+    cp_async_wait_all();
+    __syncwarp();
+}
+
 template <int CAP, int DIM, bool FLUSH>
-__device__ void g2_cell(const SimDev& s, int cell, int p, uint32_t step, bool pending, uint32_t* spl, const Stage& S,
-                        uint32_t* win, int lane) {
-    const uint32_t base = s.lay[p][cell];
-    const uint32_t top = min(s.lay[p][cell + 1], (uint32_t)s.cap);
+__device__ void g2_cell(const SimDev& s, int cell, const Hdr& H, int p, uint32_t step, bool pending, uint32_t* spl,
+                        const Stage& S, uint32_t* win, int lane) {
+    const uint32_t base = H.lay[0];
+    const uint32_t top = min(H.lay[1], (uint32_t)s.cap);
     const uint32_t capc = top > base ? top - base : 0u;
-    const uint32_t arrived = s.cnt[p][cell];
+    const uint32_t arrived = H.cnt;
     const uint32_t nb = min(arrived, capc);
     uint32_t nsp = 0;
     if (arrived > nb) nsp = collect_spill(s, p, cell, spl, lane);
     const uint32_t n = nb + nsp;
     if (n == 0) return;
     FCell f;
-    load_fcell(s, cell, f);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) f.u[d] = H.prm[d];
+    f.th = H.prm[3];
+#pragma unroll
+    for (int d = 0; d < 6; ++d) f.L[d] = H.prm[4 + d];
+    f.pr = H.prm[10];
+    f.nu = H.prm[11];
+    f.nues = H.prm[12];
+    f.pne = H.prm[13];
+    f.valid = H.prm[14] != 0.0f;
     const bool relax = pending && f.valid;
     if (FLUSH && !relax) return;
     TimeDraw td;
@@ -568,8 +581,9 @@ __device__ void g2_cell(const SimDev& s, int cell, int p, uint32_t step, bool pe
     make_ctx(s, q, C);
     const int cy = DIM == 2 ? cell / C.nx : 0;
     const int cx = DIM == 2 ? cell - cy * C.nx : 0;
-    uint32_t* wcnt = win;          // arrivals per window slot, then the running rank
-    uint32_t* wbase = win + kWin;  // reserved start of each slot in its bucket
+    uint32_t* wcnt = win;              // arrivals per window slot, then the running rank
+    uint32_t* wstart = win + kWin;     // first reserved index of each slot in its bucket
+    uint32_t* wend = win + 2 * kWin;   // end of that bucket
     for (uint32_t ch = 0; ch < nch; ++ch) {
         const uint32_t m = nch > 1 ? stage_chunk(ch, false) : m_last;
         const uint32_t off = ch * CAP;
@@ -601,10 +615,16 @@ __device__ void g2_cell(const SimDev& s, int cell, int p, uint32_t step, bool pe
             if (slot >= 0 && lane == __ffs(grp) - 1) wcnt[slot] += (uint32_t)__popc(grp);
             __syncwarp();
         }
-        // pass B: one reservation per occupied slot, all in flight together
+        // pass B: one reservation per occupied slot, all in flight together;
+        // the slot's first index and the end of its bucket go to shared memory
         for (int k = lane; k < kWin; k += 32) {
             const uint32_t cnt = wcnt[k];
-            if (cnt) wbase[k] = atomicAdd(&C.dcnt[win_cell<DIM>(k, cell, cx, cy, C.nx)], cnt);
+            if (cnt) {
+                const int dest = win_cell<DIM>(k, cell, cx, cy, C.nx);
+                const uint32_t r = atomicAdd(&C.dcnt[dest], cnt);
+                wstart[k] = C.dlay[dest] + r;
+                wend[k] = min(C.dlay[dest + 1], C.cap);
+            }
             wcnt[k] = 0;
         }
         __syncwarp();
@@ -613,33 +633,27 @@ __device__ void g2_cell(const SimDev& s, int cell, int p, uint32_t step, bool pe
         for (uint32_t b = 0; b < m; b += 32) {
             const uint32_t j = b + lane;
             const unsigned char ws = j < m ? S.sel[j] : kSlotNone;
-            float x = 0.0f, y = 0.0f;
-            int dc = -1;
+            const unsigned grp = __match_any_sync(0xffffffffu, (unsigned)ws);
             if (ws != kSlotNone) {
-                if (DIM == 2) x = S.x[j];
-                y = S.y[j];
-                dc = cell_f<DIM>(C, x, y);
-            }
-            const int gkey = ws == kSlotNone ? -1 : (ws == kSlotFar ? dc : (int)(0x40000000 | ws));
-            const unsigned grp = __match_any_sync(0xffffffffu, gkey);
-            if (gkey >= 0) {
-                const int leader = __ffs(grp) - 1;
-                uint32_t r0 = 0;
-                if (lane == leader) {
-                    if (ws != kSlotFar) {
-                        r0 = wbase[ws] + wcnt[ws];
-                        wcnt[ws] += (uint32_t)__popc(grp);
-                    } else {
-                        r0 = atomicAdd(&C.dcnt[dc], (uint32_t)__popc(grp));
+                const float x = DIM == 2 ? S.x[j] : 0.0f, y = S.y[j];
+                uint32_t i, hi;
+                if (ws < kWin) {
+                    const int leader = __ffs(grp) - 1;
+                    uint32_t r0 = 0;
+                    if (lane == leader) {
+                        r0 = wcnt[ws];
+                        wcnt[ws] = r0 + (uint32_t)__popc(grp);
                     }
+                    i = wstart[ws] + __shfl_sync(grp, r0, leader) + (uint32_t)__popc(grp & lanemask_lt());
+                    hi = wend[ws];
+                } else {   // outside the window: a reservation of its own
+                    const int dc = cell_f<DIM>(C, x, y);
+                    i = C.dlay[dc] + atomicAdd(&C.dcnt[dc], 1u);
+                    hi = min(C.dlay[dc + 1], C.cap);
                 }
-                const uint32_t rank = __shfl_sync(grp, r0, leader) + (uint32_t)__popc(grp & lanemask_lt());
-                const uint32_t lo = C.dlay[dc];
-                const uint32_t hi = min(C.dlay[dc + 1], C.cap);
                 const float v0 = S.v0[j], v1 = S.v1[j], v2 = S.v2[j];
                 const uint32_t id = S.id[j];
-                if (lo + rank < hi) {
-                    const uint32_t i = lo + rank;
+                if (i < hi) {
                     if (DIM == 2) C.dx_[i] = x;
                     C.dy_[i] = y;
                     C.dv0[i] = v0;
@@ -656,7 +670,7 @@ __device__ void g2_cell(const SimDev& s, int cell, int p, uint32_t step, bool pe
                         s.sp_vel[q][1][k] = v1;
                         s.sp_vel[q][2][k] = v2;
                         s.sp_pid[q][k] = id;
-                        s.sp_cell[q][k] = (uint32_t)dc;
+                        s.sp_cell[q][k] = (uint32_t)cell_f<DIM>(C, x, y);
                     } else {
                         atomicAdd(&s.dyn->counters[kCntOverflow], 1ull);
                     }
@@ -675,49 +689,55 @@ __device__ __forceinline__ void load_sim_warp(SimDev& dst, const SimDev& src, in
     for (int i = lane; i < (int)(sizeof(SimDev) / 16); i += 32) b[i] = a[i];
 }
 
-// Cells are handed out one at a time from a queue (wq[0]: next cell of the
-// batch's cell-tile list, wq[1]: warps that found it empty), so that a few
-// dense cells at the end of the list do not leave the other SMs idle.  The
-// last warp to leave resets the queue for the next launch.
+// Cells are handed out one at a time from a device queue (wq[0]: next entry
+// of the batch's cell-tile list), so that dense cells near the end of the
+// list do not leave the other SMs idle; the next cell is requested while the
+// current one is processed.  wq[1] counts the warps that found the queue
+// empty; the last one resets the queue for the next launch.
 template <int CAP, int DIM, bool FLUSH>
 __global__ void __launch_bounds__(128, 4) k_g2(const SimDev* __restrict__ sims, const int2* __restrict__ tiles,
                                             const int* __restrict__ ntiles, uint32_t* __restrict__ wq) {
     extern __shared__ __align__(16) unsigned char g2_smem[];
     __shared__ SimDev sim_w[4];
     __shared__ uint32_t spl_all[4][32];
-    __shared__ uint32_t win_all[4][2 * kWin];
+    __shared__ uint32_t win_all[4][3 * kWin];
+    __shared__ Hdr hdr_all[4];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const Stage S = stage_of<CAP, DIM>(g2_smem, warp);
     const uint32_t total = (uint32_t)*ntiles * kCTile;
+    const uint32_t nwarps = gridDim.x * (blockDim.x / 32);
     SimDev& s = sim_w[warp];
     int cur_sim = -1;
     uint32_t g = 0;
     if (lane == 0) g = atomicAdd(&wq[0], 1u);
     g = __shfl_sync(0xffffffffu, g, 0);
     while (g < total) {
-        uint32_t gn = 0;   // the next cell, requested while this one is processed
+        uint32_t gn = 0;   // in flight while this cell is processed
         if (lane == 0) gn = atomicAdd(&wq[0], 1u);
         const int2 tile = tiles[g / kCTile];
-        const int cell = tile.y + (int)(g % kCTile);
         if (tile.x != cur_sim) {
             __syncwarp();
             load_sim_warp(s, sims[tile.x], lane);
             __syncwarp();
             cur_sim = tile.x;
         }
+        const int cell = tile.y + (int)(g % kCTile);
         if (s.dim == DIM && cell < s.K) {
             const int p = s.dyn->cur;
             const uint32_t step = s.dyn->step;
             const bool pending = s.dyn->relax_pending != 0;
-            if (!FLUSH || pending)
-                g2_cell<CAP, DIM, FLUSH>(s, cell, p, step, pending, spl_all[warp], S, win_all[warp], lane);
+            if (!FLUSH || pending) {
+                fetch_hdr(s, p, cell, hdr_all[warp], lane);
+                g2_cell<CAP, DIM, FLUSH>(s, cell, hdr_all[warp], p, step, pending, spl_all[warp], S, win_all[warp],
+                                         lane);
+            }
         }
         g = __shfl_sync(0xffffffffu, gn, 0);
     }
     if (lane == 0) {
         __threadfence();
         const uint32_t done = atomicAdd(&wq[1], 1u);
-        if (done == gridDim.x * (blockDim.x / 32) - 1) {
+        if (done == nwarps - 1) {
             wq[0] = 0;
             wq[1] = 0;
         }

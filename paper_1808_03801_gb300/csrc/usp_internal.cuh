@@ -179,7 +179,7 @@ struct Launch {
     const int* nptiles;   // device scalar
     const int2* ctiles;   // (sim, first cell) tiles
     const int* nctiles;   // device scalar
-    uint32_t* wq;         // device work queue of k_g2: [0] next cell, [1] warps done; zero between launches
+    uint32_t* wq;         // device work queue of k_g2 (2 words, zero between launches)
     int nsims;
     int dims;             // bit 0: some simulation is 1-D, bit 1: some is 2-D
     int grid_p, grid_c;   // persistent grid sizes
