@@ -335,6 +335,8 @@ extern "C" int usp_create(const usp_gas* gas, const usp_grid* grid, const usp_bc
     for (int d = 0; d < 3; ++d) s.f_bdt[d] = (float)(s.body[d] * s.dt);
     s.f_w = (float)s.w;
     s.f_inv_R = (float)(1.0 / s.R);
+    s.inv_R = 1.0 / s.R;
+    s.es_b = 1.0 - 1.0 / s.Pr;
 
     const int K = s.K;
     int rc = USP_OK;
@@ -572,6 +574,8 @@ extern "C" int usp_init_particles(usp_handle* h, const usp_region* regions, int 
         for (int c = 0; c < K; ++c) mx = std::max(mx, start[c + 1] - start[c]);
         h->fused_R = choose_R(mx + mx / 4);
         Launch L = make_launch(h);
+        // no parameters yet: zero shift for the first moments, no relaxation
+        CK(cudaMemsetAsync(h->host.fprm, 0, sizeof(float) * kNFPrm * (size_t)K, h->stream));
         launch_fused_setup(L);
         CK(cudaGetLastError());
         CK(cudaStreamSynchronize(h->stream));
@@ -593,6 +597,8 @@ static int fused_from_unsorted(usp_handle* h) {
     launch_scatter(L, false);
     CK(cudaGetLastError());
     CK(cudaMemsetAsync(s.fill, 0, sizeof(uint32_t) * (K + 1), h->stream));
+    // no parameters yet: zero shift for the first moments, no relaxation
+    CK(cudaMemsetAsync(s.fprm, 0, sizeof(float) * kNFPrm * (size_t)K, h->stream));
     int one = 1;
     CK(cudaMemcpyAsync(&h->d_dyn->cur, &one, sizeof(int), cudaMemcpyHostToDevice, h->stream));
     std::vector<uint32_t> start(K + 2);

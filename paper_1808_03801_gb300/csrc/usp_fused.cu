@@ -8,8 +8,8 @@
 //             bucket of buffer q (the scatter of the counting sort; the
 //             bucket sizes come from the previous histogram plus slack).
 //   k_inject  reservoir buffer cells refilled into buffer q.
-//   k_g1      per cell (one warp): two-pass moments of Eq. 1 from the
-//             particles held in registers (mean, then central sums), and the
+//   k_g1      per cell (one warp): moments of Eq. 1 in one pass, as sums
+//             about the cell's mean velocity of the previous step, and the
 //             cell's n, T, |u| for its neighbours' Kn_GLL.
 //   k_params  per cell: Kn_GLL and P_ne (Eqs. 16-18), sigma* and q* (Eq. 33),
 //             the Cholesky factor of the ES covariance (Eq. 6c) in FP64, the
@@ -22,7 +22,7 @@
 // tensor, Eq. 33 and the Cholesky factor.  FP64 issue rate is scarce on
 // GB300 and an FP64 instruction costs about as much for one lane as for a
 // whole warp, so the warp-per-cell kernels keep their per-cell arithmetic
-// in FP32: moments are two-pass sums about the cell mean and the
+// in FP32: moments are sums about the previous step's cell mean and the
 // conservation factors use sums about the cell mean, so neither cancels.
 // Each particle is read once and written once by k_g2 and its velocity is
 // read once more by k_g1.
@@ -745,9 +745,12 @@ __global__ void __launch_bounds__(128, 4) k_g2(const SimDev* __restrict__ sims, 
 }
 
 // ---------------------------------------------------------------------------
-// k_g1: per-cell moments (Eq. 1), two passes over the cell's particles
+// k_g1: per-cell moments (Eq. 1) in one pass, as sums of C = c - u_s about a
+// shift u_s: the cell's mean velocity of the previous step (the parameters
+// of that step, still in fprm).  The mean moves little in one step, so the
+// FP32 sums of the centred velocities do not cancel; k_params_f promotes
+// them to FP64 with the shift taken into account.
 // ---------------------------------------------------------------------------
-template <int R>
 __global__ void __launch_bounds__(256) k_g1(const SimDev* __restrict__ sims, const int2* __restrict__ tiles,
                                             const int* __restrict__ ntiles) {
     __shared__ uint32_t spl_all[8][32];
@@ -762,6 +765,9 @@ __global__ void __launch_bounds__(256) k_g1(const SimDev* __restrict__ sims, con
         const SimDev& s = sim_sh;
         const int K = s.K;
         const int q = s.dyn->cur ^ 1;
+        const float* V0 = (const float*)s.vel[q][0];
+        const float* V1 = (const float*)s.vel[q][1];
+        const float* V2 = (const float*)s.vel[q][2];
         for (int cc = warp; cc < kCTile; cc += 8) {
             const int cell = tile.y + cc;
             if (cell >= K) break;
@@ -770,66 +776,26 @@ __global__ void __launch_bounds__(256) k_g1(const SimDev* __restrict__ sims, con
             const uint32_t capc = top > base ? top - base : 0u;
             const uint32_t arrived = s.cnt[q][cell];
             const uint32_t nb = min(arrived, capc);
+            const float u0 = s.fprm[cell], u1 = s.fprm[(size_t)K + cell], u2 = s.fprm[(size_t)2 * K + cell];
             uint32_t nsp = 0;
             if (arrived > nb) nsp = collect_spill(s, q, cell, spl_all[warp], lane);
             const uint32_t n = nb + nsp;
-            const uint32_t CH = 32u * R;
-            const uint32_t nch = (n + CH - 1) / CH;
-            float v0[R], v1[R], v2[R];
-            float m0 = 0, m1 = 0, m2 = 0;
-            const float* V0 = (const float*)s.vel[q][0];
-            const float* V1 = (const float*)s.vel[q][1];
-            const float* V2 = (const float*)s.vel[q][2];
-            auto load = [&](uint32_t j, float& a, float& b, float& c) {
-                if (j < nb) {
-                    a = V0[base + j];
-                    b = V1[base + j];
-                    c = V2[base + j];
-                } else {
-                    const uint32_t i = spl_all[warp][j - nb];
-                    a = s.sp_vel[q][0][i];
-                    b = s.sp_vel[q][1][i];
-                    c = s.sp_vel[q][2][i];
-                }
-            };
-            // pass 1: mean
-            for (uint32_t ch = 0; ch < nch; ++ch) {
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const uint32_t j = ch * CH + r * 32 + lane;
-                    v0[r] = v1[r] = v2[r] = 0.0f;
-                    if (j < n) load(j, v0[r], v1[r], v2[r]);
-                    m0 += v0[r];
-                    m1 += v1[r];
-                    m2 += v2[r];
-                }
-            }
-            m0 = warp_sumf(m0);
-            m1 = warp_sumf(m1);
-            m2 = warp_sumf(m2);
-            const float inv = n > 0 ? 1.0f / (float)n : 0.0f;
-            const float u0 = m0 * inv, u1 = m1 * inv, u2 = m2 * inv;
-            // pass 2: sums of C = c - u0
             float S[12];
 #pragma unroll
             for (int k = 0; k < 12; ++k) S[k] = 0.0f;
-            for (uint32_t ch = 0; ch < nch; ++ch) {
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const uint32_t j = ch * CH + r * 32 + lane;
-                    if (nch > 1) {
-                        v0[r] = v1[r] = v2[r] = 0.0f;
-                        if (j < n) load(j, v0[r], v1[r], v2[r]);
-                    }
-                    if (j < n) {
-                        const float C0 = v0[r] - u0, C1 = v1[r] - u1, C2 = v2[r] - u2;
-                        const float c2 = C0 * C0 + C1 * C1 + C2 * C2;
-                        S[0] += C0; S[1] += C1; S[2] += C2;
-                        S[3] += C0 * C0; S[4] += C1 * C1; S[5] += C2 * C2;
-                        S[6] += C0 * C1; S[7] += C0 * C2; S[8] += C1 * C2;
-                        S[9] += c2 * C0; S[10] += c2 * C1; S[11] += c2 * C2;
-                    }
-                }
+            auto add = [&](float a, float b, float c) {
+                const float C0 = a - u0, C1 = b - u1, C2 = c - u2;
+                const float c2 = C0 * C0 + C1 * C1 + C2 * C2;
+                S[0] += C0; S[1] += C1; S[2] += C2;
+                S[3] += C0 * C0; S[4] += C1 * C1; S[5] += C2 * C2;
+                S[6] += C0 * C1; S[7] += C0 * C2; S[8] += C1 * C2;
+                S[9] += c2 * C0; S[10] += c2 * C1; S[11] += c2 * C2;
+            };
+#pragma unroll 4
+            for (uint32_t j = lane; j < nb; j += 32) add(V0[base + j], V1[base + j], V2[base + j]);
+            for (uint32_t j = nb + lane; j < n; j += 32) {   // spill-list entries of the cell
+                const uint32_t i = spl_all[warp][j - nb];
+                add(s.sp_vel[q][0][i], s.sp_vel[q][1][i], s.sp_vel[q][2][i]);
             }
 #pragma unroll
             for (int k = 0; k < 12; ++k) S[k] = warp_sumf(S[k]);
@@ -878,7 +844,10 @@ struct LocalF {
     float n, T, umag;
 };
 
-__device__ __forceinline__ void local_f(const SimDev& s, int cell, LocalF& L, double* u, double* P, double* theta) {
+// promotion of the cell's FP32 shifted sums: mean velocity, pressure tensor
+// per unit density (P / rho) and theta = R T; inv = 1 / N
+__device__ __forceinline__ void local_f(const SimDev& s, int cell, LocalF& L, double* u, double* P, double* theta,
+                                        double& inv) {
     const int K = s.K;
     const float* M = s.momf;
     const int N = (int)M[cell];
@@ -887,26 +856,23 @@ __device__ __forceinline__ void local_f(const SimDev& s, int cell, LocalF& L, do
     L.n = (float)(N * s.w);
     L.T = 0;
     L.umag = 0;
+    inv = 0.0;
     if (N < 1) return;
-    const double inv = 1.0 / N;
+    inv = 1.0 / N;
     const double d0 = M[K + cell] * inv, d1 = M[2 * K + cell] * inv, d2 = M[3 * K + cell] * inv;
     const double uu[3] = {M[13 * K + cell] + d0, M[14 * K + cell] + d1, M[15 * K + cell] + d2};
     const double p0 = M[4 * K + cell] * inv - d0 * d0, p1 = M[5 * K + cell] * inv - d1 * d1,
                  p2 = M[6 * K + cell] * inv - d2 * d2;
-    const double th = (p0 + p1 + p2) / 3.0;
-    if (u) {
-        u[0] = uu[0]; u[1] = uu[1]; u[2] = uu[2];
-    }
-    if (P) {
-        P[0] = p0; P[1] = p1; P[2] = p2;
-        P[3] = M[7 * K + cell] * inv - d0 * d1;
-        P[4] = M[8 * K + cell] * inv - d0 * d2;
-        P[5] = M[9 * K + cell] * inv - d1 * d2;
-    }
-    if (theta) *theta = th;
+    const double th = (p0 + p1 + p2) * (1.0 / 3.0);
+    u[0] = uu[0]; u[1] = uu[1]; u[2] = uu[2];
+    P[0] = p0; P[1] = p1; P[2] = p2;
+    P[3] = M[7 * K + cell] * inv - d0 * d1;
+    P[4] = M[8 * K + cell] * inv - d0 * d2;
+    P[5] = M[9 * K + cell] * inv - d1 * d2;
+    *theta = th;
     L.valid = N >= 2 && th > 0.0;
     if (!L.valid) return;
-    L.T = (float)(th / s.R);
+    L.T = (float)(th * s.inv_R);
     L.umag = sqrtf((float)(uu[0] * uu[0] + uu[1] * uu[1] + uu[2] * uu[2]));
 }
 
@@ -935,8 +901,8 @@ __global__ void __launch_bounds__(128) k_params_f(const SimDev* __restrict__ sim
             const int cell = tile.y + cc;
             if (cell >= K) break;
             LocalF L;
-            double u[3] = {0, 0, 0}, P[6], th = 0;
-            local_f(s, cell, L, u, P, &th);
+            double u[3] = {0, 0, 0}, P[6], th = 0, inv;
+            local_f(s, cell, L, u, P, &th, inv);
             double f[kNFields];
             for (int k = 0; k < kNFields; ++k) f[k] = 0.0;
             f[0] = L.N * s.w;
@@ -987,11 +953,13 @@ __global__ void __launch_bounds__(128) k_params_f(const SimDev* __restrict__ sim
                                            fmaxf(lam * sqrtf(g2[1]) / L.T, lam * sqrtf(g2[2]) / fmaxf(L.umag, a_s)));
                     pne = __expf(-kn / (float)kKnC);                                              // Eqs. 16-18
                 }
-                const double fs = 1.0 + 0.5 * s.dt * (double)nu * pne;                         // Eq. 33
-                const double fq = 1.0 + 0.5 * s.dt * (double)nu * s.Pr * pne;
-                const double sig[6] = {(P[0] - th) / fs, (P[1] - th) / fs, (P[2] - th) / fs, P[3] / fs, P[4] / fs,
-                                       P[5] / fs};
-                const double b = 1.0 - 1.0 / s.Pr;                                              // Eq. 6c
+                // Eq. 33; FP64 divisions are costly here, so each factor is
+                // inverted once
+                const double ifs = 1.0 / (1.0 + 0.5 * s.dt * (double)nu * pne);
+                const double ifq = 1.0 / (1.0 + 0.5 * s.dt * (double)nu * s.Pr * pne);
+                const double sig[6] = {(P[0] - th) * ifs, (P[1] - th) * ifs, (P[2] - th) * ifs, P[3] * ifs, P[4] * ifs,
+                                       P[5] * ifs};
+                const double b = s.es_b;                                                        // Eq. 6c
                 const double A00 = th + b * sig[0], A11 = th + b * sig[1], A22 = th + b * sig[2];
                 const double A10 = b * sig[3], A20 = b * sig[4], A21 = b * sig[5];
                 // Cholesky factor with reciprocal square roots (no FP64 divisions)
@@ -1029,7 +997,6 @@ __global__ void __launch_bounds__(128) k_params_f(const SimDev* __restrict__ sim
                 pr[14] = 1.0f;
                 // heat flux from the third central moment of the shifted sums
                 const float* M = s.momf;
-                const double inv = 1.0 / L.N;
                 const double d0 = M[K + cell] * inv, d1 = M[2 * K + cell] * inv, d2 = M[3 * K + cell] * inv;
                 const double m00 = M[4 * K + cell] * inv, m11 = M[5 * K + cell] * inv, m22 = M[6 * K + cell] * inv;
                 const double m01 = M[7 * K + cell] * inv, m02 = M[8 * K + cell] * inv, m12 = M[9 * K + cell] * inv;
@@ -1039,16 +1006,16 @@ __global__ void __launch_bounds__(128) k_params_f(const SimDev* __restrict__ sim
                 const double Q1 = 0.5 * (t1 - d1 * tr - 2.0 * (m01 * d0 + m11 * d1 + m12 * d2) + 2.0 * d1 * dd);
                 const double Q2 = 0.5 * (t2 - d2 * tr - 2.0 * (m02 * d0 + m12 * d1 + m22 * d2) + 2.0 * d2 * dd);
                 const double rhod = L.N * s.w * s.mass, pd = rhod * th;
-                f[4] = th / s.R;
+                f[4] = th * s.inv_R;
                 f[5] = pd + rhod * sig[0];
                 f[6] = pd + rhod * sig[1];
                 f[7] = pd + rhod * sig[2];
                 f[8] = rhod * sig[3];
                 f[9] = rhod * sig[4];
                 f[10] = rhod * sig[5];
-                f[11] = rhod * Q0 / fq;
-                f[12] = rhod * Q1 / fq;
-                f[13] = rhod * Q2 / fq;
+                f[11] = rhod * Q0 * ifq;
+                f[12] = rhod * Q1 * ifq;
+                f[13] = rhod * Q2 * ifq;
                 f[14] = pne;
             }
             for (int k = 0; k < kNFPrm; ++k) s.fprm[(size_t)k * K + cell] = pr[k];
@@ -1297,9 +1264,8 @@ void launch_fused_inject(const Launch& L) {
 }
 
 void launch_fused_moments(const Launch& L, int R) {
-    if (R <= 4) k_g1<4><<<L.grid_c, 256, 0, L.stream>>>(L.sims, L.ctiles, L.nctiles);
-    else if (R <= 8) k_g1<8><<<L.grid_c, 256, 0, L.stream>>>(L.sims, L.ctiles, L.nctiles);
-    else k_g1<12><<<L.grid_c, 256, 0, L.stream>>>(L.sims, L.ctiles, L.nctiles);
+    (void)R;
+    k_g1<<<L.grid_c, 256, 0, L.stream>>>(L.sims, L.ctiles, L.nctiles);
 }
 
 void launch_fused_params(const Launch& L) { k_params_f<<<L.grid_c, 32, 0, L.stream>>>(L.sims, L.ctiles, L.nctiles); }

@@ -64,6 +64,7 @@ struct alignas(16) SimDev {
     int has_reservoir, reservoir_cols;
     double R, mass, mu_ref, T_ref, omega, Pr, dt, w;   // w: number density carried by one particle
     double avg_keep, avg_new;                          // (n_a - 1)/n_a, 1/n_a
+    double inv_R, es_b;                                // 1/R and 1 - 1/Pr (Eq. 6c), set on the host
     // single-precision copies for the FP32 kernels (set on the host)
     float f_dt, f_lo[2], f_hi[2], f_inv_dx, f_inv_dy, f_bdt[3], f_w, f_inv_R;
     int mode;
@@ -95,7 +96,7 @@ struct alignas(16) SimDev {
     uint32_t* sp_pid[2];
     uint32_t* sp_cell[2];
     float* fprm;          // kNFPrm x K relaxation parameters in FP32
-    float* momf;          // 16 x K: N, 12 sums of C = c - u0 (two-pass), u0[3]  (fused moments)
+    float* momf;          // 16 x K: N, 12 sums of C = c - u_s, the shift u_s[3]  (fused moments)
     float* floc;          // 4 x K: n, T, |u|, valid of each cell for the Kn_GLL stencil
     SimDyn* dyn;
 };
