@@ -1219,7 +1219,7 @@ extern "C" int usp_batch_run_stage(usp_batch* b, int stage) {
 extern "C" int usp_fused_supported(void) { return 1; }
 
 // Tuning knobs chosen by the autotuner: fused staging capacity (R = 4, 8 or
-// 12, i.e. 128, 256 or 512 particles per cell pass; 0 keeps the current) and
+// 12, i.e. 128, 256 or 416 particles per cell pass; 0 keeps the current) and
 // persistent blocks per SM (1..32; 0 keeps).  Captured graphs are rebuilt.
 extern "C" int usp_set_tuning(usp_handle* h, int fused_R, int grid_per_sm) {
     if (!h) return USP_ERR_INVALID_ARG;

@@ -297,6 +297,11 @@ struct Stage {
     unsigned char* sel;
 };
 
+// largest staging area per warp: holds a 360-particle cell with its
+// fluctuations (+3 standard deviations) while leaving part of the SM's
+// shared memory / L1 carve-out to the cache
+constexpr int kCapMax = 416;
+
 // bytes per staged particle: (x,) y, v0, v1, v2, id, relaxation flag
 template <int CAP, int DIM>
 __host__ __device__ constexpr int stage_bytes() {
@@ -1229,13 +1234,13 @@ void launch_fused_relax_stream(const Launch& L, int R, bool flush_only) {
     if (flush_only) {
         if (R <= 4) launch_g2<128, true>(L);
         else if (R <= 8) launch_g2<256, true>(L);
-        else launch_g2<512, true>(L);
+        else launch_g2<kCapMax, true>(L);
         k_finish_f<<<(L.nsims + 127) / 128, 128, 0, L.stream>>>(L.sims, L.nsims, 1);
         return;
     }
     if (R <= 4) launch_g2<128, false>(L);
     else if (R <= 8) launch_g2<256, false>(L);
-    else launch_g2<512, false>(L);
+    else launch_g2<kCapMax, false>(L);
 }
 
 // set the shared-memory limits of the staged kernels once, outside any capture
@@ -1247,14 +1252,14 @@ void fused_prepare_attributes() {
     cudaFuncSetAttribute(k_g2<128, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<128, 2>());
     cudaFuncSetAttribute(k_g2<256, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<256, 1>());
     cudaFuncSetAttribute(k_g2<256, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<256, 2>());
-    cudaFuncSetAttribute(k_g2<512, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<512, 1>());
-    cudaFuncSetAttribute(k_g2<512, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<512, 2>());
+    cudaFuncSetAttribute(k_g2<kCapMax, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<kCapMax, 1>());
+    cudaFuncSetAttribute(k_g2<kCapMax, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<kCapMax, 2>());
     cudaFuncSetAttribute(k_g2<128, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<128, 1>());
     cudaFuncSetAttribute(k_g2<128, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<128, 2>());
     cudaFuncSetAttribute(k_g2<256, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<256, 1>());
     cudaFuncSetAttribute(k_g2<256, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<256, 2>());
-    cudaFuncSetAttribute(k_g2<512, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<512, 1>());
-    cudaFuncSetAttribute(k_g2<512, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<512, 2>());
+    cudaFuncSetAttribute(k_g2<kCapMax, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<kCapMax, 1>());
+    cudaFuncSetAttribute(k_g2<kCapMax, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<kCapMax, 2>());
     cudaGetLastError();
 }
 
