@@ -150,7 +150,9 @@ __device__ __forceinline__ void es_draw_f(const uint2 key, const FCell& f, const
 }
 
 // ---------------------------------------------------------------------------
-// k_g2: pending relaxation + advection + bucket scatter (FLUSH: relaxation only)
+// k_g2: pending relaxation + advection + bucket scatter.  MODE kFull does
+// both; kRelaxOnly applies the pending relaxation in place (before the
+// particles are read back).
 //
 // One warp per cell.  The cell's particles are copied (cp.async, the whole
 // cell at once) into a per-warp shared memory area of CAP entries and every
@@ -379,7 +381,9 @@ __device__ __forceinline__ void fetch_hdr(const SimDev& s, int p, int cell, Hdr&
     __syncwarp();
 }
 
-template <int CAP, int DIM, bool FLUSH>
+enum { kFull = 0, kRelaxOnly = 1 };
+
+template <int CAP, int DIM, int MODE>
 __device__ void g2_cell(const SimDev& s, int cell, const Hdr& H, int p, uint32_t step, bool pending, uint32_t* spl,
                         const Stage& S, uint32_t* win, int lane) {
     const uint32_t base = H.lay[0];
@@ -403,7 +407,7 @@ __device__ void g2_cell(const SimDev& s, int cell, const Hdr& H, int p, uint32_t
     f.pne = H.prm[13];
     f.valid = H.prm[14] != 0.0f;
     const bool relax = pending && f.valid;
-    if (FLUSH && !relax) return;
+    if (MODE == kRelaxOnly && !relax) return;
     TimeDraw td;
     td.dt = s.f_dt;
     td.a = f.nues * td.dt;
@@ -566,7 +570,7 @@ __device__ void g2_cell(const SimDev& s, int cell, const Hdr& H, int p, uint32_t
         }
     };
 
-    if (FLUSH) {
+    if (MODE == kRelaxOnly) {
         for (uint32_t ch = 0; ch < nch; ++ch) {
             const uint32_t m = nch > 1 ? stage_chunk(ch, false) : m_last;
             const uint32_t off = ch * CAP;
@@ -699,7 +703,7 @@ __device__ __forceinline__ void load_sim_warp(SimDev& dst, const SimDev& src, in
 // list do not leave the other SMs idle; the next cell is requested while the
 // current one is processed.  wq[1] counts the warps that found the queue
 // empty; the last one resets the queue for the next launch.
-template <int CAP, int DIM, bool FLUSH>
+template <int CAP, int DIM, int MODE>
 __global__ void __launch_bounds__(128, 4) k_g2(const SimDev* __restrict__ sims, const int2* __restrict__ tiles,
                                             const int* __restrict__ ntiles, uint32_t* __restrict__ wq) {
     extern __shared__ __align__(16) unsigned char g2_smem[];
@@ -731,9 +735,9 @@ __global__ void __launch_bounds__(128, 4) k_g2(const SimDev* __restrict__ sims, 
             const int p = s.dyn->cur;
             const uint32_t step = s.dyn->step;
             const bool pending = s.dyn->relax_pending != 0;
-            if (!FLUSH || pending) {
+            if (MODE != kRelaxOnly || pending) {
                 fetch_hdr(s, p, cell, hdr_all[warp], lane);
-                g2_cell<CAP, DIM, FLUSH>(s, cell, hdr_all[warp], p, step, pending, spl_all[warp], S, win_all[warp],
+                g2_cell<CAP, DIM, MODE>(s, cell, hdr_all[warp], p, step, pending, spl_all[warp], S, win_all[warp],
                                          lane);
             }
         }
@@ -1208,58 +1212,61 @@ __global__ void k_finish_f(const SimDev* __restrict__ sims, int nsims, int mode)
     }
 }
 
-template <int CAP, int DIM, bool FLUSH>
+template <int CAP, int DIM, int MODE>
 void launch_g2_one(const Launch& L) {
     const int smem = 4 * stage_bytes<CAP, DIM>();
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_g2<CAP, DIM, FLUSH>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_g2<CAP, DIM, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         attr = true;
     }
-    k_g2<CAP, DIM, FLUSH><<<L.grid_c, 128, smem, L.stream>>>(L.sims, L.ctiles, L.nctiles, L.wq);
+    k_g2<CAP, DIM, MODE><<<L.grid_c, 128, smem, L.stream>>>(L.sims, L.ctiles, L.nctiles, L.wq);
 }
 
-template <int CAP, bool FLUSH>
+template <int CAP, int MODE>
 void launch_g2(const Launch& L) {
-    if (L.dims & 1) launch_g2_one<CAP, 1, FLUSH>(L);
-    if (L.dims & 2) launch_g2_one<CAP, 2, FLUSH>(L);
+    if (L.dims & 1) launch_g2_one<CAP, 1, MODE>(L);
+    if (L.dims & 2) launch_g2_one<CAP, 2, MODE>(L);
 }
 
 }  // namespace
 
 void launch_fused_setup(const Launch& L) { k_layout<true><<<L.nsims, 1024, 0, L.stream>>>(L.sims, L.nsims); }
 
+template <int MODE>
+void launch_g2_R(const Launch& L, int R) {
+    if (R <= 4) launch_g2<128, MODE>(L);
+    else if (R <= 8) launch_g2<256, MODE>(L);
+    else launch_g2<kCapMax, MODE>(L);
+}
+
 // R: particles per lane of the largest expected cell (staging area of 32 R)
 void launch_fused_relax_stream(const Launch& L, int R, bool flush_only) {
     if (flush_only) {
-        if (R <= 4) launch_g2<128, true>(L);
-        else if (R <= 8) launch_g2<256, true>(L);
-        else launch_g2<kCapMax, true>(L);
+        launch_g2_R<kRelaxOnly>(L, R);
         k_finish_f<<<(L.nsims + 127) / 128, 128, 0, L.stream>>>(L.sims, L.nsims, 1);
         return;
     }
-    if (R <= 4) launch_g2<128, false>(L);
-    else if (R <= 8) launch_g2<256, false>(L);
-    else launch_g2<kCapMax, false>(L);
+    launch_g2_R<kFull>(L, R);
 }
 
 // set the shared-memory limits of the staged kernels once, outside any capture
+template <int CAP, int MODE>
+void set_g2_smem() {
+    cudaFuncSetAttribute(k_g2<CAP, 1, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<CAP, 1>());
+    cudaFuncSetAttribute(k_g2<CAP, 2, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<CAP, 2>());
+}
+
 void fused_prepare_attributes() {
     static bool done = false;
     if (done) return;
     done = true;
-    cudaFuncSetAttribute(k_g2<128, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<128, 1>());
-    cudaFuncSetAttribute(k_g2<128, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<128, 2>());
-    cudaFuncSetAttribute(k_g2<256, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<256, 1>());
-    cudaFuncSetAttribute(k_g2<256, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<256, 2>());
-    cudaFuncSetAttribute(k_g2<kCapMax, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<kCapMax, 1>());
-    cudaFuncSetAttribute(k_g2<kCapMax, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<kCapMax, 2>());
-    cudaFuncSetAttribute(k_g2<128, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<128, 1>());
-    cudaFuncSetAttribute(k_g2<128, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<128, 2>());
-    cudaFuncSetAttribute(k_g2<256, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<256, 1>());
-    cudaFuncSetAttribute(k_g2<256, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<256, 2>());
-    cudaFuncSetAttribute(k_g2<kCapMax, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<kCapMax, 1>());
-    cudaFuncSetAttribute(k_g2<kCapMax, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<kCapMax, 2>());
+    set_g2_smem<128, kFull>();
+    set_g2_smem<256, kFull>();
+    set_g2_smem<kCapMax, kFull>();
+    set_g2_smem<128, kRelaxOnly>();
+    set_g2_smem<256, kRelaxOnly>();
+    set_g2_smem<kCapMax, kRelaxOnly>();
     cudaGetLastError();
 }
 
