@@ -36,7 +36,7 @@ namespace {
 constexpr uint32_t kNoCell = 0xFFFFFFFFu;
 
 struct FCell {
-    float u[3], th, L[6], pr, nu, nues, pne;
+    float u[3], th, M[6], pr, nu, nues, pne;   // M = L L^T - theta I (lower triangle, row-major)
     int valid;
 };
 
@@ -128,25 +128,39 @@ __device__ __forceinline__ Src src_of(const SimDev& s, int b) {
 
 // per-cell constants of the time-instant draw (Eq. 30)
 struct TimeDraw {
-    float dt, a, em1, ema, inv_nues;
+    float dt, a, em1, ema, inv_nues, inv_pr;
 };
 
-// v: the second counter's words (drawn here unless the caller has them)
-__device__ __forceinline__ void es_draw_f(const uint2 key, const FCell& f, const TimeDraw& td, uint32_t pid,
-                                          uint32_t step, const uint4& w, float* C, const uint4* v_in = nullptr) {
-    const float U1 = u01<float>(w.y);
+// Relaxation draw from the four words of one Philox call (counter
+// (pid, step, relax, 0)).  It samples the law of the FP64 path's two-call
+// scheme with fewer variates:
+//  * u = u01(w.x) selects the particle (u < P_relax); given the selection,
+//    u / P_relax is uniform on (0, 1], so it also gives the time instant
+//    of Eq. 30;
+//  * the sum sqrt(s) L xi1 + sqrt((1 - s) theta) xi2 of two independent
+//    Gaussians (Eqs. 31-32) is one Gaussian of covariance
+//    s L L^T + (1 - s) theta I = theta I + s M, sampled through its own
+//    Cholesky factor from three normals: a Box-Muller pair (w.y, w.z) and
+//    the inverse normal distribution function of w.w.
+__device__ __forceinline__ void es_draw1(const FCell& f, const TimeDraw& td, float u, const uint4& w, float* C) {
+    const float U1 = fminf(u * td.inv_pr, 1.0f);
     const float t = td.a < 1.0f ? __logf(1.0f + U1 * td.em1) * td.inv_nues
                                 : td.dt + __logf(U1 + (1.0f - U1) * td.ema) * td.inv_nues;
     const float sf = f.pne + (1.0f - f.pne) * __expf(-f.nu * t);          // Eq. 32
-    const uint4 v = v_in ? *v_in : philox(make_uint4(pid, step, kRelax, 1), key);
-    float z0, z1, z2, z3, z4, z5;
-    box_muller<float>(w.z, w.w, z0, z1);
-    box_muller<float>(v.x, v.y, z2, z3);
-    box_muller<float>(v.z, v.w, z4, z5);
-    const float A = sqrtf(sf), B = sqrtf(fmaxf(1.0f - sf, 0.0f) * f.th);
-    C[0] = A * (f.L[0] * z0) + B * z3;
-    C[1] = A * (f.L[1] * z0 + f.L[2] * z1) + B * z4;
-    C[2] = A * (f.L[3] * z0 + f.L[4] * z1 + f.L[5] * z2) + B * z5;
+    float z0, z1;
+    box_muller<float>(w.y, w.z, z0, z1);
+    const float z2 = normcdfinvf(u01<float>(w.w));
+    const float S00 = f.th + sf * f.M[0], S10 = sf * f.M[1], S11 = f.th + sf * f.M[2];
+    const float S20 = sf * f.M[3], S21 = sf * f.M[4], S22 = f.th + sf * f.M[5];
+    const float r0 = rsqrtf(S00);
+    const float l00 = S00 * r0, l10 = S10 * r0, l20 = S20 * r0;
+    const float d1 = fmaxf(S11 - l10 * l10, 1e-12f * f.th);
+    const float r1 = rsqrtf(d1);
+    const float l11 = d1 * r1, l21 = (S21 - l20 * l10) * r1;
+    const float l22 = sqrtf(fmaxf(S22 - l20 * l20 - l21 * l21, 0.0f));
+    C[0] = l00 * z0;
+    C[1] = l10 * z0 + l11 * z1;
+    C[2] = l20 * z0 + l21 * z1 + l22 * z2;
 }
 
 // ---------------------------------------------------------------------------
@@ -156,8 +170,8 @@ __device__ __forceinline__ void es_draw_f(const uint2 key, const FCell& f, const
 //
 // One warp per cell.  The cell's particles are copied (cp.async, the whole
 // cell at once) into a per-warp shared memory area of CAP entries and every
-// pass walks them with a rolled loop, so that the per-particle code (two
-// Philox draws, the ES sample, advection) appears once in the binary:
+// pass walks them with a rolled loop, so that the per-particle code (the
+// Philox draw, the ES sample, advection) appears once in the binary:
 //   stage    relaxation draws, conservation sums;
 //   pass A   conservation, advection, destination cell, arrivals counted per
 //            slot of the cell's destination window;
@@ -399,8 +413,15 @@ __device__ void g2_cell(const SimDev& s, int cell, const Hdr& H, int p, uint32_t
 #pragma unroll
     for (int d = 0; d < 3; ++d) f.u[d] = H.prm[d];
     f.th = H.prm[3];
-#pragma unroll
-    for (int d = 0; d < 6; ++d) f.L[d] = H.prm[4 + d];
+    {   // M = L L^T - theta I from the FP64-built factor L
+        const float L0 = H.prm[4], L1 = H.prm[5], L2 = H.prm[6], L3 = H.prm[7], L4 = H.prm[8], L5 = H.prm[9];
+        f.M[0] = L0 * L0 - f.th;
+        f.M[1] = L1 * L0;
+        f.M[2] = L1 * L1 + L2 * L2 - f.th;
+        f.M[3] = L3 * L0;
+        f.M[4] = L3 * L1 + L4 * L2;
+        f.M[5] = L3 * L3 + L4 * L4 + L5 * L5 - f.th;
+    }
     f.pr = H.prm[10];
     f.nu = H.prm[11];
     f.nues = H.prm[12];
@@ -414,11 +435,11 @@ __device__ void g2_cell(const SimDev& s, int cell, const Hdr& H, int p, uint32_t
     td.em1 = expm1f(td.a);
     td.ema = __expf(-td.a);
     td.inv_nues = 1.0f / f.nues;
+    td.inv_pr = f.pr > 0.0f ? 1.0f / f.pr : 0.0f;
     const int q = p ^ 1;
     const uint32_t nch = (n + CAP - 1) / CAP;
     const Src P = src_of(s, p);
     const uint2 key = make_uint2(s.key0, s.key1);
-    const bool eager = f.pr > 0.5f;
 
     // stage chunk ch: the particles are copied into the staging planes
     // (asynchronously from the bucket, directly from the spill list), then
@@ -466,19 +487,13 @@ __device__ void g2_cell(const SimDev& s, int cell, const Hdr& H, int p, uint32_t
                 }
                 const uint4 w0 = philox(make_uint4(id0, step, kRelax, 0), key);
                 const uint4 w1 = philox(make_uint4(id1, step, kRelax, 0), key);
-                // when most particles relax, draw the second counter of both up
-                // front: four independent Philox chains in flight
-                uint4 u0 = make_uint4(0, 0, 0, 0), u1 = u0;
-                if (eager) {
-                    u0 = philox(make_uint4(id0, step, kRelax, 1), key);
-                    u1 = philox(make_uint4(id1, step, kRelax, 1), key);
-                }
-                s0 = u01<float>(w0.x) < f.pr;
-                s1 = has1 && u01<float>(w1.x) < f.pr;
+                const float x0 = u01<float>(w0.x), x1 = u01<float>(w1.x);
+                s0 = x0 < f.pr;
+                s1 = has1 && x1 < f.pr;
                 if (s0 | s1) {
                     float C0[3], C1[3];
-                    es_draw_f(key, f, td, id0, step, w0, C0, eager ? &u0 : nullptr);
-                    es_draw_f(key, f, td, id1, step, w1, C1, eager ? &u1 : nullptr);
+                    es_draw1(f, td, x0, w0, C0);
+                    es_draw1(f, td, x1, w1, C1);
                     if (s0) {
                         if (sums) {
                             const float o0 = p0 - f.u[0], o1 = q0 - f.u[1], o2 = r0 - f.u[2];
