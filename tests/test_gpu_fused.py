@@ -125,6 +125,47 @@ def test_fused_homogeneous_relaxation_closed_form(usp, mode):
     assert abs(sig1 - r * sig0) < 5 * se, (sig1, r * sig0, se)
 
 
+def test_fused_relaxation_full_covariance(usp):
+    """Every component of the stress relaxes by the same factor (Eqs. 8b,
+    29-33): a Gaussian state with a full, rotated covariance exercises the
+    off-diagonal terms of the sampled ES covariance and the third normal."""
+    n = 1_000_000
+    w = _fused(W.homogeneous_box(ppc=n, dt_over_tauc=5.0, mode="usp"))
+    pos, _, pid = W.bimaxwellian(n, seed=23)
+    kb_over_m = 1.380649e-23 / W.M_AR
+    th = np.array([1.4, 0.9, 0.7]) * W.T0 * kb_over_m
+    a1, a2 = 0.5, 0.3
+    R1 = np.array([[math.cos(a1), -math.sin(a1), 0.0], [math.sin(a1), math.cos(a1), 0.0], [0.0, 0.0, 1.0]])
+    R2 = np.array([[1.0, 0.0, 0.0], [0.0, math.cos(a2), -math.sin(a2)], [0.0, math.sin(a2), math.cos(a2)]])
+    R = R2 @ R1
+    cov = R @ np.diag(th) @ R.T
+    rng = np.random.default_rng(5)
+    vel = rng.standard_normal((n, 3)) @ np.linalg.cholesky(cov).T
+    g = usp.Simulation(w).set_particles(pos, vel, pid)
+    g.step(1)
+    prm_dt = g.info()["dt"]
+    F = g.sample()
+    g.step(1)
+    F2 = g.sample()
+    o = oracle.OracleSim(W.homogeneous_box(ppc=n, dt_over_tauc=5.0, mode="usp")).set_particles(pos, vel, pid)
+    o.step(1)
+    po = o.params()[0]
+    nu, nu_es = po[11], po[12]
+    a = nu_es * prm_dt
+    kappa = 1.0 / (1.0 + 0.5 * nu * prm_dt)
+    f = 1.0 + 0.5 * prm_dt * nu          # sampled stress is sigma* (Eq. 33)
+    r = math.exp(-a) + (1 - math.exp(-a)) * (1 - 1 / W.PR_MONO) * kappa
+    rho = F[0, 0] * W.M_AR
+    p0 = rho * KB_M_AR * F[4, 0]
+    p1 = rho * KB_M_AR * F2[4, 0]
+    iso = np.array([1, 1, 1, 0, 0, 0], dtype=float)
+    sig0 = (F[5:11, 0] - p0 * iso) * f
+    sig1 = (F2[5:11, 0] - p1 * iso) * f
+    assert np.all(np.abs(sig0[3:]) > 0.05 * p0)     # the state is really sheared
+    se = p0 * math.sqrt(2.0 / n)
+    assert np.all(np.abs(sig1 - r * sig0) < 5 * se), (sig1, r * sig0, se)
+
+
 def test_fused_couette_matches_oracle_statistically(usp):
     base = W.couette(ny=20, ppc=200, Kn=0.1, dt_over_tauc=0.5)
     g = usp.Simulation(_fused(base)).init_particles()
