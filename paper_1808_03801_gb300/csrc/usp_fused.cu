@@ -713,14 +713,33 @@ __device__ __forceinline__ void load_sim_warp(SimDev& dst, const SimDev& src, in
     for (int i = lane; i < (int)(sizeof(SimDev) / 16); i += 32) b[i] = a[i];
 }
 
-// Cells are handed out one at a time from a device queue (wq[0]: next entry
-// of the batch's cell-tile list), so that dense cells near the end of the
-// list do not leave the other SMs idle; the next cell is requested while the
-// current one is processed.  wq[1] counts the warps that found the queue
-// empty; the last one resets the queue for the next launch.
+// Cells are handed out one at a time from per-simulation queues
+// (SimDyn::qnext): each warp starts on a home simulation and takes its next
+// cell from it, so its descriptor stays in shared memory and neighbouring
+// cells are processed together; when the home simulation runs out, the warp
+// looks for one with cells left (32 candidates per round).  The next cell is
+// requested while the current one is processed.  wq[0] counts the warps that
+// left; the last one resets every queue for the next launch.
+template <int DIM>
+__device__ __forceinline__ int find_sim(const SimDev* __restrict__ sims, int nsims, int from, int lane) {
+    for (int base = 0; base < nsims; base += 32) {
+        const int k = base + lane;
+        bool ok = false;
+        int idx = 0;
+        if (k < nsims) {
+            idx = from + 1 + k;
+            if (idx >= nsims) idx -= nsims;
+            const SimDev& c = sims[idx];
+            ok = c.dim == DIM && __ldcg(&c.dyn->qnext) < (uint32_t)c.K;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, ok);
+        if (m) return __shfl_sync(0xffffffffu, idx, __ffs(m) - 1);
+    }
+    return -1;
+}
+
 template <int CAP, int DIM, int MODE>
-__global__ void __launch_bounds__(128, 4) k_g2(const SimDev* __restrict__ sims, const int2* __restrict__ tiles,
-                                            const int* __restrict__ ntiles, uint32_t* __restrict__ wq) {
+__global__ void __launch_bounds__(128, 4) k_g2(const SimDev* __restrict__ sims, int nsims, uint32_t* __restrict__ wq) {
     extern __shared__ __align__(16) unsigned char g2_smem[];
     __shared__ SimDev sim_w[4];
     __shared__ uint32_t spl_all[4][32];
@@ -728,42 +747,42 @@ __global__ void __launch_bounds__(128, 4) k_g2(const SimDev* __restrict__ sims, 
     __shared__ Hdr hdr_all[4];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const Stage S = stage_of<CAP, DIM>(g2_smem, warp);
-    const uint32_t total = (uint32_t)*ntiles * kCTile;
     const uint32_t nwarps = gridDim.x * (blockDim.x / 32);
     SimDev& s = sim_w[warp];
-    int cur_sim = -1;
-    uint32_t g = 0;
-    if (lane == 0) g = atomicAdd(&wq[0], 1u);
-    g = __shfl_sync(0xffffffffu, g, 0);
-    while (g < total) {
-        uint32_t gn = 0;   // in flight while this cell is processed
-        if (lane == 0) gn = atomicAdd(&wq[0], 1u);
-        const int2 tile = tiles[g / kCTile];
-        if (tile.x != cur_sim) {
-            __syncwarp();
-            load_sim_warp(s, sims[tile.x], lane);
-            __syncwarp();
-            cur_sim = tile.x;
+    int h = (int)((blockIdx.x * (blockDim.x / 32) + warp) % (unsigned)nsims);
+    if (sims[h].dim != DIM) h = find_sim<DIM>(sims, nsims, h, lane);
+    while (h >= 0) {
+        __syncwarp();
+        load_sim_warp(s, sims[h], lane);
+        __syncwarp();
+        const int p = s.dyn->cur;
+        const uint32_t step = s.dyn->step;
+        const bool pending = s.dyn->relax_pending != 0;
+        const uint32_t K = (uint32_t)s.K;
+        if (MODE == kRelaxOnly && !pending) {   // nothing to apply: close its queue
+            if (lane == 0) atomicMax(&s.dyn->qnext, K);
+            h = find_sim<DIM>(sims, nsims, h, lane);
+            continue;
         }
-        const int cell = tile.y + (int)(g % kCTile);
-        if (s.dim == DIM && cell < s.K) {
-            const int p = s.dyn->cur;
-            const uint32_t step = s.dyn->step;
-            const bool pending = s.dyn->relax_pending != 0;
-            if (MODE != kRelaxOnly || pending) {
-                fetch_hdr(s, p, cell, hdr_all[warp], lane);
-                g2_cell<CAP, DIM, MODE>(s, cell, hdr_all[warp], p, step, pending, spl_all[warp], S, win_all[warp],
-                                         lane);
-            }
+        uint32_t c = 0;
+        if (lane == 0) c = atomicAdd(&s.dyn->qnext, 1u);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        while (c < K) {
+            uint32_t cn = 0;   // the next cell, requested now
+            if (lane == 0) cn = atomicAdd(&s.dyn->qnext, 1u);
+            fetch_hdr(s, p, (int)c, hdr_all[warp], lane);
+            g2_cell<CAP, DIM, MODE>(s, (int)c, hdr_all[warp], p, step, pending, spl_all[warp], S, win_all[warp],
+                                    lane);
+            c = __shfl_sync(0xffffffffu, cn, 0);
         }
-        g = __shfl_sync(0xffffffffu, gn, 0);
+        h = find_sim<DIM>(sims, nsims, h, lane);
     }
     if (lane == 0) {
         __threadfence();
-        const uint32_t done = atomicAdd(&wq[1], 1u);
+        const uint32_t done = atomicAdd(&wq[0], 1u);
         if (done == nwarps - 1) {
             wq[0] = 0;
-            wq[1] = 0;
+            for (int i = 0; i < nsims; ++i) sims[i].dyn->qnext = 0;
         }
     }
 }
@@ -1227,6 +1246,20 @@ __global__ void k_finish_f(const SimDev* __restrict__ sims, int nsims, int mode)
     }
 }
 
+// one wave of resident blocks: late blocks would only find empty queues
+template <int CAP, int DIM, int MODE>
+int g2_grid(int smem) {
+    static int grid = 0;
+    if (!grid) {
+        int dev = 0, sms = 152, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_g2<CAP, DIM, MODE>, 128, smem);
+        grid = sms * (per > 0 ? per : 1);
+    }
+    return grid;
+}
+
 template <int CAP, int DIM, int MODE>
 void launch_g2_one(const Launch& L) {
     const int smem = 4 * stage_bytes<CAP, DIM>();
@@ -1235,7 +1268,7 @@ void launch_g2_one(const Launch& L) {
         cudaFuncSetAttribute(k_g2<CAP, DIM, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         attr = true;
     }
-    k_g2<CAP, DIM, MODE><<<L.grid_c, 128, smem, L.stream>>>(L.sims, L.ctiles, L.nctiles, L.wq);
+    k_g2<CAP, DIM, MODE><<<g2_grid<CAP, DIM, MODE>(smem), 128, smem, L.stream>>>(L.sims, L.nsims, L.wq);
 }
 
 template <int CAP, int MODE>
@@ -1270,6 +1303,8 @@ template <int CAP, int MODE>
 void set_g2_smem() {
     cudaFuncSetAttribute(k_g2<CAP, 1, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<CAP, 1>());
     cudaFuncSetAttribute(k_g2<CAP, 2, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<CAP, 2>());
+    g2_grid<CAP, 1, MODE>(4 * stage_bytes<CAP, 1>());
+    g2_grid<CAP, 2, MODE>(4 * stage_bytes<CAP, 2>());
 }
 
 void fused_prepare_attributes() {

@@ -48,6 +48,8 @@ struct SimDyn {
     int cur;            // buffer holding the current state
     int relax_pending;  // fused pipeline: the relaxation of the last step is still to be applied
     uint32_t sp_n[2];   // fused pipeline: entries in the spill lists
+    uint32_t qnext;     // fused pipeline: next cell handed out by k_g2 (zero between launches)
+    uint32_t qpad;
     unsigned long long counters[8];
 };
 
@@ -180,7 +182,7 @@ struct Launch {
     const int* nptiles;   // device scalar
     const int2* ctiles;   // (sim, first cell) tiles
     const int* nctiles;   // device scalar
-    uint32_t* wq;         // device work queue of k_g2 (2 words, zero between launches)
+    uint32_t* wq;         // k_g2: warps done (2 words, zero between launches)
     int nsims;
     int dims;             // bit 0: some simulation is 1-D, bit 1: some is 2-D
     int grid_p, grid_c;   // persistent grid sizes
