@@ -439,8 +439,11 @@ static int alloc_particles(usp_handle* h, int64_t n) {
         cap = (int64_t)std::ceil(n * ff) + 24 * (int64_t)s.K + 4 * (int64_t)s.inj_total + 4096;
     }
     if (cap > (int64_t)0x7FFFFFFFll) return fail(h, USP_ERR_CAPACITY, "particle capacity exceeds 2^31 - 1");
-    free_particles(h);
     destroy_graphs(h->graphs);
+    // storage of a similar size is kept (a re-load of the same problem
+    // allocates nothing); the tile tables depend only on the capacity
+    if (!h->part_allocs.empty() && cap <= s.cap && 2 * cap > s.cap) return USP_OK;
+    free_particles(h);
     const size_t es = h->precision == USP_FP64 ? 8 : 4;
     auto grab = [&](size_t bytes) -> void* {
         void* p = dalloc(h, bytes);
@@ -625,25 +628,24 @@ extern "C" int usp_set_particles(usp_handle* h, int64_t n, const double* pos, co
     s.key0 = (uint32_t)seed;
     s.key1 = (uint32_t)(seed >> 32);
     if ((rc = upload_sim(h)) != 0) return rc;
+    // the caller's arrays go to the device as they are (one copy each; fast
+    // when they are pinned), the transpose into planes runs on the GPU
     const bool fp64 = h->precision == USP_FP64;
-    const size_t es = fp64 ? 8 : 4;
-    std::vector<unsigned char> buf(es * (size_t)std::max<int64_t>(n, 1));
-    auto put = [&](void* dst, const double* src, int stride, int comp) -> cudaError_t {
-        for (int64_t i = 0; i < n; ++i) {
-            double v = src[stride * i + comp];
-            if (fp64) ((double*)buf.data())[i] = v;
-            else ((float*)buf.data())[i] = (float)v;
-        }
-        cudaError_t e = cudaMemcpyAsync(dst, buf.data(), es * n, cudaMemcpyHostToDevice, h->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-        return e;
-    };
     cudaError_t e = cudaSuccess;
     if (n > 0) {
-        if (s.dim == 2) e = put(s.pos[0][0], pos, 2, 0);
-        if (e == cudaSuccess) e = put(s.pos[0][1], pos, 2, 1);
-        for (int d = 0; d < 3 && e == cudaSuccess; ++d) e = put(s.vel[0][d], vel, 3, d);
+        void* stage = dalloc(h, sizeof(double) * 5 * (size_t)n);
+        if (!stage) return fail(h, USP_ERR_OOM, "staging buffer for the particle upload");
+        double* dpos = (double*)stage;
+        double* dvel = dpos + 2 * n;
+        e = cudaMemcpyAsync(dpos, pos, sizeof(double) * 2 * n, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dvel, vel, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(s.pid[0], pid, 4 * n, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) {
+            launch_unpack(s, fp64, dpos, dvel, n, h->stream);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        dfree(h, stage);
     }
     if (e != cudaSuccess) return fail(h, USP_ERR_CUDA, cudaGetErrorString(e));
     if ((rc = reset_dynamic(h, (uint32_t)n, next_pid)) != 0) return rc;

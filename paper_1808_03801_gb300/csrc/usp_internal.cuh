@@ -204,6 +204,7 @@ void launch_relax(const Launch& L, bool fp64);
 void launch_finish(const Launch& L);
 void launch_init(const Launch& L, bool fp64, const double* reg_theta, const double* reg_u, const int* cell_reg);
 void launch_assign(const Launch& L, bool fp64);
+void launch_unpack(const SimDev& s, bool fp64, const double* pos, const double* vel, int64_t n, cudaStream_t st);
 // fused FP32 pipeline (usp_fused.cu); R = particles per lane held in registers
 void launch_fused_setup(const Launch& L);
 void launch_fused_relax_stream(const Launch& L, int R, bool flush_only);

@@ -589,6 +589,31 @@ void launch_relax(const Launch& L, bool fp64) {
 }
 void launch_finish(const Launch& L) { k_finish<<<(L.nsims + 127) / 128, 128, 0, L.stream>>>(L.sims, L.nsims); }
 
+// user-supplied particles (host layout: pos[n][2], vel[n][3] in FP64, copied
+// to the device as they are) into the storage planes of buffer 0
+template <class T>
+__global__ void k_unpack(const double* __restrict__ pos, const double* __restrict__ vel, int64_t n, int dim, T* x,
+                         T* y, T* v0, T* v1, T* v2) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (dim == 2) x[i] = (T)pos[2 * i];
+        y[i] = (T)pos[2 * i + 1];
+        v0[i] = (T)vel[3 * i];
+        v1[i] = (T)vel[3 * i + 1];
+        v2[i] = (T)vel[3 * i + 2];
+    }
+}
+
+void launch_unpack(const SimDev& s, bool fp64, const double* pos, const double* vel, int64_t n, cudaStream_t st) {
+    if (n <= 0) return;
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+    if (fp64)
+        k_unpack<double><<<grid, 256, 0, st>>>(pos, vel, n, s.dim, (double*)s.pos[0][0], (double*)s.pos[0][1],
+                                               (double*)s.vel[0][0], (double*)s.vel[0][1], (double*)s.vel[0][2]);
+    else
+        k_unpack<float><<<grid, 256, 0, st>>>(pos, vel, n, s.dim, (float*)s.pos[0][0], (float*)s.pos[0][1],
+                                              (float*)s.vel[0][0], (float*)s.vel[0][1], (float*)s.vel[0][2]);
+}
+
 void launch_init(const Launch& L, bool fp64, const double* reg_theta, const double* reg_u, const int* cell_reg) {
     if (fp64)
         k_init_fill<double><<<L.grid_c, 256, 0, L.stream>>>(L.sims, L.ctiles, L.nctiles, reg_theta, reg_u, cell_reg);

@@ -192,3 +192,33 @@ def test_batch_fp64_matches_alone_per_particle(usp):
     os_ = oracle.OracleSim(ws).init_particles()
     os_.step(12)
     assert_particles_close(others[1].particles(), os_.particles(), VSCALE, _cell_size(ws))
+
+
+@pytest.mark.parametrize("pipeline", ["plain", "fused"])
+def test_reload_reuses_storage(usp, pipeline):
+    """Loading particles again into a handle (same size: the storage is kept;
+    much smaller: it is reallocated) gives the state of a fresh handle: FP64
+    per particle after steps (plain), identical particles right after the
+    load (fused, FP32)."""
+    prec = "fp64" if pipeline == "plain" else "fp32"
+    w = W.couette(ny=40, ppc=50, precision=prec)
+    w["params"]["pipeline"] = pipeline
+    first = usp.Simulation(w).init_particles()
+    P0 = first.particles()
+    first.step(3)
+    sub = {k: v[: len(v) // 8] for k, v in P0.items()}
+    for P in (P0, sub, P0):
+        first.set_particles(P["pos"], P["vel"], P["pid"])
+        fresh = usp.Simulation(w).set_particles(P["pos"], P["vel"], P["pid"])
+        if pipeline == "plain":
+            first.step(4)
+            fresh.step(4)
+            assert_particles_close(first.particles(), fresh.particles(), VSCALE, _cell_size(w))
+        else:
+            a, b = by_pid(first.particles()), by_pid(fresh.particles())
+            for k in ("pid", "pos", "vel", "cell"):
+                assert np.array_equal(a[k], b[k]), k
+            first.step(4)
+            fresh.step(4)
+            assert first.info()["n_particles"] == fresh.info()["n_particles"] == len(P["pid"])
+        fresh.close()
