@@ -128,7 +128,20 @@ typedef struct {
  *   precision    : USP_FP64 or USP_FP32_MIXED
  *   pipeline     : USP_PIPE_PLAIN or USP_PIPE_FUSED
  *   capacity_factor: particle slots allocated = factor * initial count
- *                  (>= 1; 0 selects 1.25, or 2 with reservoirs) */
+ *                  (>= 1; 0 selects 1.25, or 2 with reservoirs)
+ *   slab_count, slab_index, slab_group: spatial decomposition (not in the
+ *                  paper: how one domain is split over several devices,
+ *                  exercised here inside one GPU).  slab_count > 1 makes the
+ *                  handle own the rows [slab_index*ny/slab_count,
+ *                  (slab_index+1)*ny/slab_count) of the grid (cells along y
+ *                  in 1-D) while advection sees the whole grid and its faces.
+ *                  The slabs of one domain share slab_group, are admitted to
+ *                  one batch consecutively in slab_index order, and are only
+ *                  stepped through that batch: particles crossing into
+ *                  another slab are written into that slab's buckets, and the
+ *                  Kn_GLL stencil (Eq. 18) reads the adjacent slab's row.
+ *                  Requires the fused pipeline, no reservoir faces, and ny a
+ *                  multiple of slab_count; 0 or 1 means no decomposition. */
 typedef struct {
     double Kn, L_ref, n_ref;
     double dt, dt_over_tauc;
@@ -139,6 +152,7 @@ typedef struct {
     int precision;
     int pipeline;
     double capacity_factor;
+    int slab_count, slab_index, slab_group;
 } usp_params;
 
 /* A box of initial gas at number density n, temperature T, velocity u. */

@@ -45,6 +45,7 @@ struct usp_handle {
     double capacity_factor = 0;
     double n_ref = 0;                 // reference number density and particles per cell,
     int ppc_ref = 1;                  // for the initial particle counts
+    int slab_group = 0;               // spatial decomposition group (0: none)
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     usp_allocator alloc{};
@@ -243,6 +244,11 @@ extern "C" int usp_create(const usp_gas* gas, const usp_grid* grid, const usp_bc
         }
     }
     if (any_res && prm->reservoir_cols < 1) return USP_ERR_INVALID_ARG;
+    const bool slab = prm->slab_count > 1;
+    if (prm->slab_count < 0) return USP_ERR_INVALID_ARG;
+    if (slab && (prm->pipeline != USP_PIPE_FUSED || any_res || grid->ny % prm->slab_count != 0 ||
+                 prm->slab_index < 0 || prm->slab_index >= prm->slab_count))
+        return USP_ERR_INVALID_ARG;
     for (int g = 0; g < nseg; ++g) {
         if (grid->dim != 2) return USP_ERR_INVALID_ARG;
         if (segs[g].kind != USP_BC_DIFFUSE && segs[g].kind != USP_BC_SPECULAR) return USP_ERR_INVALID_ARG;
@@ -275,7 +281,13 @@ extern "C" int usp_create(const usp_gas* gas, const usp_grid* grid, const usp_bc
     s.dim = grid->dim;
     s.nx = nx;
     s.ny = grid->ny;
-    s.K = nx * grid->ny;
+    s.slab_count = slab ? prm->slab_count : 1;
+    s.slab_index = slab ? prm->slab_index : 0;
+    s.slab_first = -1;
+    s.rows = grid->ny / s.slab_count;
+    s.row0 = s.slab_index * s.rows;
+    s.K = nx * s.rows;
+    h->slab_group = slab ? prm->slab_group : 0;
     for (int i = 0; i < 2; ++i) {
         s.lo[i] = grid->lo[i];
         s.hi[i] = grid->hi[i];
@@ -513,6 +525,7 @@ extern "C" int usp_init_particles(usp_handle* h, const usp_region* regions, int 
     if (!h) return USP_ERR_INVALID_ARG;
     if (nregions < 0 || (nregions > 0 && !regions)) return fail(h, USP_ERR_INVALID_ARG, "bad regions");
     if (h->batch_refs) return fail(h, USP_ERR_STATE, "handle is admitted to a batch");
+    if (h->host.slab_count > 1) return fail(h, USP_ERR_STATE, "a slab is loaded with usp_set_particles");
     SimDev& s = h->host;
     const int K = s.K;
     std::vector<int> reg(K, -1);
@@ -679,6 +692,7 @@ extern "C" int usp_step(usp_handle* h, int nsteps) {
     if (!h->initialised) return fail(h, USP_ERR_STATE, "particles not initialised");
     if (h->mid_step) return fail(h, USP_ERR_STATE, "a staged step is in progress");
     if (h->batch_refs) return fail(h, USP_ERR_STATE, "handle is admitted to a batch");
+    if (h->host.slab_count > 1) return fail(h, USP_ERR_STATE, "a slab steps only in a batch with its neighbours");
     if (nsteps == 0) return USP_OK;
     int rc;
     if (!h->graphs.one && (rc = capture(h, 1, &h->graphs.one)) != 0) return rc;
@@ -726,6 +740,7 @@ extern "C" int usp_run_stage(usp_handle* h, int stage) {
     if (!h) return USP_ERR_INVALID_ARG;
     if (!h->initialised) return fail(h, USP_ERR_STATE, "particles not initialised");
     if (h->batch_refs) return fail(h, USP_ERR_STATE, "handle is admitted to a batch");
+    if (h->host.slab_count > 1) return fail(h, USP_ERR_STATE, "a slab steps only in a batch with its neighbours");
     Launch L = make_launch(h);
     if (stage_launch(L, h->pipeline, h->precision == USP_FP64, h->fused_R, h->host.has_reservoir != 0, stage))
         return fail(h, USP_ERR_INVALID_ARG, "stage must be 0..6 (plain) or 10..15 (fused)");
@@ -834,7 +849,7 @@ static int get_particles_fused(usp_handle* h, double* pos, double* vel, uint32_t
         if (vel)
             for (int k = 0; k < 3; ++k) vel[3 * o + k] = A[2 + k][i];
         if (pid) pid[o] = id;
-        if (cell) cell[o] = c;
+        if (cell) cell[o] = c + s.row0 * s.nx;   // global cell id (slabs own a row range)
         ++o;
     };
     for (int c = 0; c < K; ++c) {
@@ -1074,6 +1089,21 @@ static int batch_rebuild(usp_batch* b) {
         sims.push_back(h->host);
         for (int t = 0; t < h->nptiles; ++t) pt.push_back(make_int2((int)i, t * kPTile));
         for (int t = 0; t < h->nctiles; ++t) ct.push_back(make_int2((int)i, t * kCTile));
+    }
+    // the slabs of a decomposed domain must sit consecutively, in slab order,
+    // each one pointing at slab 0 of its group
+    for (size_t i = 0; i < sims.size(); ++i) {
+        SimDev& d = sims[i];
+        if (d.slab_count <= 1) continue;
+        const int first = (int)i - d.slab_index;
+        bool ok = first >= 0 && first + d.slab_count <= (int)sims.size();
+        for (int k = 0; ok && k < d.slab_count; ++k) {
+            const usp_handle* o = b->members[first + k];
+            ok = o->slab_group == b->members[i]->slab_group && o->host.slab_count == d.slab_count &&
+                 o->host.slab_index == k && o->host.nx == d.nx && o->host.ny == d.ny;
+        }
+        if (!ok) return bfail(b, USP_ERR_STATE, "the slabs of a group must be admitted together and in slab order");
+        d.slab_first = first;
     }
     bool regraph = false;
     if (pt.size() > b->ptile_cap) {

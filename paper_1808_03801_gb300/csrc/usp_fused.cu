@@ -189,7 +189,7 @@ __device__ __noinline__ bool advect_slow(const SimDev& s, uint32_t step, uint32_
 // per-cell register copy of what the advection and the scatter need
 struct Ctx {
     float tau, lo0, hi0, lo1, hi1, inv_dx, inv_dy, b0, b1, b2;
-    int nx, nxm1, nym1, nseg, reservoir, K;
+    int nx, nxm1, nym1, nseg, reservoir, K, cell0;   // cell0: first global cell of a slab
     float* dx_;   // destination planes
     float* dy_;
     float* dv0;
@@ -227,6 +227,7 @@ __device__ __forceinline__ void make_ctx(const SimDev& s, int q, Ctx& C) {
     C.dlay = s.lay[q];
     C.dcnt = s.cnt[q];
     C.cap = (uint32_t)s.cap;
+    C.cell0 = s.row0 * s.nx;
 }
 
 // cell of an FP32 position: floor of the scaled offset, clamped to the grid
@@ -358,6 +359,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 constexpr int kWin = 64;
 constexpr unsigned char kSlotNone = 0xFF;   // removed, nothing to write
 constexpr unsigned char kSlotFar = 0xFE;    // outside the window
+constexpr unsigned char kSlotOther = 0xFD;  // in another slab of a decomposed domain
 
 template <int DIM>
 __device__ __forceinline__ int win_slot(int dc, int cell, int cx, int cy, int nx) {
@@ -395,10 +397,49 @@ __device__ __forceinline__ void fetch_hdr(const SimDev& s, int p, int cell, Hdr&
     __syncwarp();
 }
 
+// a particle that crossed into another slab of a decomposed domain: its
+// place is reserved in that slab's bucket (or spill list) of buffer q, all
+// slabs of a domain stepping together
+template <int DIM>
+__device__ __noinline__ void emit_other(const SimDev* __restrict__ sims, const SimDev& s, int q, float x, float y,
+                                        float v0, float v1, float v2, uint32_t id) {
+    const float fy = fminf(fmaxf(floorf((y - s.f_lo[1]) * s.f_inv_dy), 0.0f), (float)(s.ny - 1));
+    const int row = (int)fy;
+    int gc = row;
+    if (DIM == 2) gc = row * s.nx + (int)fminf(fmaxf(floorf((x - s.f_lo[0]) * s.f_inv_dx), 0.0f), (float)(s.nx - 1));
+    const SimDev& o = sims[s.slab_first + row / s.rows];
+    const int dc = gc - o.row0 * o.nx;
+    const uint32_t i = o.lay[q][dc] + atomicAdd(&o.cnt[q][dc], 1u);
+    const uint32_t hi = min(o.lay[q][dc + 1], (uint32_t)o.cap);
+    if (i < hi) {
+        if (DIM == 2) ((float*)o.pos[q][0])[i] = x;
+        ((float*)o.pos[q][1])[i] = y;
+        ((float*)o.vel[q][0])[i] = v0;
+        ((float*)o.vel[q][1])[i] = v1;
+        ((float*)o.vel[q][2])[i] = v2;
+        o.pid[q][i] = id;
+        return;
+    }
+    const uint32_t k = atomicAdd(&o.dyn->sp_n[q], 1u);
+    atomicAdd(&o.dyn->counters[kCntSpilled], 1ull);
+    if (k < (uint32_t)kSpillCap) {
+        if (DIM == 2) o.sp_pos[q][0][k] = x;
+        o.sp_pos[q][1][k] = y;
+        o.sp_vel[q][0][k] = v0;
+        o.sp_vel[q][1][k] = v1;
+        o.sp_vel[q][2][k] = v2;
+        o.sp_pid[q][k] = id;
+        o.sp_cell[q][k] = (uint32_t)dc;
+    } else {
+        atomicAdd(&o.dyn->counters[kCntOverflow], 1ull);
+    }
+}
+
 enum { kFull = 0, kRelaxOnly = 1 };
 
 template <int CAP, int DIM, int MODE>
-__device__ void g2_cell(const SimDev& s, int cell, const Hdr& H, int p, uint32_t step, bool pending, uint32_t* spl,
+__device__ void g2_cell(const SimDev* __restrict__ sims, const SimDev& s, int cell, const Hdr& H, int p, uint32_t step,
+                        bool pending, uint32_t* spl,
                         const Stage& S, uint32_t* win, int lane) {
     const uint32_t base = H.lay[0];
     const uint32_t top = min(H.lay[1], (uint32_t)s.cap);
@@ -623,8 +664,10 @@ __device__ void g2_cell(const SimDev& s, int cell, const Hdr& H, int p, uint32_t
                 final_velocity(off, j, c);
                 unsigned char ws = kSlotNone;
                 if (advect_fast<DIM>(s, C, step, S.id[j], x, y, c)) {
-                    const int dc = cell_f<DIM>(C, x, y);
-                    if (!C.reservoir || !in_buffer(s, dc)) {
+                    const int dc = cell_f<DIM>(C, x, y) - C.cell0;   // local cell
+                    if ((unsigned)dc >= (unsigned)C.K) {
+                        ws = kSlotOther;
+                    } else if (!C.reservoir || !in_buffer(s, dc)) {
                         slot = win_slot<DIM>(dc, cell, cx, cy, C.nx);
                         ws = slot >= 0 ? (unsigned char)slot : kSlotFar;
                     } else {
@@ -658,7 +701,9 @@ __device__ void g2_cell(const SimDev& s, int cell, const Hdr& H, int p, uint32_t
             const uint32_t j = b + lane;
             const unsigned char ws = j < m ? S.sel[j] : kSlotNone;
             const unsigned grp = __match_any_sync(0xffffffffu, (unsigned)ws);
-            if (ws != kSlotNone) {
+            if (ws == kSlotOther) {   // into the buckets of another slab
+                emit_other<DIM>(sims, s, q, DIM == 2 ? S.x[j] : 0.0f, S.y[j], S.v0[j], S.v1[j], S.v2[j], S.id[j]);
+            } else if (ws != kSlotNone) {
                 const float x = DIM == 2 ? S.x[j] : 0.0f, y = S.y[j];
                 uint32_t i, hi;
                 if (ws < kWin) {
@@ -671,7 +716,7 @@ __device__ void g2_cell(const SimDev& s, int cell, const Hdr& H, int p, uint32_t
                     i = wstart[ws] + __shfl_sync(grp, r0, leader) + (uint32_t)__popc(grp & lanemask_lt());
                     hi = wend[ws];
                 } else {   // outside the window: a reservation of its own
-                    const int dc = cell_f<DIM>(C, x, y);
+                    const int dc = cell_f<DIM>(C, x, y) - C.cell0;
                     i = C.dlay[dc] + atomicAdd(&C.dcnt[dc], 1u);
                     hi = min(C.dlay[dc + 1], C.cap);
                 }
@@ -694,7 +739,7 @@ __device__ void g2_cell(const SimDev& s, int cell, const Hdr& H, int p, uint32_t
                         s.sp_vel[q][1][k] = v1;
                         s.sp_vel[q][2][k] = v2;
                         s.sp_pid[q][k] = id;
-                        s.sp_cell[q][k] = (uint32_t)cell_f<DIM>(C, x, y);
+                        s.sp_cell[q][k] = (uint32_t)(cell_f<DIM>(C, x, y) - C.cell0);
                     } else {
                         atomicAdd(&s.dyn->counters[kCntOverflow], 1ull);
                     }
@@ -771,7 +816,7 @@ __global__ void __launch_bounds__(128, 4) k_g2(const SimDev* __restrict__ sims, 
             uint32_t cn = 0;   // the next cell, requested now
             if (lane == 0) cn = atomicAdd(&s.dyn->qnext, 1u);
             fetch_hdr(s, p, (int)c, hdr_all[warp], lane);
-            g2_cell<CAP, DIM, MODE>(s, (int)c, hdr_all[warp], p, step, pending, spl_all[warp], S, win_all[warp],
+            g2_cell<CAP, DIM, MODE>(sims, s, (int)c, hdr_all[warp], p, step, pending, spl_all[warp], S, win_all[warp],
                                     lane);
             c = __shfl_sync(0xffffffffu, cn, 0);
         }
@@ -929,6 +974,39 @@ __device__ __forceinline__ void local_nb(const SimDev& s, int cell, LocalF& L) {
     L.N = 0;
 }
 
+// state of the neighbour of `cell` along `axis` (dir = -1 / +1) for the
+// Kn_GLL stencil; across a slab boundary it is the adjacent slab's row.
+// Returns whether the neighbour exists and is valid.
+__device__ __forceinline__ bool nb_state(const SimDev* __restrict__ sims, const SimDev& s, int cell, int axis, int dir,
+                                         LocalF& L) {
+    const int ix = cell % s.nx, iy = cell / s.nx;
+    const SimDev* t = &s;
+    int c;
+    if (axis == 0) {
+        int j = ix + dir;
+        if (j < 0 || j >= s.nx) {
+            if (!s.periodic_x) return false;
+            j = (j + s.nx) % s.nx;
+        }
+        c = iy * s.nx + j;
+    } else {
+        int gj = s.row0 + iy + dir;   // global row
+        if (gj < 0 || gj >= s.ny) {
+            if (!s.periodic_y) return false;
+            gj = (gj + s.ny) % s.ny;
+        }
+        const int r = gj - s.row0;
+        if (r >= 0 && r < s.rows) {
+            c = r * s.nx + ix;
+        } else {
+            t = &sims[s.slab_first + gj / s.rows];
+            c = (gj - t->row0) * s.nx + ix;
+        }
+    }
+    local_nb(*t, c, L);
+    return L.valid != 0;
+}
+
 __global__ void __launch_bounds__(128) k_params_f(const SimDev* __restrict__ sims, const int2* __restrict__ tiles,
                                                   const int* __restrict__ ntiles) {
     __shared__ SimDev sim_sh;
@@ -972,16 +1050,9 @@ __global__ void __launch_bounds__(128) k_params_f(const SimDev* __restrict__ sim
                     float g2[3] = {0, 0, 0};
                     for (int axis = s.dim == 1 ? 1 : 0; axis < 2; ++axis) {
                         const float h = (float)(axis == 0 ? s.dx : s.dy);
-                        int m = neighbor(s, cell, axis, -1), p = neighbor(s, cell, axis, +1);
-                        LocalF Lm, Lp;
-                        if (m >= 0) {
-                            local_nb(s, m, Lm);
-                            if (!Lm.valid) m = -1;
-                        }
-                        if (p >= 0) {
-                            local_nb(s, p, Lp);
-                            if (!Lp.valid) p = -1;
-                        }
+                        LocalF Lm{}, Lp{};
+                        const int m = nb_state(sims, s, cell, axis, -1, Lm) ? 1 : -1;
+                        const int p = nb_state(sims, s, cell, axis, +1, Lp) ? 1 : -1;
                         const float Qm[3] = {Lm.n, Lm.T, Lm.umag}, Qp[3] = {Lp.n, Lp.T, Lp.umag};
                         for (int k = 0; k < 3; ++k) {
                             float d = 0.0f;

@@ -67,6 +67,10 @@ struct alignas(16) SimDev {
     double R, mass, mu_ref, T_ref, omega, Pr, dt, w;   // w: number density carried by one particle
     double avg_keep, avg_new;                          // (n_a - 1)/n_a, 1/n_a
     double inv_R, es_b;                                // 1/R and 1 - 1/Pr (Eq. 6c), set on the host
+    // spatial decomposition: this handle owns rows [row0, row0 + rows) of the
+    // grid above (K = nx * rows cells, local index = global - row0 * nx);
+    // slab_first is the batch index of slab 0 (-1 outside a batch)
+    int slab_count, slab_index, slab_first, row0, rows;
     // single-precision copies for the FP32 kernels (set on the host)
     float f_dt, f_lo[2], f_hi[2], f_inv_dx, f_inv_dy, f_bdt[3], f_w, f_inv_R;
     int mode;

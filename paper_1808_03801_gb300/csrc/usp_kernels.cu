@@ -80,7 +80,10 @@ __global__ void __launch_bounds__(256) k_assign(const SimDev* __restrict__ sims,
         for (int j = threadIdx.x; j < kPTile; j += blockDim.x) {
             const int64_t i = (int64_t)tile.y + j;
             if (i >= (int64_t)n) break;
-            const int cell = cell_index<T>(s, s.dim == 2 ? P.x[i] : (T)0, P.y[i]);
+            // local cell of a slab (row0 = 0 without a decomposition),
+            // clamped into the slab's cell range
+            const int cell = min(max(cell_index<T>(s, s.dim == 2 ? P.x[i] : (T)0, P.y[i]) - s.row0 * s.nx, 0),
+                                 s.K - 1);
             s.cell[i] = (uint32_t)cell;
             aggregated_add(s.count, (uint32_t)cell);
         }

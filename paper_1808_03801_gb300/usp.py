@@ -55,7 +55,8 @@ class Params(ctypes.Structure):
     _fields_ = [("Kn", c_double), ("L_ref", c_double), ("n_ref", c_double), ("dt", c_double),
                 ("dt_over_tauc", c_double), ("body_accel", c_double * 3), ("ppc_ref", c_int),
                 ("n_avg", c_int), ("mode", c_int), ("fixed_pne", c_double), ("reservoir_cols", c_int),
-                ("precision", c_int), ("pipeline", c_int), ("capacity_factor", c_double)]
+                ("precision", c_int), ("pipeline", c_int), ("capacity_factor", c_double),
+                ("slab_count", c_int), ("slab_index", c_int), ("slab_group", c_int)]
 
 
 class Region(ctypes.Structure):
@@ -212,7 +213,8 @@ def make_structs(w: dict, pipeline: str | None = None):
     params = Params(pr["Kn"], pr["L_ref"], pr["n_ref"], pr["dt"], pr["dt_over_tauc"],
                     (c_double * 3)(*pr["body_accel"]), pr["ppc_ref"], pr["n_avg"], MODE[pr["mode"]],
                     pr["fixed_pne"], pr["reservoir_cols"], PRECISION[pr["precision"]], PIPELINE[pipe],
-                    float(pr.get("capacity_factor", 0.0)))
+                    float(pr.get("capacity_factor", 0.0)), int(pr.get("slab_count", 0)),
+                    int(pr.get("slab_index", 0)), int(pr.get("slab_group", 0)))
     return gas, grid, faces, segs, len(w.get("segments", [])), params
 
 
@@ -244,7 +246,10 @@ class Simulation:
             raise UspError(rc, "usp_create rejected the workload")
         self._h = h
         self.dim = w["grid"]["dim"]
-        self.K = (w["grid"]["nx"] if self.dim == 2 else 1) * w["grid"]["ny"]
+        # cells owned by this handle (a slab of a decomposed domain owns
+        # ny / slab_count rows)
+        slabs = max(1, int(w["params"].get("slab_count", 0)))
+        self.K = (w["grid"]["nx"] if self.dim == 2 else 1) * (w["grid"]["ny"] // slabs)
 
     def _check(self, rc, what):
         if rc != OK:
