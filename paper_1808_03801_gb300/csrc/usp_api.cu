@@ -1155,6 +1155,7 @@ static Launch batch_launch(usp_batch* b) {
     L.nsims = (int)b->members.size();
     L.dims = 0;
     for (auto* h : b->members) L.dims |= h->host.dim == 1 ? 1 : 2;
+    for (auto* h : b->members) L.slabs |= h->host.slab_count > 1;
     // fixed persistent grids: the tile counts are read on the device, so the
     // captured graph stays valid while simulations come and go
     int per_sm = 1;

@@ -435,7 +435,9 @@ __device__ __noinline__ void emit_other(const SimDev* __restrict__ sims, const S
     }
 }
 
-enum { kFull = 0, kRelaxOnly = 1 };
+// kFullSlab: kFull for batches holding slabs of a decomposed domain (routes
+// particles that leave the slab; the plain kFull code carries no such check)
+enum { kFull = 0, kRelaxOnly = 1, kFullSlab = 2 };
 
 template <int CAP, int DIM, int MODE>
 __device__ void g2_cell(const SimDev* __restrict__ sims, const SimDev& s, int cell, const Hdr& H, int p, uint32_t step,
@@ -664,8 +666,8 @@ __device__ void g2_cell(const SimDev* __restrict__ sims, const SimDev& s, int ce
                 final_velocity(off, j, c);
                 unsigned char ws = kSlotNone;
                 if (advect_fast<DIM>(s, C, step, S.id[j], x, y, c)) {
-                    const int dc = cell_f<DIM>(C, x, y) - C.cell0;   // local cell
-                    if ((unsigned)dc >= (unsigned)C.K) {
+                    const int dc = cell_f<DIM>(C, x, y) - (MODE == kFullSlab ? C.cell0 : 0);   // local cell
+                    if (MODE == kFullSlab && (unsigned)dc >= (unsigned)C.K) {
                         ws = kSlotOther;
                     } else if (!C.reservoir || !in_buffer(s, dc)) {
                         slot = win_slot<DIM>(dc, cell, cx, cy, C.nx);
@@ -701,7 +703,7 @@ __device__ void g2_cell(const SimDev* __restrict__ sims, const SimDev& s, int ce
             const uint32_t j = b + lane;
             const unsigned char ws = j < m ? S.sel[j] : kSlotNone;
             const unsigned grp = __match_any_sync(0xffffffffu, (unsigned)ws);
-            if (ws == kSlotOther) {   // into the buckets of another slab
+            if (MODE == kFullSlab && ws == kSlotOther) {   // into the buckets of another slab
                 emit_other<DIM>(sims, s, q, DIM == 2 ? S.x[j] : 0.0f, S.y[j], S.v0[j], S.v1[j], S.v2[j], S.id[j]);
             } else if (ws != kSlotNone) {
                 const float x = DIM == 2 ? S.x[j] : 0.0f, y = S.y[j];
@@ -716,7 +718,7 @@ __device__ void g2_cell(const SimDev* __restrict__ sims, const SimDev& s, int ce
                     i = wstart[ws] + __shfl_sync(grp, r0, leader) + (uint32_t)__popc(grp & lanemask_lt());
                     hi = wend[ws];
                 } else {   // outside the window: a reservation of its own
-                    const int dc = cell_f<DIM>(C, x, y) - C.cell0;
+                    const int dc = cell_f<DIM>(C, x, y) - (MODE == kFullSlab ? C.cell0 : 0);
                     i = C.dlay[dc] + atomicAdd(&C.dcnt[dc], 1u);
                     hi = min(C.dlay[dc + 1], C.cap);
                 }
@@ -739,7 +741,7 @@ __device__ void g2_cell(const SimDev* __restrict__ sims, const SimDev& s, int ce
                         s.sp_vel[q][1][k] = v1;
                         s.sp_vel[q][2][k] = v2;
                         s.sp_pid[q][k] = id;
-                        s.sp_cell[q][k] = (uint32_t)(cell_f<DIM>(C, x, y) - C.cell0);
+                        s.sp_cell[q][k] = (uint32_t)(cell_f<DIM>(C, x, y) - (MODE == kFullSlab ? C.cell0 : 0));
                     } else {
                         atomicAdd(&s.dyn->counters[kCntOverflow], 1ull);
                     }
@@ -1366,7 +1368,8 @@ void launch_fused_relax_stream(const Launch& L, int R, bool flush_only) {
         k_finish_f<<<(L.nsims + 127) / 128, 128, 0, L.stream>>>(L.sims, L.nsims, 1);
         return;
     }
-    launch_g2_R<kFull>(L, R);
+    if (L.slabs) launch_g2_R<kFullSlab>(L, R);
+    else launch_g2_R<kFull>(L, R);
 }
 
 // set the shared-memory limits of the staged kernels once, outside any capture
@@ -1388,6 +1391,9 @@ void fused_prepare_attributes() {
     set_g2_smem<128, kRelaxOnly>();
     set_g2_smem<256, kRelaxOnly>();
     set_g2_smem<kCapMax, kRelaxOnly>();
+    set_g2_smem<128, kFullSlab>();
+    set_g2_smem<256, kFullSlab>();
+    set_g2_smem<kCapMax, kFullSlab>();
     cudaGetLastError();
 }
 

@@ -189,6 +189,7 @@ struct Launch {
     uint32_t* wq;         // k_g2: warps done (2 words, zero between launches)
     int nsims;
     int dims;             // bit 0: some simulation is 1-D, bit 1: some is 2-D
+    int slabs = 0;        // some simulation is a slab of a decomposed domain
     int grid_p, grid_c;   // persistent grid sizes
     cudaStream_t stream;
 };
