@@ -201,18 +201,24 @@ int usp_create(const usp_gas* gas, const usp_grid* grid, const usp_bc faces[4],
  * (the last listed region wins): round(n / n_ref * ppc_ref) particles with
  * uniform positions in the cell and Maxwellian velocities at (T, u);
  * particle ids 0.. in cell order; random numbers keyed by seed.  Resets the
- * step counter and the averages. */
+ * step counter and the averages.  STATE for a slab of a decomposed domain
+ * (slabs are loaded with usp_set_particles). */
 int usp_init_particles(usp_handle* h, const usp_region* regions, int nregions, uint64_t seed);
 
 /* Load an arbitrary state from HOST arrays: pos[n][2] (x, y; x ignored in
  * 1-D), vel[n][3], pid[n]; next_pid is the first id given to injected
- * particles.  Resets the step counter and the averages. */
+ * particles.  The arrays are copied to the device as they are (pinned memory
+ * makes this a direct DMA) and transposed into the storage planes there; the
+ * particle storage of an earlier load of a similar size is reused.  Returns
+ * after the copy.  A slab keeps particles outside its rows in its edge cells
+ * until they move.  Resets the step counter and the averages. */
 int usp_set_particles(usp_handle* h, int64_t n, const double* pos, const double* vel,
                       const uint32_t* pid, uint32_t next_pid, uint64_t seed);
 
 /* Advance nsteps time steps on the handle's stream (asynchronous).  Steps
  * are replayed from a captured CUDA graph.  Returns CAPACITY if injection
- * would exceed the particle slots (checked before launching). */
+ * would exceed the particle slots (checked before launching), STATE for a
+ * slab of a decomposed domain (slabs step only through a batch). */
 int usp_step(usp_handle* h, int nsteps);
 
 /* Copy the USP_NFIELDS x n_cells FP64 fields ([field][cell]) into out
@@ -255,7 +261,8 @@ const char* usp_status_string(int status);
 int usp_batch_create(size_t hbm_budget, int max_sims, void* stream, usp_batch** out);
 /* CAPACITY when the handle does not fit the budget or the slot count. */
 int usp_batch_admit(usp_batch* b, usp_handle* h);
-/* Advance every admitted handle nsteps steps. */
+/* Advance every admitted handle nsteps steps.  STATE when the slabs of a
+ * decomposed domain are not all admitted, consecutively and in slab order. */
 int usp_batch_step(usp_batch* b, int nsteps);
 int usp_batch_retire(usp_batch* b, usp_handle* h);
 int usp_batch_info(usp_batch* b, int* n_sims, size_t* bytes_in_use);
