@@ -316,7 +316,7 @@ int usp_get_tuning(usp_handle* h, int* fused_R, int* grid_per_sm);
 /* 1 when the library carries the fused FP32 pipeline (USP_PIPE_FUSED).  Its
  * stages for usp_run_stage / usp_batch_run_stage are 10 relaxation of the
  * previous step + advection + bucket scatter, 11 reservoir refill, 12
- * moments, 13 parameters and fields, 14 bucket layout, 15 end of step. */
+ * moments, 13 parameters and fields, 14 bucket layout and end of step. */
 int usp_fused_supported(void);
 int usp_batch_destroy(usp_batch* b);
 

@@ -175,8 +175,7 @@ static void enqueue_fused_step(const Launch& L, int R, bool reservoir) {
     if (reservoir) launch_fused_inject(L);
     launch_fused_moments(L, R);
     launch_fused_params(L);
-    launch_fused_layout(L);
-    launch_fused_finish(L);
+    launch_fused_layout(L);   // ends the step too
 }
 
 static void enqueue_any(usp_handle* h, const Launch& L) {
@@ -707,7 +706,7 @@ extern "C" int usp_step(usp_handle* h, int nsteps) {
     return USP_OK;
 }
 
-// one stage of a step: plain pipeline 0..6, fused pipeline 10..15
+// one stage of a step: plain pipeline 0..6, fused pipeline 10..14
 static int stage_launch(const Launch& L, int pipeline, bool fp64, int R, bool reservoir, int stage) {
     if (pipeline == USP_PIPE_FUSED) {
         switch (stage) {
@@ -715,8 +714,7 @@ static int stage_launch(const Launch& L, int pipeline, bool fp64, int R, bool re
         case 11: if (reservoir) launch_fused_inject(L); return 0;
         case 12: launch_fused_moments(L, R); return 0;
         case 13: launch_fused_params(L); return 0;
-        case 14: launch_fused_layout(L); return 0;
-        case 15: launch_fused_finish(L); return 0;
+        case 14: launch_fused_layout(L); return 0;   // layout + end of step
         default: return -1;
         }
     }
@@ -743,13 +741,13 @@ extern "C" int usp_run_stage(usp_handle* h, int stage) {
     if (h->host.slab_count > 1) return fail(h, USP_ERR_STATE, "a slab steps only in a batch with its neighbours");
     Launch L = make_launch(h);
     if (stage_launch(L, h->pipeline, h->precision == USP_FP64, h->fused_R, h->host.has_reservoir != 0, stage))
-        return fail(h, USP_ERR_INVALID_ARG, "stage must be 0..6 (plain) or 10..15 (fused)");
+        return fail(h, USP_ERR_INVALID_ARG, "stage must be 0..6 (plain) or 10..14 (fused)");
     if (h->pipeline == USP_PIPE_PLAIN) {
         if (stage == 0) h->sorted = false;
         if (stage == 2) h->mid_step = h->sorted = true;
         if (stage == 6) h->mid_step = false;
     } else {
-        h->mid_step = stage >= 10 && stage < 15;
+        h->mid_step = stage >= 10 && stage < 14;
     }
     CK(cudaGetLastError());
     return USP_OK;
@@ -1244,7 +1242,7 @@ extern "C" int usp_batch_run_stage(usp_batch* b, int stage) {
         R = std::max(R, h->fused_R);
     }
     if (stage_launch(L, b->pipeline, fp64, R, res, stage))
-        return bfail(b, USP_ERR_INVALID_ARG, "stage must be 0..6 (plain) or 10..15 (fused)");
+        return bfail(b, USP_ERR_INVALID_ARG, "stage must be 0..6 (plain) or 10..14 (fused)");
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? USP_OK : bfail(b, USP_ERR_CUDA, cudaGetErrorString(e));
 }

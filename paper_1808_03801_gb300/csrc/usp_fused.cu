@@ -15,8 +15,8 @@
 //             the Cholesky factor of the ES covariance (Eq. 6c) in FP64, the
 //             fields and the average of Eq. 34.
 //   k_layout  per simulation: histogram -> bucket sizes -> exclusive scan,
-//             the layout that the next step writes with.
-//   k_finish  swap buffers, advance the step.
+//             the layout that the next step writes with; then the end of
+//             the step (swap buffers, advance the step).
 // Per particle all arithmetic is FP32.  FP64 is used per cell in k_params_f
 // (one cell per thread): the promotion of the moment sums, the stress
 // tensor, Eq. 33 and the Cholesky factor.  FP64 issue rate is scarce on
@@ -1296,6 +1296,16 @@ __global__ void __launch_bounds__(1024) k_layout(const SimDev* __restrict__ sims
         }
         for (int c = threadIdx.x; c < K; c += blockDim.x) s.cnt[dst][c] = 0;
         __syncthreads();
+        if (!SETUP && threadIdx.x == 0) {   // end of the step (every thread has read cur)
+            if (s.has_reservoir) {
+                dyn->next_pid += s.inj_total;
+                dyn->counters[kCntInjected] += s.inj_total;
+            }
+            dyn->cur ^= 1;
+            dyn->step += 1;
+            dyn->nsamples += 1;
+            dyn->relax_pending = 1;
+        }
     }
 }
 
