@@ -1310,23 +1310,11 @@ __global__ void __launch_bounds__(1024) k_layout(const SimDev* __restrict__ sims
 }
 
 // end of a fused step (mode 0) or after a flush of the pending relaxation (mode 1)
-__global__ void k_finish_f(const SimDev* __restrict__ sims, int nsims, int mode) {
-    for (int si = blockIdx.x * blockDim.x + threadIdx.x; si < nsims; si += gridDim.x * blockDim.x) {
-        const SimDev& s = sims[si];
-        SimDyn* d = s.dyn;
-        if (mode == 1) {
-            d->relax_pending = 0;
-            continue;
-        }
-        if (s.has_reservoir) {
-            d->next_pid += s.inj_total;
-            d->counters[kCntInjected] += s.inj_total;
-        }
-        d->cur ^= 1;
-        d->step += 1;
-        d->nsamples += 1;
-        d->relax_pending = 1;
-    }
+// clears the pending relaxation once it has been applied in place before a
+// read-back (the end of a step is part of k_layout)
+__global__ void k_clear_pending(const SimDev* __restrict__ sims, int nsims) {
+    for (int si = blockIdx.x * blockDim.x + threadIdx.x; si < nsims; si += gridDim.x * blockDim.x)
+        sims[si].dyn->relax_pending = 0;
 }
 
 // one wave of resident blocks: late blocks would only find empty queues
@@ -1375,7 +1363,7 @@ void launch_g2_R(const Launch& L, int R) {
 void launch_fused_relax_stream(const Launch& L, int R, bool flush_only) {
     if (flush_only) {
         launch_g2_R<kRelaxOnly>(L, R);
-        k_finish_f<<<(L.nsims + 127) / 128, 128, 0, L.stream>>>(L.sims, L.nsims, 1);
+        k_clear_pending<<<(L.nsims + 127) / 128, 128, 0, L.stream>>>(L.sims, L.nsims);
         return;
     }
     if (L.slabs) launch_g2_R<kFullSlab>(L, R);
@@ -1421,8 +1409,5 @@ void launch_fused_params(const Launch& L) { k_params_f<<<L.grid_c, 32, 0, L.stre
 
 void launch_fused_layout(const Launch& L) { k_layout<false><<<L.nsims, 1024, 0, L.stream>>>(L.sims, L.nsims); }
 
-void launch_fused_finish(const Launch& L) {
-    k_finish_f<<<(L.nsims + 127) / 128, 128, 0, L.stream>>>(L.sims, L.nsims, 0);
-}
 
 }  // namespace usp

@@ -217,7 +217,6 @@ void launch_fused_inject(const Launch& L);
 void launch_fused_moments(const Launch& L, int R);
 void launch_fused_params(const Launch& L);
 void launch_fused_layout(const Launch& L);
-void launch_fused_finish(const Launch& L);
 void fused_prepare_attributes();
 cudaError_t debug_philox(int64_t n, const uint32_t* d_ctr, uint32_t k0, uint32_t k1, uint32_t* d_out, cudaStream_t st);
 

@@ -243,3 +243,25 @@ def test_fused_batch_equals_alone_statistically(usp):
     assert np.abs(z).max() < 4.0, z
     B.retire(mixed)
     assert mixed.info()["step"] == 200 + 16 * 40
+
+
+def test_fused_stages_compose_a_step(usp):
+    """The stages 10, 12, 13, 14 run one by one give the step: after the first
+    step (nothing pending yet) the same particles at the same positions in
+    the same cells, the same step counter, and relaxation pending."""
+    w = _fused(W.sod(ny=100, ppc_left=80, seed=4))
+    a = usp.Simulation(w).init_particles()
+    P = a.particles()
+    b = usp.Simulation(w).set_particles(P["pos"], P["vel"], P["pid"])
+    a.set_particles(P["pos"], P["vel"], P["pid"])
+    a.step(1)
+    for k, _ in usp.stage_list("fused"):
+        b.run_stage(k)
+    assert usp.launches_per_step("fused") == 4
+    ia, ib = a.info(), b.info()
+    assert ia["step"] == ib["step"] == 1
+    from tests._util import by_pid
+    pa, pb = by_pid(a.particles()), by_pid(b.particles())
+    for k in ("pid", "pos", "cell"):
+        assert np.array_equal(pa[k], pb[k]), k
+    assert ia["counters"][4] == 0 and b.info()["counters"][4] > 0   # the read-back applied b's relaxation
