@@ -141,7 +141,8 @@ struct TimeDraw {
 //    Gaussians (Eqs. 31-32) is one Gaussian of covariance
 //    s L L^T + (1 - s) theta I = theta I + s M, sampled through its own
 //    Cholesky factor from three normals: a Box-Muller pair (w.y, w.z) and
-//    the inverse normal distribution function of w.w.
+//    one Box-Muller normal from w.w and the bits the other uniforms leave
+//    unused.
 __device__ __forceinline__ void es_draw1(const FCell& f, const TimeDraw& td, float u, const uint4& w, float* C) {
     const float U1 = fminf(u * td.inv_pr, 1.0f);
     const float t = td.a < 1.0f ? __logf(1.0f + U1 * td.em1) * td.inv_nues
@@ -149,7 +150,11 @@ __device__ __forceinline__ void es_draw1(const FCell& f, const TimeDraw& td, flo
     const float sf = f.pne + (1.0f - f.pne) * __expf(-f.nu * t);          // Eq. 32
     float z0, z1;
     box_muller<float>(w.y, w.z, z0, z1);
-    const float z2 = normcdfinvf(u01<float>(w.w));
+    // third normal: Box-Muller on w.w and the 23 low bits that the uniforms
+    // of w.x, w.y and w.z leave unused (each takes the top 23 bits)
+    const uint32_t lo = (w.x & 511u) | ((w.y & 511u) << 9) | ((w.z & 31u) << 18);
+    const float r2 = sqrtf(-1.3862943611198906f * __log2f(u01<float>(w.w)));
+    const float z2 = r2 * __cosf(6.283185307179586f * (((float)lo + 0.5f) * 1.1920928955078125e-7f) - 3.14159265358979f);
     const float S00 = f.th + sf * f.M[0], S10 = sf * f.M[1], S11 = f.th + sf * f.M[2];
     const float S20 = sf * f.M[3], S21 = sf * f.M[4], S22 = f.th + sf * f.M[5];
     const float r0 = rsqrtf(S00);
