@@ -265,3 +265,22 @@ def test_fused_stages_compose_a_step(usp):
     for k in ("pid", "pos", "cell"):
         assert np.array_equal(pa[k], pb[k]), k
     assert ia["counters"][4] == 0 and b.info()["counters"][4] > 0   # the read-back applied b's relaxation
+
+
+def test_fused_empty_and_single_particle(usp):
+    """Degenerate loads: no particle at all, and one particle (no cell can
+    relax: fewer than two particles)."""
+    w = _fused(W.couette(ny=10, ppc=20))
+    g = usp.Simulation(w).set_particles(np.zeros((0, 2)), np.zeros((0, 3)), np.zeros(0, dtype=np.uint32))
+    g.step(3)
+    assert g.info()["n_particles"] == 0
+    assert np.all(g.sample()[0] == 0) and len(g.particles()["pid"]) == 0
+    h = w["grid"]["hi"][1] - w["grid"]["lo"][1]
+    pos = np.array([[0.0, w["grid"]["lo"][1] + 0.37 * h]])
+    vel = np.array([[10.0, 120.0, -5.0]])
+    one = usp.Simulation(w).set_particles(pos, vel, np.array([7], dtype=np.uint32))
+    one.step(5)
+    P = one.particles()
+    assert P["pid"].tolist() == [7]
+    assert one.info()["counters"][4] == 0
+    assert w["grid"]["lo"][1] <= P["pos"][0, 1] <= w["grid"]["hi"][1]
