@@ -170,13 +170,22 @@ def host_cpu():
     """CPU model and usable cores of this host."""
     import platform
     model = None
+    impl = part = None
     try:
         for line in open("/proc/cpuinfo"):
-            if line.lower().startswith("model name"):
+            key = line.split(":", 1)[0].strip().lower()
+            if key == "model name" and model is None:
                 model = line.split(":", 1)[1].strip()
-                break
+            elif key == "cpu implementer" and impl is None:
+                impl = line.split(":", 1)[1].strip()
+            elif key == "cpu part" and part is None:
+                part = line.split(":", 1)[1].strip()
     except OSError:
         pass
+    if model is None and part is not None:
+        names = {("0x41", "0xd4f"): "Arm Neoverse V2", ("0x41", "0xd40"): "Arm Neoverse V1",
+                 ("0x41", "0xd0c"): "Arm Neoverse N1"}
+        model = names.get((impl, part), f"Arm implementer {impl} part {part}")
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
     return {"model": model or platform.machine(), "cores": cores}
 
