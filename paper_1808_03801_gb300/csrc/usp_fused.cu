@@ -181,8 +181,12 @@ __device__ __forceinline__ void es_draw1(const FCell& f, const TimeDraw& td, flo
 //   pass A   conservation, advection, destination cell, arrivals counted per
 //            slot of the cell's destination window;
 //   pass B   one atomic reservation per occupied slot in the destination
-//            buckets (a single round trip for the whole cell);
-//   pass C   rank within the slot, write.
+//            buckets (a single round trip for the whole cell) and each
+//            slot's offset in a slot-ordered list of the cell's particles;
+//   pass C   rank within the slot -> the particle's place in that list;
+//   pass D   the list written out: consecutive lanes write consecutive
+//            places of a destination bucket (whole lines, not scattered
+//            words).
 // Cells above CAP particles are processed in chunks: the conservation sums in
 // a first sweep, the update in a second sweep that redraws the same
 // counter-based random numbers.
@@ -440,6 +444,35 @@ __device__ __noinline__ void emit_other(const SimDev* __restrict__ sims, const S
     }
 }
 
+// write a particle into slot i of its own simulation's destination bucket
+// (buffer q), or into the spill list when the bucket is full (dc: its cell)
+template <int DIM>
+__device__ __forceinline__ void put_own(const SimDev& s, const Ctx& C, int q, uint32_t i, uint32_t hi, int dc, float x,
+                                        float y, float v0, float v1, float v2, uint32_t id) {
+    if (i < hi) {
+        if (DIM == 2) C.dx_[i] = x;
+        C.dy_[i] = y;
+        C.dv0[i] = v0;
+        C.dv1[i] = v1;
+        C.dv2[i] = v2;
+        C.did[i] = id;
+        return;
+    }
+    const uint32_t k = atomicAdd(&s.dyn->sp_n[q], 1u);
+    atomicAdd(&s.dyn->counters[kCntSpilled], 1ull);
+    if (k < (uint32_t)kSpillCap) {
+        if (DIM == 2) s.sp_pos[q][0][k] = x;
+        s.sp_pos[q][1][k] = y;
+        s.sp_vel[q][0][k] = v0;
+        s.sp_vel[q][1][k] = v1;
+        s.sp_vel[q][2][k] = v2;
+        s.sp_pid[q][k] = id;
+        s.sp_cell[q][k] = (uint32_t)dc;
+    } else {
+        atomicAdd(&s.dyn->counters[kCntOverflow], 1ull);
+    }
+}
+
 // kFullSlab: kFull for batches holding slabs of a decomposed domain (routes
 // particles that leave the slab; the plain kFull code carries no such check)
 enum { kFull = 0, kRelaxOnly = 1, kFullSlab = 2 };
@@ -447,7 +480,7 @@ enum { kFull = 0, kRelaxOnly = 1, kFullSlab = 2 };
 template <int CAP, int DIM, int MODE>
 __device__ void g2_cell(const SimDev* __restrict__ sims, const SimDev& s, int cell, const Hdr& H, int p, uint32_t step,
                         bool pending, uint32_t* spl,
-                        const Stage& S, uint32_t* win, int lane) {
+                        const Stage& S, uint32_t* win, uint16_t* perm, int lane) {
     const uint32_t base = H.lay[0];
     const uint32_t top = min(H.lay[1], (uint32_t)s.cap);
     const uint32_t capc = top > base ? top - base : 0u;
@@ -656,6 +689,7 @@ __device__ void g2_cell(const SimDev* __restrict__ sims, const SimDev& s, int ce
     uint32_t* wcnt = win;              // arrivals per window slot, then the running rank
     uint32_t* wstart = win + kWin;     // first reserved index of each slot in its bucket
     uint32_t* wend = win + 2 * kWin;   // end of that bucket
+    uint32_t* woff = win + 3 * kWin;   // offset of the slot in the slot-ordered list
     for (uint32_t ch = 0; ch < nch; ++ch) {
         const uint32_t m = nch > 1 ? stage_chunk(ch, false) : m_last;
         const uint32_t off = ch * CAP;
@@ -690,7 +724,26 @@ __device__ void g2_cell(const SimDev* __restrict__ sims, const SimDev& s, int ce
             __syncwarp();
         }
         // pass B: one reservation per occupied slot, all in flight together;
-        // the slot's first index and the end of its bucket go to shared memory
+        // the slot's first index, the end of its bucket and its offset in the
+        // slot-ordered list of the cell's particles go to shared memory
+        uint32_t tot_win = 0;
+        {
+            const uint32_t c0 = wcnt[lane], c1 = wcnt[lane + 32];
+            uint32_t x0 = c0, x1 = c1;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y0 = __shfl_up_sync(0xffffffffu, x0, o);
+                const uint32_t y1 = __shfl_up_sync(0xffffffffu, x1, o);
+                if (lane >= o) {
+                    x0 += y0;
+                    x1 += y1;
+                }
+            }
+            const uint32_t t0 = __shfl_sync(0xffffffffu, x0, 31);
+            woff[lane] = x0 - c0;
+            woff[lane + 32] = t0 + x1 - c1;
+            tot_win = t0 + __shfl_sync(0xffffffffu, x1, 31);
+        }
         for (int k = lane; k < kWin; k += 32) {
             const uint32_t cnt = wcnt[k];
             if (cnt) {
@@ -702,7 +755,8 @@ __device__ void g2_cell(const SimDev* __restrict__ sims, const SimDev& s, int ce
             wcnt[k] = 0;
         }
         __syncwarp();
-        // pass C: rank within the slot, write into the destination bucket
+        // pass C: rank within the slot -> position in the slot-ordered list
+        // (particles leaving the window are written here, one by one)
 #pragma unroll 1
         for (uint32_t b = 0; b < m; b += 32) {
             const uint32_t j = b + lane;
@@ -710,50 +764,36 @@ __device__ void g2_cell(const SimDev* __restrict__ sims, const SimDev& s, int ce
             const unsigned grp = __match_any_sync(0xffffffffu, (unsigned)ws);
             if (MODE == kFullSlab && ws == kSlotOther) {   // into the buckets of another slab
                 emit_other<DIM>(sims, s, q, DIM == 2 ? S.x[j] : 0.0f, S.y[j], S.v0[j], S.v1[j], S.v2[j], S.id[j]);
-            } else if (ws != kSlotNone) {
+            } else if (ws < kWin) {
+                const int leader = __ffs(grp) - 1;
+                uint32_t r0 = 0;
+                if (lane == leader) {
+                    r0 = wcnt[ws];
+                    wcnt[ws] = r0 + (uint32_t)__popc(grp);
+                }
+                const uint32_t rank = __shfl_sync(grp, r0, leader) + (uint32_t)__popc(grp & lanemask_lt());
+                perm[woff[ws] + rank] = (uint16_t)j;
+            } else if (ws == kSlotFar) {   // outside the window: a reservation of its own
                 const float x = DIM == 2 ? S.x[j] : 0.0f, y = S.y[j];
-                uint32_t i, hi;
-                if (ws < kWin) {
-                    const int leader = __ffs(grp) - 1;
-                    uint32_t r0 = 0;
-                    if (lane == leader) {
-                        r0 = wcnt[ws];
-                        wcnt[ws] = r0 + (uint32_t)__popc(grp);
-                    }
-                    i = wstart[ws] + __shfl_sync(grp, r0, leader) + (uint32_t)__popc(grp & lanemask_lt());
-                    hi = wend[ws];
-                } else {   // outside the window: a reservation of its own
-                    const int dc = cell_f<DIM>(C, x, y) - (MODE == kFullSlab ? C.cell0 : 0);
-                    i = C.dlay[dc] + atomicAdd(&C.dcnt[dc], 1u);
-                    hi = min(C.dlay[dc + 1], C.cap);
-                }
-                const float v0 = S.v0[j], v1 = S.v1[j], v2 = S.v2[j];
-                const uint32_t id = S.id[j];
-                if (i < hi) {
-                    if (DIM == 2) C.dx_[i] = x;
-                    C.dy_[i] = y;
-                    C.dv0[i] = v0;
-                    C.dv1[i] = v1;
-                    C.dv2[i] = v2;
-                    C.did[i] = id;
-                } else {
-                    const uint32_t k = atomicAdd(&s.dyn->sp_n[q], 1u);
-                    atomicAdd(&s.dyn->counters[kCntSpilled], 1ull);
-                    if (k < (uint32_t)kSpillCap) {
-                        if (DIM == 2) s.sp_pos[q][0][k] = x;
-                        s.sp_pos[q][1][k] = y;
-                        s.sp_vel[q][0][k] = v0;
-                        s.sp_vel[q][1][k] = v1;
-                        s.sp_vel[q][2][k] = v2;
-                        s.sp_pid[q][k] = id;
-                        s.sp_cell[q][k] = (uint32_t)(cell_f<DIM>(C, x, y) - (MODE == kFullSlab ? C.cell0 : 0));
-                    } else {
-                        atomicAdd(&s.dyn->counters[kCntOverflow], 1ull);
-                    }
-                }
+                const int dc = cell_f<DIM>(C, x, y) - (MODE == kFullSlab ? C.cell0 : 0);
+                const uint32_t i = C.dlay[dc] + atomicAdd(&C.dcnt[dc], 1u);
+                const uint32_t hi = min(C.dlay[dc + 1], C.cap);
+                put_own<DIM>(s, C, q, i, hi, dc, x, y, S.v0[j], S.v1[j], S.v2[j], S.id[j]);
             }
             __syncwarp();
         }
+        // pass D: the slot-ordered list written out, consecutive lanes to
+        // consecutive slots of the destination buckets
+#pragma unroll 1
+        for (uint32_t k = lane; k < tot_win; k += 32) {
+            const uint32_t j = perm[k];
+            const unsigned char ws = S.sel[j];
+            const uint32_t i = wstart[ws] + (k - woff[ws]);
+            const float x = DIM == 2 ? S.x[j] : 0.0f, y = S.y[j];
+            const int dc = i < wend[ws] ? 0 : cell_f<DIM>(C, x, y) - (MODE == kFullSlab ? C.cell0 : 0);
+            put_own<DIM>(s, C, q, i, wend[ws], dc, x, y, S.v0[j], S.v1[j], S.v2[j], S.id[j]);
+        }
+        __syncwarp();
     }
     __syncwarp();
 }
@@ -795,7 +835,8 @@ __global__ void __launch_bounds__(128, 4) k_g2(const SimDev* __restrict__ sims, 
     extern __shared__ __align__(16) unsigned char g2_smem[];
     __shared__ SimDev sim_w[4];
     __shared__ uint32_t spl_all[4][32];
-    __shared__ uint32_t win_all[4][3 * kWin];
+    __shared__ uint32_t win_all[4][4 * kWin];
+    __shared__ uint16_t perm_all[4][kCapMax];
     __shared__ Hdr hdr_all[4];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const Stage S = stage_of<CAP, DIM>(g2_smem, warp);
@@ -824,7 +865,7 @@ __global__ void __launch_bounds__(128, 4) k_g2(const SimDev* __restrict__ sims, 
             if (lane == 0) cn = atomicAdd(&s.dyn->qnext, 1u);
             fetch_hdr(s, p, (int)c, hdr_all[warp], lane);
             g2_cell<CAP, DIM, MODE>(sims, s, (int)c, hdr_all[warp], p, step, pending, spl_all[warp], S, win_all[warp],
-                                    lane);
+                                    perm_all[warp], lane);
             c = __shfl_sync(0xffffffffu, cn, 0);
         }
         h = find_sim<DIM>(sims, nsims, h, lane);
