@@ -946,7 +946,7 @@ __global__ void __launch_bounds__(256) k_g1(const SimDev* __restrict__ sims, con
 #pragma unroll
                 for (int k = 1; k < 12; ++k)
                     if (lane == k + 1) v = S[k];
-                s.momf[(size_t)lane * K + cell] = v;
+                s.momf[(size_t)cell * 16 + lane] = v;   // one 64-byte record per cell
             }
             if (lane == 31) {
                 // local state of the cell for its neighbours' Kn_GLL (FP32)
@@ -962,10 +962,7 @@ __global__ void __launch_bounds__(256) k_g1(const SimDev* __restrict__ sims, con
                         um = sqrtf(w0 * w0 + w1 * w1 + w2 * w2);
                     }
                 }
-                s.floc[cell] = nn;
-                s.floc[(size_t)K + cell] = T;
-                s.floc[(size_t)2 * K + cell] = um;
-                s.floc[(size_t)3 * K + cell] = valid;
+                reinterpret_cast<float4*>(s.floc)[cell] = make_float4(nn, T, um, valid);
             }
         }
     }
@@ -984,9 +981,8 @@ struct LocalF {
 // per unit density (P / rho) and theta = R T; inv = 1 / N
 __device__ __forceinline__ void local_f(const SimDev& s, int cell, LocalF& L, double* u, double* P, double* theta,
                                         double& inv) {
-    const int K = s.K;
-    const float* M = s.momf;
-    const int N = (int)M[cell];
+    const float* M = s.momf + (size_t)cell * 16;   // N, 12 sums, shift[3]
+    const int N = (int)M[0];
     L.N = N;
     L.valid = 0;
     L.n = (float)(N * s.w);
@@ -995,16 +991,16 @@ __device__ __forceinline__ void local_f(const SimDev& s, int cell, LocalF& L, do
     inv = 0.0;
     if (N < 1) return;
     inv = 1.0 / N;
-    const double d0 = M[K + cell] * inv, d1 = M[2 * K + cell] * inv, d2 = M[3 * K + cell] * inv;
-    const double uu[3] = {M[13 * K + cell] + d0, M[14 * K + cell] + d1, M[15 * K + cell] + d2};
-    const double p0 = M[4 * K + cell] * inv - d0 * d0, p1 = M[5 * K + cell] * inv - d1 * d1,
-                 p2 = M[6 * K + cell] * inv - d2 * d2;
+    const double d0 = M[1] * inv, d1 = M[2] * inv, d2 = M[3] * inv;
+    const double uu[3] = {M[13] + d0, M[14] + d1, M[15] + d2};
+    const double p0 = M[4] * inv - d0 * d0, p1 = M[5] * inv - d1 * d1,
+                 p2 = M[6] * inv - d2 * d2;
     const double th = (p0 + p1 + p2) * (1.0 / 3.0);
     u[0] = uu[0]; u[1] = uu[1]; u[2] = uu[2];
     P[0] = p0; P[1] = p1; P[2] = p2;
-    P[3] = M[7 * K + cell] * inv - d0 * d1;
-    P[4] = M[8 * K + cell] * inv - d0 * d2;
-    P[5] = M[9 * K + cell] * inv - d1 * d2;
+    P[3] = M[7] * inv - d0 * d1;
+    P[4] = M[8] * inv - d0 * d2;
+    P[5] = M[9] * inv - d1 * d2;
     *theta = th;
     L.valid = N >= 2 && th > 0.0;
     if (!L.valid) return;
@@ -1014,11 +1010,11 @@ __device__ __forceinline__ void local_f(const SimDev& s, int cell, LocalF& L, do
 
 // neighbour state for the Kn_GLL stencil, written in FP32 by k_g1
 __device__ __forceinline__ void local_nb(const SimDev& s, int cell, LocalF& L) {
-    const int K = s.K;
-    L.n = s.floc[cell];
-    L.T = s.floc[(size_t)K + cell];
-    L.umag = s.floc[(size_t)2 * K + cell];
-    L.valid = s.floc[(size_t)3 * K + cell] != 0.0f;
+    const float4 f = reinterpret_cast<const float4*>(s.floc)[cell];
+    L.n = f.x;
+    L.T = f.y;
+    L.umag = f.z;
+    L.valid = f.w != 0.0f;
     L.N = 0;
 }
 
@@ -1158,11 +1154,11 @@ __global__ void __launch_bounds__(128) k_params_f(const SimDev* __restrict__ sim
                 pr[13] = pne;
                 pr[14] = 1.0f;
                 // heat flux from the third central moment of the shifted sums
-                const float* M = s.momf;
-                const double d0 = M[K + cell] * inv, d1 = M[2 * K + cell] * inv, d2 = M[3 * K + cell] * inv;
-                const double m00 = M[4 * K + cell] * inv, m11 = M[5 * K + cell] * inv, m22 = M[6 * K + cell] * inv;
-                const double m01 = M[7 * K + cell] * inv, m02 = M[8 * K + cell] * inv, m12 = M[9 * K + cell] * inv;
-                const double t0 = M[10 * K + cell] * inv, t1 = M[11 * K + cell] * inv, t2 = M[12 * K + cell] * inv;
+                const float* M = s.momf + (size_t)cell * 16;
+                const double d0 = M[1] * inv, d1 = M[2] * inv, d2 = M[3] * inv;
+                const double m00 = M[4] * inv, m11 = M[5] * inv, m22 = M[6] * inv;
+                const double m01 = M[7] * inv, m02 = M[8] * inv, m12 = M[9] * inv;
+                const double t0 = M[10] * inv, t1 = M[11] * inv, t2 = M[12] * inv;
                 const double tr = m00 + m11 + m22, dd = d0 * d0 + d1 * d1 + d2 * d2;
                 const double Q0 = 0.5 * (t0 - d0 * tr - 2.0 * (m00 * d0 + m01 * d1 + m02 * d2) + 2.0 * d0 * dd);
                 const double Q1 = 0.5 * (t1 - d1 * tr - 2.0 * (m01 * d0 + m11 * d1 + m12 * d2) + 2.0 * d1 * dd);
