@@ -390,18 +390,21 @@ __device__ __forceinline__ int win_cell(int k, int cell, int cx, int cy, int nx)
 // Per-warp copy of the header of one cell: bucket bounds, arrivals and the
 // FP32 relaxation parameters, fetched with one round of cp.async (one word
 // per lane) instead of two dependent rounds of loads.
-constexpr int kHdrPrm = 15;   // u[3], theta, L[6], P_relax, nu, nu_ES, P_ne, valid
-
-struct Hdr {
+struct alignas(16) Hdr {
+    float prm[kNFPrm];   // the cell's parameter record: u[3], theta, L[6], P_relax, nu, nu_ES, P_ne, valid
     uint32_t lay[2];
     uint32_t cnt;
-    float prm[kHdrPrm];
 };
+
+__device__ __forceinline__ void cp_async16_ca(void* dst, const void* src) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
 
 __device__ __forceinline__ void fetch_hdr(const SimDev& s, int p, int cell, Hdr& H, int lane) {
     if (lane < 2) cp_async4(&H.lay[lane], s.lay[p] + cell + lane);
     else if (lane == 2) cp_async4(&H.cnt, s.cnt[p] + cell);
-    else if (lane < 3 + kHdrPrm) cp_async4(&H.prm[lane - 3], s.fprm + (size_t)(lane - 3) * s.K + cell);
+    else if (lane < 7) cp_async16_ca(&H.prm[4 * (lane - 3)], s.fprm + (size_t)cell * kNFPrm + 4 * (lane - 3));
     cp_async_wait_all();
     __syncwarp();
 }
@@ -912,7 +915,8 @@ __global__ void __launch_bounds__(256) k_g1(const SimDev* __restrict__ sims, con
             const uint32_t capc = top > base ? top - base : 0u;
             const uint32_t arrived = s.cnt[q][cell];
             const uint32_t nb = min(arrived, capc);
-            const float u0 = s.fprm[cell], u1 = s.fprm[(size_t)K + cell], u2 = s.fprm[(size_t)2 * K + cell];
+            const float4 us = reinterpret_cast<const float4*>(s.fprm)[(size_t)cell * (kNFPrm / 4)];
+            const float u0 = us.x, u1 = us.y, u2 = us.z;
             uint32_t nsp = 0;
             if (arrived > nb) nsp = collect_spill(s, q, cell, spl_all[warp], lane);
             const uint32_t n = nb + nsp;
@@ -1176,7 +1180,11 @@ __global__ void __launch_bounds__(128) k_params_f(const SimDev* __restrict__ sim
                 f[13] = rhod * Q2 * ifq;
                 f[14] = pne;
             }
-            for (int k = 0; k < kNFPrm; ++k) s.fprm[(size_t)k * K + cell] = pr[k];
+            {   // one 64-byte parameter record per cell
+                float4* dst = reinterpret_cast<float4*>(s.fprm) + (size_t)cell * (kNFPrm / 4);
+#pragma unroll
+                for (int k = 0; k < kNFPrm / 4; ++k) dst[k] = make_float4(pr[4 * k], pr[4 * k + 1], pr[4 * k + 2], pr[4 * k + 3]);
+            }
             const bool first = s.dyn->nsamples == 0;
             for (int k = 0; k < kNFields; ++k) {
                 s.inst[(size_t)k * K + cell] = f[k];

@@ -101,7 +101,7 @@ struct alignas(16) SimDev {
     float* sp_vel[2][3];
     uint32_t* sp_pid[2];
     uint32_t* sp_cell[2];
-    float* fprm;          // kNFPrm x K relaxation parameters in FP32
+    float* fprm;          // [K][kNFPrm] relaxation parameters in FP32 (one 64-byte record per cell)
     float* momf;          // [K][16]: N, 12 sums of C = c - u_s, the shift u_s[3]  (fused moments)
     float* floc;          // [K][4]: n, T, |u|, valid of each cell for the Kn_GLL stencil
     SimDyn* dyn;
