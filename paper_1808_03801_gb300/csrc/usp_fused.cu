@@ -1094,7 +1094,12 @@ __global__ void __launch_bounds__(128) k_params_f(const SimDev* __restrict__ sim
                 if (s.mode == kModeSP) pne = 0.0f;
                 else if (s.mode == kModeFixed) pne = (float)s.fixed_pne;
                 else {
+                    // the gradients are taken relative to the cell's own value
+                    // (|grad Q| / Q): absolute density gradients (~1e25 m^-3 over
+                    // sub-micron cells) would overflow FP32 when squared
+                    const float a_s = sqrtf((float)kGammaMono * thf);
                     const float Qc[3] = {L.n, L.T, L.umag};
+                    const float rq[3] = {1.0f / L.n, 1.0f / L.T, 1.0f / fmaxf(L.umag, a_s)};
                     float g2[3] = {0, 0, 0};
                     for (int axis = s.dim == 1 ? 1 : 0; axis < 2; ++axis) {
                         const float h = (float)(axis == 0 ? s.dx : s.dy);
@@ -1104,15 +1109,13 @@ __global__ void __launch_bounds__(128) k_params_f(const SimDev* __restrict__ sim
                         const float Qm[3] = {Lm.n, Lm.T, Lm.umag}, Qp[3] = {Lp.n, Lp.T, Lp.umag};
                         for (int k = 0; k < 3; ++k) {
                             float d = 0.0f;
-                            if (m >= 0 && p >= 0) d = (Qp[k] - Qm[k]) / (2.0f * h);
-                            else if (p >= 0) d = (Qp[k] - Qc[k]) / h;
-                            else if (m >= 0) d = (Qc[k] - Qm[k]) / h;
+                            if (m >= 0 && p >= 0) d = (Qp[k] - Qm[k]) * rq[k] / (2.0f * h);
+                            else if (p >= 0) d = (Qp[k] - Qc[k]) * rq[k] / h;
+                            else if (m >= 0) d = (Qc[k] - Qm[k]) * rq[k] / h;
                             g2[k] += d * d;
                         }
                     }
-                    const float a_s = sqrtf((float)kGammaMono * thf);
-                    const float kn = fmaxf(lam * sqrtf(g2[0]) / L.n,
-                                           fmaxf(lam * sqrtf(g2[1]) / L.T, lam * sqrtf(g2[2]) / fmaxf(L.umag, a_s)));
+                    const float kn = lam * sqrtf(fmaxf(g2[0], fmaxf(g2[1], g2[2])));
                     pne = __expf(-kn / (float)kKnC);                                              // Eqs. 16-18
                 }
                 // Eq. 33; FP64 divisions are costly here, so each factor is
