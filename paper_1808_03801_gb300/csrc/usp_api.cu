@@ -608,7 +608,7 @@ static int fused_from_unsorted(usp_handle* h) {
     const int K = s.K;
     Launch L = make_launch(h);
     launch_assign(L, false);
-    launch_scan(L);
+    launch_scan(L, false);   // the loaded particles only: no room for a refill
     launch_scatter(L, false);
     CK(cudaGetLastError());
     CK(cudaMemsetAsync(s.fill, 0, sizeof(uint32_t) * (K + 1), h->stream));

@@ -200,7 +200,7 @@ constexpr int kSpillCap = 4096;  // spill entries per parity (fused pipeline)
 constexpr int kNFPrm = 16;       // u[3], theta, L[6], P_relax, nu, nu_ES, P_ne, valid, spare
 
 void launch_stream(const Launch& L, bool fp64);
-void launch_scan(const Launch& L);
+void launch_scan(const Launch& L, bool with_inj = true);
 void launch_scatter(const Launch& L, bool fp64);
 void launch_inject(const Launch& L, bool fp64);
 void launch_moments(const Launch& L, bool fp64);

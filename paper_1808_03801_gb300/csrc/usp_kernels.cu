@@ -93,7 +93,9 @@ __global__ void __launch_bounds__(256) k_assign(const SimDev* __restrict__ sims,
 // ---------------------------------------------------------------------------
 // K2: per-simulation exclusive scan of counts (+ injected) -> start
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_scan(const SimDev* __restrict__ sims, int nsims) {
+// with_inj: leave room for the reservoir refill of the step (the plain step);
+// 0 when a loaded state is only being sorted (fused set-up)
+__global__ void __launch_bounds__(1024) k_scan(const SimDev* __restrict__ sims, int nsims, int with_inj) {
     __shared__ uint32_t warp_sums[32];
     __shared__ uint32_t carry;
     for (int si = blockIdx.x; si < nsims; si += gridDim.x) {
@@ -105,7 +107,7 @@ __global__ void __launch_bounds__(1024) k_scan(const SimDev* __restrict__ sims, 
             const int c = base + threadIdx.x;
             uint32_t v = 0;
             if (c < K) {
-                v = s.count[c] + (s.has_reservoir ? s.inj_count[c] : 0u);
+                v = s.count[c] + (with_inj && s.has_reservoir ? s.inj_count[c] : 0u);
                 s.count[c] = 0;
             } else if (c == K) {
                 s.count[c] = 0;   // removed particles are not kept
@@ -572,7 +574,7 @@ void launch_assign(const Launch& L, bool fp64) {
     if (fp64) k_assign<double><<<L.grid_p, 256, 0, L.stream>>>(L.sims, L.ptiles, L.nptiles);
     else k_assign<float><<<L.grid_p, 256, 0, L.stream>>>(L.sims, L.ptiles, L.nptiles);
 }
-void launch_scan(const Launch& L) { k_scan<<<L.nsims, 1024, 0, L.stream>>>(L.sims, L.nsims); }
+void launch_scan(const Launch& L, bool with_inj) { k_scan<<<L.nsims, 1024, 0, L.stream>>>(L.sims, L.nsims, with_inj ? 1 : 0); }
 void launch_scatter(const Launch& L, bool fp64) {
     if (fp64) k_scatter<double><<<L.grid_p, 256, 0, L.stream>>>(L.sims, L.ptiles, L.nptiles);
     else k_scatter<float><<<L.grid_p, 256, 0, L.stream>>>(L.sims, L.ptiles, L.nptiles);
