@@ -323,3 +323,37 @@ def test_fused_parameters_match_plain_fp32(usp, name):
     assert np.all(Fb[14] > 0.05) or name != "couette"
     assert a.info()["counters"][5] == 0 and a.info()["counters"][6] == 0    # nothing lost or spilled
     assert np.allclose(Fa[14], Fb[14], atol=1e-4), (Fa[14][:8], Fb[14][:8])   # P_ne
+
+
+def test_fused_batch_one_step_matches_alone(usp):
+    """Simulations of different kinds (1-D and 2-D, walls, reservoirs, a
+    plate) stepped together in one batch give, after one step from the same
+    loaded states, the fields each gives alone: the batch's shared launches,
+    tile tables and per-simulation cell queues change nothing."""
+    bases = [W.couette(ny=20, ppc=100, Kn=0.1, seed=5), W.sod(ny=60, ppc_left=80, seed=5),
+             W.cavity(n=12, ppc=40, Kn=0.05, seed=5), W.slit(nx=20, ny=10, ppc=30, seed=5)]
+    states, alone, inbatch = [], [], []
+    for base in bases:
+        w = W.with_precision(base, "fp32")
+        w["params"]["pipeline"] = "fused"
+        g = usp.Simulation(dict(w, params=dict(w["params"], pipeline="plain"))).init_particles()
+        g.step(5)
+        P = g.particles()
+        states.append((w, P))
+        alone.append(usp.Simulation(w).set_particles(P["pos"], P["vel"], P["pid"]))
+        inbatch.append(usp.Simulation(w).set_particles(P["pos"], P["vel"], P["pid"]))
+    B = usp.Batch(hbm_budget=4 << 30, max_sims=len(bases))
+    for s in inbatch:
+        assert B.admit(s) == 0
+    B.step(1)
+    for s in alone:
+        s.step(1)
+    for s in inbatch:
+        B.retire(s)
+    for a, b in zip(alone, inbatch):
+        Fa, Fb = a.sample(), b.sample()
+        assert np.array_equal(Fa[15], Fb[15])
+        for k in (0, 1, 2, 3, 4):
+            assert np.allclose(Fa[k], Fb[k], rtol=1e-5, atol=1e-5 * np.abs(Fa[k]).max()), k
+        assert np.allclose(Fa[14], Fb[14], atol=1e-4)
+    B.close()
