@@ -28,7 +28,6 @@
 // read once more by k_g1.
 #include "usp_device.cuh"
 
-
 namespace usp {
 
 namespace {
@@ -621,32 +620,23 @@ __device__ void g2_cell(const SimDev* __restrict__ sims, const SimDev& s, int ce
             a0 = warp_sumf(a0); a1 = warp_sumf(a1); a2 = warp_sumf(a2); ae = warp_sumf(ae);
             b0 = warp_sumf(b0); b1 = warp_sumf(b1); b2 = warp_sumf(b2); be = warp_sumf(be);
             // FP32: the sums are taken about the cell mean, so the differences
-            // below do not cancel; an FP64 instruction would cost a whole warp
-            int ok = 0;
-            if (lane == 0) {
-                const float inv = 1.0f / nr;
-                const float Eo = ae - (a0 * a0 + a1 * a1 + a2 * a2) * inv;
-                const float En = be - (b0 * b0 + b1 * b1 + b2 * b2) * inv;
-                if (En > 0.0f && Eo >= 0.0f) {
-                    ok = 1;
-                    alpha = sqrtf(Eo / En);
-                    uo0 = f.u[0] + a0 * inv;
-                    uo1 = f.u[1] + a1 * inv;
-                    uo2 = f.u[2] + a2 * inv;
-                    mn0 = b0 * inv;
-                    mn1 = b1 * inv;
-                    mn2 = b2 * inv;
-                    atomicAdd(&s.dyn->counters[kCntRelaxed], (unsigned long long)(unsigned)nr);
-                }
+            // below do not cancel.  The butterfly sums are bitwise the same on
+            // every lane (each stage adds the same two values), so every lane
+            // computes the same factors without a broadcast.
+            const float inv = 1.0f / nr;
+            const float Eo = ae - (a0 * a0 + a1 * a1 + a2 * a2) * inv;
+            const float En = be - (b0 * b0 + b1 * b1 + b2 * b2) * inv;
+            if (En > 0.0f && Eo >= 0.0f) {
+                apply = true;
+                alpha = sqrtf(Eo / En);
+                uo0 = f.u[0] + a0 * inv;
+                uo1 = f.u[1] + a1 * inv;
+                uo2 = f.u[2] + a2 * inv;
+                mn0 = b0 * inv;
+                mn1 = b1 * inv;
+                mn2 = b2 * inv;
+                if (lane == 0) atomicAdd(&s.dyn->counters[kCntRelaxed], (unsigned long long)(unsigned)nr);
             }
-            apply = __shfl_sync(0xffffffffu, ok, 0) != 0;
-            alpha = __shfl_sync(0xffffffffu, alpha, 0);
-            uo0 = __shfl_sync(0xffffffffu, uo0, 0);
-            uo1 = __shfl_sync(0xffffffffu, uo1, 0);
-            uo2 = __shfl_sync(0xffffffffu, uo2, 0);
-            mn0 = __shfl_sync(0xffffffffu, mn0, 0);
-            mn1 = __shfl_sync(0xffffffffu, mn1, 0);
-            mn2 = __shfl_sync(0xffffffffu, mn2, 0);
         }
     }
 
