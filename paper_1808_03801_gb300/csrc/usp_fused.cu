@@ -1059,6 +1059,21 @@ __global__ void __launch_bounds__(128) k_params_f(const SimDev* __restrict__ sim
         for (int cc = threadIdx.x; cc < kCTile; cc += blockDim.x) {
             const int cell = tile.y + cc;
             if (cell >= K) break;
+            // every load of the cell first (one round of latency): the
+            // running averages, the neighbours' states for the stencil, then
+            // the cell's own sums
+            const bool first = s.dyn->nsamples == 0;
+            double av[kNFields];
+#pragma unroll
+            for (int k = 0; k < kNFields; ++k) av[k] = first ? 0.0 : s.avg[(size_t)k * K + cell];
+            LocalF Nm[2] = {}, Np[2] = {};
+            bool hm[2] = {false, false}, hp[2] = {false, false};
+            if (s.mode == kModeUSP) {
+                for (int axis = s.dim == 1 ? 1 : 0; axis < 2; ++axis) {
+                    hm[axis] = nb_state(sims, s, cell, axis, -1, Nm[axis]);
+                    hp[axis] = nb_state(sims, s, cell, axis, +1, Np[axis]);
+                }
+            }
             LocalF L;
             double u[3] = {0, 0, 0}, P[6], th = 0, inv;
             local_f(s, cell, L, u, P, &th, inv);
@@ -1093,9 +1108,10 @@ __global__ void __launch_bounds__(128) k_params_f(const SimDev* __restrict__ sim
                     float g2[3] = {0, 0, 0};
                     for (int axis = s.dim == 1 ? 1 : 0; axis < 2; ++axis) {
                         const float h = (float)(axis == 0 ? s.dx : s.dy);
-                        LocalF Lm{}, Lp{};
-                        const int m = nb_state(sims, s, cell, axis, -1, Lm) ? 1 : -1;
-                        const int p = nb_state(sims, s, cell, axis, +1, Lp) ? 1 : -1;
+                        const LocalF& Lm = Nm[axis];
+                        const LocalF& Lp = Np[axis];
+                        const int m = hm[axis] ? 1 : -1;
+                        const int p = hp[axis] ? 1 : -1;
                         const float Qm[3] = {Lm.n, Lm.T, Lm.umag}, Qp[3] = {Lp.n, Lp.T, Lp.umag};
                         for (int k = 0; k < 3; ++k) {
                             float d = 0.0f;
@@ -1178,11 +1194,10 @@ __global__ void __launch_bounds__(128) k_params_f(const SimDev* __restrict__ sim
 #pragma unroll
                 for (int k = 0; k < kNFPrm / 4; ++k) dst[k] = make_float4(pr[4 * k], pr[4 * k + 1], pr[4 * k + 2], pr[4 * k + 3]);
             }
-            const bool first = s.dyn->nsamples == 0;
+#pragma unroll
             for (int k = 0; k < kNFields; ++k) {
                 s.inst[(size_t)k * K + cell] = f[k];
-                double* a = &s.avg[(size_t)k * K + cell];
-                *a = first ? f[k] : s.avg_keep * *a + f[k] * s.avg_new;                         // Eq. 34
+                s.avg[(size_t)k * K + cell] = first ? f[k] : s.avg_keep * av[k] + f[k] * s.avg_new;   // Eq. 34
             }
         }
     }
