@@ -82,7 +82,7 @@ struct orc_sim {
     cell_params* par;
     double* inst;                /* ORC_NFIELDS x K */
     double* avg;
-    int64_t counters[4];
+    int64_t counters[5];
 };
 
 /* ------------------------------------------------------------------------ */
@@ -136,6 +136,15 @@ orc_sim* orc_create(const orc_config* cfg) {
     if (cfg->mass <= 0 || cfg->T_ref <= 0 || cfg->Pr <= 0 || cfg->n_ref <= 0 || cfg->ppc_ref < 1) return NULL;
     /* a body force may act only along directions that are not resolved */
     if (cfg->body_accel[1] != 0 || (cfg->dim == 2 && cfg->body_accel[0] != 0)) return NULL;
+    /* the counting plane lies strictly inside the domain, across an axis
+     * whose faces are not periodic */
+    if (cfg->flux_axis < 0 || cfg->flux_axis > 2) return NULL;
+    if (cfg->flux_axis) {
+        int a = cfg->flux_axis - 1;
+        if (a == 0 && cfg->dim != 2) return NULL;
+        if (cfg->face_kind[2 * a] == ORC_BC_PERIODIC) return NULL;
+        if (!(cfg->flux_pos > cfg->lo[a] && cfg->flux_pos < cfg->hi[a])) return NULL;
+    }
     orc_sim* s = (orc_sim*)calloc(1, sizeof(orc_sim));
     s->cfg = *cfg;
     if (cfg->dim == 1) s->cfg.nx = 1;
@@ -398,6 +407,24 @@ static void stream_one(orc_sim* s, particle* q) {
     }
     if (c->dim == 2 && c->face_kind[0] == ORC_BC_PERIODIC) q->x = wrap(q->x, c->lo[0], c->hi[0]);
     if (c->face_kind[2] == ORC_BC_PERIODIC) q->y = wrap(q->y, c->lo[1], c->hi[1]);
+}
+
+/* 1 when the particle is at or above the counting plane, 0 below it */
+static int flux_side(const orc_config* c, const particle* q) {
+    double v = c->flux_axis == 1 ? q->x : q->y;
+    return v >= c->flux_pos;
+}
+
+/* advection of every particle; the net flow through the counting plane is
+ * the change of side summed over the particles (a particle that leaves
+ * through a reservoir face ends on that face) */
+static void stream_phase(orc_sim* s) {
+    for (int64_t i = 0; i < s->np; ++i) {
+        particle* q = &s->p[i];
+        int before = s->cfg.flux_axis ? flux_side(&s->cfg, q) : 0;
+        stream_one(s, q);
+        if (s->cfg.flux_axis) s->counters[4] += flux_side(&s->cfg, q) - before;
+    }
 }
 
 /* ------------------------------------------------------------------------ */
@@ -761,9 +788,7 @@ static void sample_phase(orc_sim* s) {
 int orc_phase(orc_sim* s, int phase) {
     if (!s) return -1;
     switch (phase) {
-    case ORC_PH_STREAM:
-        for (int64_t i = 0; i < s->np; ++i) stream_one(s, &s->p[i]);
-        return 0;
+    case ORC_PH_STREAM: stream_phase(s); return 0;
     case ORC_PH_RESERVOIR: reservoir_phase(s); return 0;
     case ORC_PH_SORT: sort_phase(s); return 0;
     case ORC_PH_MOMENTS: moments_phase(s); return 0;

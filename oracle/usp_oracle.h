@@ -59,6 +59,10 @@ typedef struct {
     int mode;                  /* ORC_MODE_* */
     double fixed_pne;
     int reservoir_cols;        /* buffer cell layers next to a reservoir face */
+    /* counting plane for the mass flow rate of Eq. 41: normal to x (1) or
+     * y (2) at flux_pos; 0 = none */
+    int flux_axis;
+    double flux_pos;
 } orc_config;
 
 typedef struct {
@@ -99,7 +103,9 @@ int orc_get_fields(const orc_sim* s, int averaged, double* out);
 /* per-cell relaxation parameters: [K][16] = u0,u1,u2, theta, L00,L10,L11,L20,L21,L22,
  * P_relax, nu, nu_ES, P_ne, valid, n_relaxed */
 int orc_get_params(const orc_sim* s, double* out);
-/* counters: [0] Cholesky fallbacks, [1] bounce-cap clamps, [2] removed, [3] injected */
+/* counters: [0] Cholesky fallbacks, [1] bounce-cap clamps, [2] removed, [3] injected,
+ * [4] net particles through the counting plane (+1 for each advection that
+ * starts below flux_pos and ends at or above it, -1 for the reverse) */
 int orc_get_counters(const orc_sim* s, int64_t* out);
 
 #ifdef __cplusplus

@@ -14,7 +14,8 @@ A workload is a plain dict:
     segments: zero-thickness plates normal to x: pos, lo, hi, kind, T, u
     params  : Kn, L_ref, n_ref, dt [s] (0: use dt_over_tauc), dt_over_tauc,
               body_accel, ppc_ref, n_avg, mode ('usp' | 'sp' | 'fixed'),
-              fixed_pne, reservoir_cols, precision ('fp64' | 'fp32')
+              fixed_pne, reservoir_cols, precision ('fp64' | 'fp32'),
+              flux_axis / flux_pos (optional counting plane)
     regions : initial uniform boxes: lo, hi, n, T, u
     seed    : key of the counter-based generator
     steps   : number of time steps of the full problem
@@ -108,23 +109,48 @@ def cavity(n=200, ppc=100, Kn=1e-3, dt_over_tauc=None, u_lid=50.0, precision="fp
 
 
 def slit(nx=400, ny=200, ppc=200, Kn=1e-2, dt_over_tauc=1.0, pressure_ratio=10.0, precision="fp32",
-         steps=2000, seed=1, reservoir_cols=2):
+         steps=2000, seed=1, reservoir_cols=2, delta=None):
     """2-D flow through a slit (Sec. 4.5), upper half domain: x in [-10a, 10a],
     y in [0, 10a]; specular symmetry plane at y = 0; diffuse wall at y = 10a;
     a zero-thickness diffuse plate at x = 0 for y >= a/2; reservoir buffer
     columns at both x ends (upstream n_1, downstream n_1 / pressure_ratio at
-    the same temperature).  Hard-sphere gas; Kn refers to the slit width a.
-    The whole domain starts at the upstream state."""
+    the same temperature; pressure_ratio = inf gives the paper's vacuum).
+    Hard-sphere gas; Kn refers to the slit width a, unless the rarefaction
+    parameter delta is given: then the viscosity at the upstream state
+    follows Eq. 40 (mu_1 = a p_1 / (delta v_1), v_1 = sqrt(2 k T_1 / m)).
+    The whole domain starts at the upstream state.  A counting plane at
+    x = 0 gives the net particle flow through the slit (Eq. 41)."""
     a = 1.0e-5
     lo, hi = (-10.0 * a, 0.0), (10.0 * a, 10.0 * a)
-    faces = [_face("reservoir", T0, (0, 0, 0), N0), _face("reservoir", T0, (0, 0, 0), N0 / pressure_ratio),
+    n_down = 0.0 if math.isinf(pressure_ratio) else N0 / pressure_ratio
+    faces = [_face("reservoir", T0, (0, 0, 0), N0), _face("reservoir", T0, (0, 0, 0), n_down),
              _face("specular"), _face("diffuse")]
     w = _base(2, nx, ny, lo, hi, faces, Kn=Kn, L_ref=a, dt_over_tauc=dt_over_tauc, ppc=ppc, omega=0.5,
               precision=precision, steps=steps, seed=seed)
     w["segments"] = [{"pos": 0.0, "lo": 0.5 * a, "hi": 10.0 * a, "kind": "diffuse", "T": T0,
                       "u": (0.0, 0.0, 0.0)}]
     w["params"]["reservoir_cols"] = reservoir_cols
+    w["params"]["flux_axis"] = 1
+    w["params"]["flux_pos"] = 0.0
+    w["slit_width"] = a
+    if delta is not None:
+        kB = 1.380649e-23
+        p1 = N0 * kB * T0
+        v1 = math.sqrt(2.0 * kB * T0 / M_AR)
+        w["gas"]["mu_ref"] = a * p1 / (delta * v1)
     return w
+
+
+# Table 7: (cells along x, cells along y, dt / tau_c,1) of the paper's slit cases
+SLIT_CASES = {1: (580, 280, 0.2), 2: (580, 280, 1.0), 3: (580, 280, 2.0), 4: (280, 140, 3.0),
+              5: (160, 80, 4.0), 6: (160, 80, 5.0)}
+
+
+def slit_case(case=4, ppc=100, precision="fp32", steps=4000, seed=1):
+    """A slit case of Table 7: delta = 20, vacuum downstream."""
+    nx, ny, r = SLIT_CASES[case]
+    return slit(nx=nx, ny=ny, ppc=ppc, dt_over_tauc=r, pressure_ratio=math.inf, precision=precision,
+                steps=steps, seed=seed, delta=20.0)
 
 
 def homogeneous_box(ppc=1000, Kn=0.05, dt_over_tauc=0.5, mode="usp", precision="fp64", Pr=PR_MONO,
