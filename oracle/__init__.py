@@ -45,7 +45,7 @@ class _Config(ctypes.Structure):
         ("body_accel", ctypes.c_double * 3),
         ("ppc_ref", ctypes.c_int), ("n_avg", ctypes.c_int), ("mode", ctypes.c_int),
         ("fixed_pne", ctypes.c_double), ("reservoir_cols", ctypes.c_int),
-        ("flux_axis", ctypes.c_int), ("flux_pos", ctypes.c_double),
+        ("flux_axis", ctypes.c_int), ("flux_pos", ctypes.c_double), ("gll_average", ctypes.c_int),
     ]
 
 
@@ -144,6 +144,7 @@ def make_config(w: dict) -> _Config:
     c.ppc_ref, c.n_avg, c.mode = pr["ppc_ref"], pr["n_avg"], _MODE[pr["mode"]]
     c.fixed_pne, c.reservoir_cols = pr["fixed_pne"], pr["reservoir_cols"]
     c.flux_axis, c.flux_pos = int(pr.get("flux_axis", 0)), float(pr.get("flux_pos", 0.0))
+    c.gll_average = int(pr.get("gll_average", 0))
     return c
 
 

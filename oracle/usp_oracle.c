@@ -67,6 +67,12 @@ typedef struct {
     int n_relaxed;
 } cell_params;
 
+/* the state a cell contributes to the Kn_GLL stencil (Eqs. 17-18) */
+typedef struct {
+    int valid;
+    double n, T, umag, a_sound, lambda;
+} grad_state;
+
 struct orc_sim {
     orc_config cfg;
     double R, dt, mu_ref, w;     /* gas constant, time step, reference viscosity, density per particle */
@@ -80,6 +86,7 @@ struct orc_sim {
     int nsamples;
     cell_moments* mom;
     cell_params* par;
+    grad_state* gs;
     double* inst;                /* ORC_NFIELDS x K */
     double* avg;
     int64_t counters[5];
@@ -167,6 +174,7 @@ orc_sim* orc_create(const orc_config* cfg) {
     s->K = s->cfg.nx * cfg->ny;
     s->mom = (cell_moments*)calloc(s->K, sizeof(cell_moments));
     s->par = (cell_params*)calloc(s->K, sizeof(cell_params));
+    s->gs = (grad_state*)calloc((size_t)s->K, sizeof(grad_state));
     s->inst = (double*)calloc((size_t)ORC_NFIELDS * s->K, sizeof(double));
     s->avg = (double*)calloc((size_t)ORC_NFIELDS * s->K, sizeof(double));
     return s;
@@ -174,7 +182,7 @@ orc_sim* orc_create(const orc_config* cfg) {
 
 void orc_destroy(orc_sim* s) {
     if (!s) return;
-    free(s->p); free(s->mom); free(s->par); free(s->inst); free(s->avg);
+    free(s->p); free(s->mom); free(s->par); free(s->gs); free(s->inst); free(s->avg);
     free(s);
 }
 
@@ -552,9 +560,9 @@ static int neighbor(const orc_sim* s, int cell, int axis, int dir) {
 static double deriv(const orc_sim* s, int cell, int axis, int which) {
     double h = axis == 0 ? s->dx : s->dy;
     int m = neighbor(s, cell, axis, -1), p = neighbor(s, cell, axis, +1);
-    if (m >= 0 && !s->par[m].valid) m = -1;
-    if (p >= 0 && !s->par[p].valid) p = -1;
-    const cell_params* P = s->par;
+    if (m >= 0 && !s->gs[m].valid) m = -1;
+    if (p >= 0 && !s->gs[p].valid) p = -1;
+    const grad_state* P = s->gs;
     double qc, qm = 0, qp = 0;
 #define FIELD(i) (which == 0 ? P[i].n : which == 1 ? P[i].T : P[i].umag)
     qc = FIELD(cell);
@@ -587,6 +595,32 @@ static void params_phase(orc_sim* s) {
         P->nu_es = c->Pr * P->nu;                                    /* ESBGK frequency, Eq. 6a */
         P->lambda = 16.0 / (5.0 * sqrt(2.0 * PI)) * P->mu / sqrt(rho * P->p);   /* Eq. 36 */
     }
+    /* states seen by the Kn_GLL stencil: the instantaneous ones, or the
+     * Eq. 34 averages of n, u, T (with lambda of Eq. 36 at the averaged
+     * state) */
+    const int averaged = c->gll_average && s->nsamples > 0;
+    for (int cell = 0; cell < s->K; ++cell) {
+        grad_state* G = &s->gs[cell];
+        const cell_params* P = &s->par[cell];
+        if (!averaged) {
+            G->valid = P->valid;
+            G->n = P->n; G->T = P->T; G->umag = P->umag; G->a_sound = P->a_sound; G->lambda = P->lambda;
+            continue;
+        }
+        const double* A = s->avg;
+        const int K = s->K;
+        G->n = A[cell];
+        G->T = A[(size_t)4 * K + cell];
+        double u0 = A[(size_t)1 * K + cell], u1 = A[(size_t)2 * K + cell], u2 = A[(size_t)3 * K + cell];
+        G->umag = sqrt(u0 * u0 + u1 * u1 + u2 * u2);
+        G->valid = G->n > 0 && G->T > 0;
+        if (!G->valid) continue;
+        double theta = s->R * G->T;
+        G->a_sound = sqrt(GAMMA_MONO * theta);
+        double rho = G->n * c->mass, p = rho * theta;
+        double mu = s->mu_ref * pow(G->T / c->T_ref, c->omega);                  /* Eq. 35 */
+        G->lambda = 16.0 / (5.0 * sqrt(2.0 * PI)) * mu / sqrt(rho * p);           /* Eq. 36 */
+    }
     /* pass 2: GLL Knudsen number, P_ne, corrected moments, ES covariance */
     for (int cell = 0; cell < s->K; ++cell) {
         cell_moments* M = &s->mom[cell];
@@ -596,20 +630,26 @@ static void params_phase(orc_sim* s) {
         if (c->mode == ORC_MODE_SP) pne = 0.0;
         else if (c->mode == ORC_MODE_FIXED_PNE) pne = c->fixed_pne;
         else {
-            double g[3];
-            for (int q = 0; q < 3; ++q) {
-                double sum = 0;
-                for (int axis = c->dim == 1 ? 1 : 0; axis < 2; ++axis) {
-                    double d = deriv(s, cell, axis, q);
-                    sum += d * d;
+            /* a cell whose own stencil state is missing (never sampled as
+             * valid) has no gradient: Kn_GLL = 0 */
+            const grad_state* G = &s->gs[cell];
+            double kn = 0.0;
+            if (G->valid) {
+                double g[3];
+                for (int q = 0; q < 3; ++q) {
+                    double sum = 0;
+                    for (int axis = c->dim == 1 ? 1 : 0; axis < 2; ++axis) {
+                        double d = deriv(s, cell, axis, q);
+                        sum += d * d;
+                    }
+                    g[q] = sqrt(sum);
                 }
-                g[q] = sqrt(sum);
+                double kn_rho = G->lambda * g[0] / G->n;                      /* Eq. 18, Q = rho */
+                double kn_T = G->lambda * g[1] / G->T;                        /* Eq. 18, Q = T */
+                double kn_u = G->lambda * g[2] / fmax(G->umag, G->a_sound);   /* Eq. 18, Q = |u| */
+                kn = fmax(kn_rho, fmax(kn_T, kn_u));                          /* Eq. 17 */
             }
-            double kn_rho = P->lambda * g[0] / P->n;                      /* Eq. 18, Q = rho */
-            double kn_T = P->lambda * g[1] / P->T;                        /* Eq. 18, Q = T */
-            double kn_u = P->lambda * g[2] / fmax(P->umag, P->a_sound);   /* Eq. 18, Q = |u| */
-            double kn = fmax(kn_rho, fmax(kn_T, kn_u));                   /* Eq. 17 */
-            pne = exp(-kn / KN_C);                                        /* Eq. 16 */
+            pne = exp(-kn / KN_C);                                            /* Eq. 16 */
         }
         P->pne = pne;
         double fs = 1.0 + 0.5 * s->dt * P->nu * pne;            /* Eq. 33, stress */

@@ -63,6 +63,11 @@ typedef struct {
      * y (2) at flux_pos; 0 = none */
     int flux_axis;
     double flux_pos;
+    /* 1: the Kn_GLL of Eqs. 17-18 is taken from the Eq. 34 averaged fields
+     * (n, u, T of every cell) once at least one sample exists -- the time
+     * averaging that Sec. 3 applies to steady flows to cut statistical
+     * noise; 0: from the instantaneous moments */
+    int gll_average;
 } orc_config;
 
 typedef struct {
