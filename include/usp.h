@@ -141,7 +141,23 @@ typedef struct {
  *                  another slab are written into that slab's buckets, and the
  *                  Kn_GLL stencil (Eq. 18) reads the adjacent slab's row.
  *                  Requires the fused pipeline, no reservoir faces, and ny a
- *                  multiple of slab_count; 0 or 1 means no decomposition. */
+ *                  multiple of slab_count; 0 or 1 means no decomposition.
+ *   flux_axis, flux_pos: a counting plane normal to axis x (flux_axis 1) or
+ *                  y (2) at coordinate flux_pos, strictly inside the domain
+ *                  along a non-periodic axis (1-D grids: y only); 0 = none.
+ *                  Every advection adds +1 to counters[7] for a particle
+ *                  that starts below the plane (coordinate < flux_pos) and
+ *                  ends at or above it, -1 for the reverse; a particle that
+ *                  leaves through a reservoir face ends at that face.  The
+ *                  sum is the net number of particles through the plane,
+ *                  which gives the mass flow rate of Eq. 41 (slit).
+ *   gll_average  : 1 takes the Kn_GLL of Eqs. 17-18 (hence P_ne, Eq. 16)
+ *                  from the Eq. 34 averaged fields n, u, T of every cell
+ *                  (lambda of Eq. 36 at the averaged state) once a sample
+ *                  exists -- the time averaging the paper applies to steady
+ *                  flows to cut statistical noise; a cell whose averaged
+ *                  state is empty has Kn_GLL = 0.  0 (default): from the
+ *                  instantaneous moments of the step. */
 typedef struct {
     double Kn, L_ref, n_ref;
     double dt, dt_over_tauc;
@@ -153,6 +169,9 @@ typedef struct {
     int pipeline;
     double capacity_factor;
     int slab_count, slab_index, slab_group;
+    int flux_axis;
+    double flux_pos;
+    int gll_average;
 } usp_params;
 
 /* A box of initial gas at number density n, temperature T, velocity u. */
@@ -181,7 +200,8 @@ typedef struct {
     int64_t counters[8];  /* cumulative: 0 Cholesky fallbacks, 1 bounce-cap clamps,
                              2 removed, 3 injected, 4 relaxed, 5 particles lost to
                              slot overflow (must stay 0), 6 particles spilled past
-                             a full bucket (fused pipeline), 7 reserved */
+                             a full bucket (fused pipeline), 7 net particles
+                             through the counting plane (signed; params.flux_axis) */
     size_t device_bytes;  /* device memory held by the handle */
 } usp_info;
 
@@ -191,7 +211,8 @@ typedef struct {
  * and the legacy default stream cannot be captured).  Derives mu_ref (Eq. 36) and dt (Eq. 37), allocates per-cell
  * arrays; particle storage is allocated by usp_init_particles /
  * usp_set_particles.  Errors: INVALID_ARG for inconsistent input (periodic
- * on one face of an axis, resolved-axis body force, non-positive sizes),
+ * on one face of an axis, resolved-axis body force, non-positive sizes, a
+ * counting plane outside the domain or on a periodic axis),
  * OOM, CUDA. */
 int usp_create(const usp_gas* gas, const usp_grid* grid, const usp_bc faces[4],
                const usp_wall_segment* segs, int nseg, const usp_params* params,

@@ -243,6 +243,14 @@ extern "C" int usp_create(const usp_gas* gas, const usp_grid* grid, const usp_bc
         }
     }
     if (any_res && prm->reservoir_cols < 1) return USP_ERR_INVALID_ARG;
+    if (prm->flux_axis < 0 || prm->flux_axis > 2) return USP_ERR_INVALID_ARG;
+    if (prm->gll_average < 0 || prm->gll_average > 1) return USP_ERR_INVALID_ARG;
+    if (prm->flux_axis) {
+        const int a = prm->flux_axis - 1;
+        if (a == 0 && grid->dim != 2) return USP_ERR_INVALID_ARG;
+        if (faces[2 * a].kind == USP_BC_PERIODIC) return USP_ERR_INVALID_ARG;
+        if (!(prm->flux_pos > grid->lo[a] && prm->flux_pos < grid->hi[a])) return USP_ERR_INVALID_ARG;
+    }
     const bool slab = prm->slab_count > 1;
     if (prm->slab_count < 0) return USP_ERR_INVALID_ARG;
     if (slab && (prm->pipeline != USP_PIPE_FUSED || any_res || grid->ny % prm->slab_count != 0 ||
@@ -313,6 +321,10 @@ extern "C" int usp_create(const usp_gas* gas, const usp_grid* grid, const usp_bc
     s.avg_new = 1.0 / prm->n_avg;
     s.mode = prm->mode;
     s.fixed_pne = prm->fixed_pne;
+    s.flux_axis = prm->flux_axis;
+    s.flux_pos = prm->flux_pos;
+    s.f_flux_pos = (float)prm->flux_pos;
+    s.gll_average = prm->gll_average != 0;
     for (int d = 0; d < 3; ++d) s.body[d] = prm->body_accel[d];
     for (int f = 0; f < 4; ++f) {
         s.face[f].kind = faces[f].kind;
@@ -369,6 +381,7 @@ extern "C" int usp_create(const usp_gas* gas, const usp_grid* grid, const usp_bc
     CALLOC(inj_count, uint32_t, K);
     CALLOC(inj_pidoff, uint32_t, K);
     CALLOC(fprm, float, (size_t)kNFPrm * K);
+    if (prm->gll_average && prm->pipeline == USP_PIPE_PLAIN) { CALLOC(gavg, double, 3 * (size_t)K); }
     if (prm->pipeline == USP_PIPE_FUSED) {
         CALLOC(momf, float, 16 * (size_t)K);
         CALLOC(floc, float, 4 * (size_t)K);

@@ -204,6 +204,17 @@ __device__ bool advect(const SimDev& s, uint32_t step, uint32_t pid, T& x, T& y,
     return true;
 }
 
+// net flow through the counting plane: +1 for a particle that moved from
+// below the plane to at or above it, -1 for the reverse (the FP32 path
+// compares with the plane position rounded to FP32)
+template <class T>
+__device__ __forceinline__ void count_flux(const SimDev& s, T x0, T y0, T x1, T y1) {
+    const T p = sizeof(T) == 4 ? (T)s.f_flux_pos : (T)s.flux_pos;
+    const bool a = (s.flux_axis == 1 ? x0 : y0) >= p;
+    const bool b = (s.flux_axis == 1 ? x1 : y1) >= p;
+    if (a != b) atomicAdd(&s.dyn->counters[kCntFlux], b ? 1ull : ~0ull);   // ~0 is -1 modulo 2^64
+}
+
 // warp-aggregated increment of counter[key]; returns this lane's offset
 __device__ __forceinline__ uint32_t aggregated_add(uint32_t* counter, uint32_t key) {
     unsigned active = __activemask();
@@ -309,6 +320,52 @@ __device__ __forceinline__ void local_state(const SimDev& s, int cell, Local& L,
     L.mu = s.mu_ref * pow(L.T / s.T_ref, s.omega);                              // Eq. 35
     L.nu = L.p / L.mu;                                                          // nu = p / mu
     L.lambda = 16.0 / (5.0 * sqrt(2.0 * kPi)) * L.mu / sqrt(L.rho * L.p);       // Eq. 36
+}
+
+// state a cell contributes to the Kn_GLL stencil (Eqs. 17-18): its
+// instantaneous state, or (gll_average, after the first sample) the Eq. 34
+// averages of n, u, T with lambda of Eq. 36 at that state
+struct GradState {
+    int valid;
+    double n, T, umag, a_sound, lambda;
+};
+
+__device__ __forceinline__ bool gll_averaged(const SimDev& s) { return s.gll_average && s.dyn->nsamples > 0; }
+
+// plain pipeline: k_moments copies the averaged n, T, |u| of its cell into
+// gavg ([3][K]) before k_params updates the averages, so that the stencil
+// reads every neighbour's average as it stood at the start of the step
+__device__ __forceinline__ void snap_avg(const SimDev& s, int cell) {
+    const int K = s.K;
+    const double* A = s.avg;
+    const double u0 = A[(size_t)1 * K + cell], u1 = A[(size_t)2 * K + cell], u2 = A[(size_t)3 * K + cell];
+    s.gavg[cell] = A[cell];
+    s.gavg[(size_t)K + cell] = A[(size_t)4 * K + cell];
+    s.gavg[(size_t)2 * K + cell] = sqrt(u0 * u0 + u1 * u1 + u2 * u2);
+}
+
+__device__ __forceinline__ void grad_from_avg(const SimDev& s, int cell, GradState& G) {
+    const int K = s.K;
+    G.n = s.gavg[cell];
+    G.T = s.gavg[(size_t)K + cell];
+    G.umag = s.gavg[(size_t)2 * K + cell];
+    G.valid = G.n > 0.0 && G.T > 0.0;
+    G.a_sound = G.lambda = 0.0;
+    if (!G.valid) return;
+    const double theta = s.R * G.T;
+    G.a_sound = sqrt(kGammaMono * theta);
+    const double rho = G.n * s.mass, p = rho * theta;
+    const double mu = s.mu_ref * pow(G.T / s.T_ref, s.omega);                 // Eq. 35
+    G.lambda = 16.0 / (5.0 * sqrt(2.0 * kPi)) * mu / sqrt(rho * p);           // Eq. 36
+}
+
+__device__ __forceinline__ void grad_from_local(const Local& L, GradState& G) {
+    G.valid = L.valid;
+    G.n = L.n;
+    G.T = L.T;
+    G.umag = L.umag;
+    G.a_sound = L.a_sound;
+    G.lambda = L.lambda;
 }
 
 __device__ __forceinline__ int neighbor(const SimDev& s, int cell, int axis, int dir) {

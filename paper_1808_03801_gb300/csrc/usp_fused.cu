@@ -708,6 +708,7 @@ __device__ void g2_cell(const SimDev* __restrict__ sims, const SimDev& s, int ce
                         atomicAdd(&s.dyn->counters[kCntRemoved], 1ull);
                     }
                 }
+                if (s.flux_axis) count_flux<float>(s, DIM == 2 ? S.x[j] : 0.0f, S.y[j], x, y);
                 if (DIM == 2) S.x[j] = x;
                 S.y[j] = y; S.v0[j] = c[0]; S.v1[j] = c[1]; S.v2[j] = c[2];
                 S.sel[j] = ws;
@@ -943,9 +944,19 @@ __global__ void __launch_bounds__(256) k_g1(const SimDev* __restrict__ sims, con
                 s.momf[(size_t)cell * 16 + lane] = v;   // one 64-byte record per cell
             }
             if (lane == 31) {
-                // local state of the cell for its neighbours' Kn_GLL (FP32)
+                // local state of the cell for its neighbours' Kn_GLL (FP32):
+                // the instantaneous one, or the Eq. 34 average as it stood at
+                // the start of the step (k_params_f updates it later)
                 float nn = (float)n * s.f_w, T = 0.0f, um = 0.0f, valid = 0.0f;
-                if (n >= 2) {
+                if (s.gll_average && s.dyn->nsamples > 0) {
+                    const int K = s.K;
+                    const double a1 = s.avg[(size_t)1 * K + cell], a2 = s.avg[(size_t)2 * K + cell],
+                                 a3 = s.avg[(size_t)3 * K + cell];
+                    nn = (float)s.avg[cell];
+                    T = (float)s.avg[(size_t)4 * K + cell];
+                    um = (float)sqrt(a1 * a1 + a2 * a2 + a3 * a3);
+                    valid = nn > 0.0f && T > 0.0f ? 1.0f : 0.0f;
+                } else if (n >= 2) {
                     const float inv2 = 1.0f / (float)n;
                     const float d0 = S[0] * inv2, d1 = S[1] * inv2, d2 = S[2] * inv2;
                     const float th = ((S[3] + S[4] + S[5]) * inv2 - (d0 * d0 + d1 * d1 + d2 * d2)) * (1.0f / 3.0f);
@@ -1099,12 +1110,29 @@ __global__ void __launch_bounds__(128) k_params_f(const SimDev* __restrict__ sim
                 if (s.mode == kModeSP) pne = 0.0f;
                 else if (s.mode == kModeFixed) pne = (float)s.fixed_pne;
                 else {
+                    // the cell's own stencil state: instantaneous, or the
+                    // Eq. 34 average (loaded above, before this step's update)
+                    float gn = L.n, gT = L.T, gu = L.umag, glam = lam, ga = sqrtf((float)kGammaMono * thf);
+                    bool gvalid = true;
+                    if (s.gll_average && !first) {
+                        gn = (float)av[0];
+                        gT = (float)av[4];
+                        gu = (float)sqrt(av[1] * av[1] + av[2] * av[2] + av[3] * av[3]);
+                        gvalid = gn > 0.0f && gT > 0.0f;
+                        if (gvalid) {
+                            const float gth = gT * (float)s.R;
+                            const float grho = gn * (float)s.mass;
+                            const float gmu = (float)s.mu_ref * __powf(gT / (float)s.T_ref, (float)s.omega);
+                            glam = 1.2766152f * gmu / sqrtf(grho * grho * gth);   // Eq. 36 at the averaged state
+                            ga = sqrtf((float)kGammaMono * gth);
+                        }
+                    }
                     // the gradients are taken relative to the cell's own value
                     // (|grad Q| / Q): absolute density gradients (~1e25 m^-3 over
                     // sub-micron cells) would overflow FP32 when squared
-                    const float a_s = sqrtf((float)kGammaMono * thf);
-                    const float Qc[3] = {L.n, L.T, L.umag};
-                    const float rq[3] = {1.0f / L.n, 1.0f / L.T, 1.0f / fmaxf(L.umag, a_s)};
+                    const float a_s = ga;
+                    const float Qc[3] = {gn, gT, gu};
+                    const float rq[3] = {1.0f / gn, 1.0f / gT, 1.0f / fmaxf(gu, a_s)};
                     float g2[3] = {0, 0, 0};
                     for (int axis = s.dim == 1 ? 1 : 0; axis < 2; ++axis) {
                         const float h = (float)(axis == 0 ? s.dx : s.dy);
@@ -1121,7 +1149,7 @@ __global__ void __launch_bounds__(128) k_params_f(const SimDev* __restrict__ sim
                             g2[k] += d * d;
                         }
                     }
-                    const float kn = lam * sqrtf(fmaxf(g2[0], fmaxf(g2[1], g2[2])));
+                    const float kn = gvalid ? glam * sqrtf(fmaxf(g2[0], fmaxf(g2[1], g2[2]))) : 0.0f;
                     pne = __expf(-kn / (float)kKnC);                                              // Eqs. 16-18
                 }
                 // Eq. 33; FP64 divisions are costly here, so each factor is

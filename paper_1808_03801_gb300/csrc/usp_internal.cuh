@@ -23,7 +23,7 @@ enum { kModeUSP = 0, kModeSP = 1, kModeFixed = 2 };
 
 // counters (u64, device)
 enum { kCntChol = 0, kCntClamp = 1, kCntRemoved = 2, kCntInjected = 3, kCntRelaxed = 4, kCntOverflow = 5,
-       kCntSpilled = 6 };
+       kCntSpilled = 6, kCntFlux = 7 };
 
 struct FaceDev {
     int kind;
@@ -72,9 +72,14 @@ struct alignas(16) SimDev {
     // slab_first is the batch index of slab 0 (-1 outside a batch)
     int slab_count, slab_index, slab_first, row0, rows;
     // single-precision copies for the FP32 kernels (set on the host)
-    float f_dt, f_lo[2], f_hi[2], f_inv_dx, f_inv_dy, f_bdt[3], f_w, f_inv_R;
+    float f_dt, f_lo[2], f_hi[2], f_inv_dx, f_inv_dy, f_bdt[3], f_w, f_inv_R, f_flux_pos;
     int mode;
     double fixed_pne;
+    // counting plane of the mass flow (Eq. 41): normal to x (1) or y (2) at
+    // flux_pos; 0 = none
+    int flux_axis;
+    double flux_pos;
+    int gll_average;      // Kn_GLL from the Eq. 34 averages once a sample exists
     double body[3];
     uint32_t key0, key1;
     int64_t cap;
@@ -91,6 +96,7 @@ struct alignas(16) SimDev {
     double* inst;         // kNFields x K
     double* avg;          // kNFields x K
     double* ushift;       // 3 x K, previous mean velocity (shift of the sums)
+    double* gavg;         // 3 x K, averaged n, T, |u| at the start of the step (plain pipeline, gll_average)
     uint32_t* inj_count;  // K (buffer cells only)
     uint32_t* inj_pidoff; // K
     uint32_t inj_total;

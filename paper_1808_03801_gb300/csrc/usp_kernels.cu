@@ -43,7 +43,9 @@ __global__ void __launch_bounds__(256) k_stream(const SimDev* __restrict__ sims,
             T y = P.y[i];
             T c[3] = {P.c0[i], P.c1[i], P.c2[i]};
             const uint32_t pid = P.pid[i];
+            const T x0 = x, y0 = y;
             bool alive = advect<T>(s, step, pid, x, y, c);
+            if (s.flux_axis) count_flux<T>(s, x0, y0, x, y);
             int cell = s.K;
             if (alive) {
                 cell = cell_index<T>(s, x, y);
@@ -267,6 +269,7 @@ __global__ void __launch_bounds__(256) k_moments(const SimDev* __restrict__ sims
 #pragma unroll
                 for (int m = 0; m < 12; ++m) s.mom[(size_t)(m + 1) * K + cell] = a[m];
                 s.fill[cell] = 0;
+                if (gll_averaged(s)) snap_avg(s, cell);
             }
         }
     }
@@ -315,35 +318,52 @@ __global__ void __launch_bounds__(128) k_params(const SimDev* __restrict__ sims,
                 else {
                     // gradient-length local Knudsen number (Eqs. 17-18): central
                     // differences, one-sided next to a missing or invalid neighbour
-                    double Qc[3] = {L.n, L.T, L.umag};
-                    double g2[3] = {0.0, 0.0, 0.0};
-                    for (int axis = s.dim == 1 ? 1 : 0; axis < 2; ++axis) {
-                        const double h = axis == 0 ? s.dx : s.dy;
-                        int m = neighbor(s, cell, axis, -1), p = neighbor(s, cell, axis, +1);
-                        Local Lm, Lp;
-                        if (m >= 0) {
-                            local_state(s, m, Lm, nullptr, nullptr);
-                            if (!Lm.valid) m = -1;
+                    const bool avg = gll_averaged(s);
+                    GradState G;
+                    if (avg) grad_from_avg(s, cell, G);
+                    else grad_from_local(L, G);
+                    double kn = 0.0;   // no stencil state of its own: no gradient
+                    if (G.valid) {
+                        double Qc[3] = {G.n, G.T, G.umag};
+                        double g2[3] = {0.0, 0.0, 0.0};
+                        for (int axis = s.dim == 1 ? 1 : 0; axis < 2; ++axis) {
+                            const double h = axis == 0 ? s.dx : s.dy;
+                            int m = neighbor(s, cell, axis, -1), p = neighbor(s, cell, axis, +1);
+                            GradState Gm, Gp;
+                            if (m >= 0) {
+                                if (avg) grad_from_avg(s, m, Gm);
+                                else {
+                                    Local Lm;
+                                    local_state(s, m, Lm, nullptr, nullptr);
+                                    grad_from_local(Lm, Gm);
+                                }
+                                if (!Gm.valid) m = -1;
+                            }
+                            if (p >= 0) {
+                                if (avg) grad_from_avg(s, p, Gp);
+                                else {
+                                    Local Lp;
+                                    local_state(s, p, Lp, nullptr, nullptr);
+                                    grad_from_local(Lp, Gp);
+                                }
+                                if (!Gp.valid) p = -1;
+                            }
+                            double Qm[3], Qp[3];
+                            if (m >= 0) { Qm[0] = Gm.n; Qm[1] = Gm.T; Qm[2] = Gm.umag; }
+                            if (p >= 0) { Qp[0] = Gp.n; Qp[1] = Gp.T; Qp[2] = Gp.umag; }
+                            for (int q = 0; q < 3; ++q) {
+                                double d = 0.0;
+                                if (m >= 0 && p >= 0) d = (Qp[q] - Qm[q]) / (2.0 * h);
+                                else if (p >= 0) d = (Qp[q] - Qc[q]) / h;
+                                else if (m >= 0) d = (Qc[q] - Qm[q]) / h;
+                                g2[q] += d * d;
+                            }
                         }
-                        if (p >= 0) {
-                            local_state(s, p, Lp, nullptr, nullptr);
-                            if (!Lp.valid) p = -1;
-                        }
-                        double Qm[3], Qp[3];
-                        if (m >= 0) { Qm[0] = Lm.n; Qm[1] = Lm.T; Qm[2] = Lm.umag; }
-                        if (p >= 0) { Qp[0] = Lp.n; Qp[1] = Lp.T; Qp[2] = Lp.umag; }
-                        for (int q = 0; q < 3; ++q) {
-                            double d = 0.0;
-                            if (m >= 0 && p >= 0) d = (Qp[q] - Qm[q]) / (2.0 * h);
-                            else if (p >= 0) d = (Qp[q] - Qc[q]) / h;
-                            else if (m >= 0) d = (Qc[q] - Qm[q]) / h;
-                            g2[q] += d * d;
-                        }
+                        const double kn_rho = G.lambda * sqrt(g2[0]) / G.n;
+                        const double kn_T = G.lambda * sqrt(g2[1]) / G.T;
+                        const double kn_u = G.lambda * sqrt(g2[2]) / fmax(G.umag, G.a_sound);
+                        kn = fmax(kn_rho, fmax(kn_T, kn_u));                 // Eq. 17
                     }
-                    const double kn_rho = L.lambda * sqrt(g2[0]) / L.n;
-                    const double kn_T = L.lambda * sqrt(g2[1]) / L.T;
-                    const double kn_u = L.lambda * sqrt(g2[2]) / fmax(L.umag, L.a_sound);
-                    const double kn = fmax(kn_rho, fmax(kn_T, kn_u));       // Eq. 17
                     pne = exp(-kn / kKnC);                                   // Eq. 16
                 }
                 const double fs = 1.0 + 0.5 * s.dt * L.nu * pne;            // Eq. 33

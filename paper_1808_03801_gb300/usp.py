@@ -8,6 +8,7 @@ and (optionally) the device allocator.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 
 import numpy as np
@@ -56,7 +57,8 @@ class Params(ctypes.Structure):
                 ("dt_over_tauc", c_double), ("body_accel", c_double * 3), ("ppc_ref", c_int),
                 ("n_avg", c_int), ("mode", c_int), ("fixed_pne", c_double), ("reservoir_cols", c_int),
                 ("precision", c_int), ("pipeline", c_int), ("capacity_factor", c_double),
-                ("slab_count", c_int), ("slab_index", c_int), ("slab_group", c_int)]
+                ("slab_count", c_int), ("slab_index", c_int), ("slab_group", c_int),
+                ("flux_axis", c_int), ("flux_pos", c_double), ("gll_average", c_int)]
 
 
 class Region(ctypes.Structure):
@@ -214,7 +216,9 @@ def make_structs(w: dict, pipeline: str | None = None):
                     (c_double * 3)(*pr["body_accel"]), pr["ppc_ref"], pr["n_avg"], MODE[pr["mode"]],
                     pr["fixed_pne"], pr["reservoir_cols"], PRECISION[pr["precision"]], PIPELINE[pipe],
                     float(pr.get("capacity_factor", 0.0)), int(pr.get("slab_count", 0)),
-                    int(pr.get("slab_index", 0)), int(pr.get("slab_group", 0)))
+                    int(pr.get("slab_index", 0)), int(pr.get("slab_group", 0)),
+                    int(pr.get("flux_axis", 0)), float(pr.get("flux_pos", 0.0)),
+                    int(pr.get("gll_average", 0)))
     return gas, grid, faces, segs, len(w.get("segments", [])), params
 
 
@@ -345,6 +349,28 @@ class Simulation:
         out = np.zeros((self.K, NPRM))
         self._check(lib().usp_get_params(self._h, out.ctypes.data, out.size), "usp_get_params")
         return out
+
+
+def reduced_mass_flow(w: dict, net: int, steps: int, dt: float) -> float:
+    """Reduced mass flow rate W = Mdot / Mdot_fm through the slit (Eq. 41).
+
+    net: particles counted through the plane (counters[7] difference) over
+    `steps` steps of length dt.  Mdot counts both halves of the symmetric
+    slit (the simulated domain is the upper half); each particle stands for
+    n_ref / ppc_ref * dx * dy molecules per unit depth.  Mdot_fm = a p_1 /
+    (sqrt(pi) v_1) is the free-molecular flow of the planar slit of width a,
+    with p_1 and v_1 = sqrt(2 k T_1 / m) of the upstream reservoir (face
+    x-lo)."""
+    kB = 1.380649e-23
+    gr, pr, up = w["grid"], w["params"], w["faces"][0]
+    m = w["gas"]["mass"]
+    dx = (gr["hi"][0] - gr["lo"][0]) / gr["nx"]
+    dy = (gr["hi"][1] - gr["lo"][1]) / gr["ny"]
+    molecules = pr["n_ref"] / pr["ppc_ref"] * dx * dy
+    mdot = 2.0 * m * molecules * net / (steps * dt)
+    p1 = up["n"] * kB * up["T"]
+    v1 = math.sqrt(2.0 * kB * up["T"] / m)
+    return mdot / (w["slit_width"] * p1 / (math.sqrt(math.pi) * v1))
 
 
 def debug_philox(ctr, key):

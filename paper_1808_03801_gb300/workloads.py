@@ -146,11 +146,21 @@ SLIT_CASES = {1: (580, 280, 0.2), 2: (580, 280, 1.0), 3: (580, 280, 2.0), 4: (28
               5: (160, 80, 4.0), 6: (160, 80, 5.0)}
 
 
-def slit_case(case=4, ppc=100, precision="fp32", steps=4000, seed=1):
-    """A slit case of Table 7: delta = 20, vacuum downstream."""
+def slit_case(case=4, ppc=100, precision="fp32", steps=4000, seed=1, buffer_flights=3.0):
+    """A slit case of Table 7: delta = 20, vacuum downstream.
+
+    The reservoir buffer must be deeper than a particle flies in one step, or
+    the particles that would enter from beyond it are missing and the
+    upstream chamber is starved.  With Eq. 36 at the upstream state, Eq. 37
+    and Eq. 40, a most-probable-speed flight is v_1 dt = 0.8 (dt / tau_c,1)
+    a / delta; the buffer is `buffer_flights` such flights deep (at least 2
+    cells)."""
     nx, ny, r = SLIT_CASES[case]
+    delta = 20.0
+    dx_over_a = 20.0 / nx
+    cols = max(2, math.ceil(buffer_flights * 0.8 * r / (delta * dx_over_a)))
     return slit(nx=nx, ny=ny, ppc=ppc, dt_over_tauc=r, pressure_ratio=math.inf, precision=precision,
-                steps=steps, seed=seed, delta=20.0)
+                steps=steps, seed=seed, delta=delta, reservoir_cols=cols)
 
 
 def homogeneous_box(ppc=1000, Kn=0.05, dt_over_tauc=0.5, mode="usp", precision="fp64", Pr=PR_MONO,

@@ -49,8 +49,42 @@ def _create_rc(w, pipeline=None):
     lambda w: w["params"].__setitem__("mode", "bogus") if False else w["params"].__setitem__("n_avg", 0),
     lambda w: w["params"].__setitem__("precision", "fp64") or w["params"].__setitem__("pipeline", "fused"),
     lambda w: w["params"].__setitem__("dt_over_tauc", 0.0),
+    lambda w: w["params"].update(flux_axis=1, flux_pos=0.5),             # no x axis in 1-D
+    lambda w: w["params"].update(flux_axis=2, flux_pos=0.0),             # on a face
+    lambda w: w["params"].update(flux_axis=2, flux_pos=1.0),             # outside the domain
+    lambda w: w["params"].update(flux_axis=3, flux_pos=1e-7),
 ])
 def test_invalid_arguments_rejected_without_gpu(mutate):
     w = W.couette(ny=10, ppc=10)
     mutate(w)
     assert _create_rc(w) == -1
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """The ctypes mirrors of the public structs have the C compiler's sizes
+    and field offsets (include/usp.h compiled as plain C)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"usp_gas": U.Gas, "usp_grid": U.Grid, "usp_bc": U.Bc, "usp_wall_segment": U.WallSegment,
+               "usp_params": U.Params, "usp_region": U.Region, "usp_allocator": U.Allocator,
+               "usp_info": U.Info}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "usp.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f in py._fields_:
+            lines.append(f'printf("{cname} {f[0]} %zu\\n", offsetof({cname}, {f[0]}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run([cc, "-std=c99", "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l}
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f in py._fields_:
+            assert got[(cname, f[0])] == getattr(py, f[0]).offset, (cname, f[0])

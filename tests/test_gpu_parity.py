@@ -99,6 +99,7 @@ def test_fp64_step_parity(usp, name, steps):
         ig = g.info()
         assert ig["n_particles"] == o.n
         assert ig["counters"][2] == o.counters()[2] and ig["counters"][3] == o.counters()[3]
+        assert ig["counters"][7] == o.counters()[4]
 
 
 def test_stagewise_sort_parity(usp):
@@ -222,3 +223,83 @@ def test_reload_reuses_storage(usp, pipeline):
             fresh.step(4)
             assert first.info()["n_particles"] == fresh.info()["n_particles"] == len(P["pid"])
         fresh.close()
+
+
+def test_flux_plane_fp64_parity(usp):
+    """The net count through the slit plane (the flow of Eq. 41) equals the
+    oracle's after every step (paper slit: delta = 20, vacuum downstream)."""
+    w = W.slit(nx=40, ny=20, ppc=30, precision="fp64", pressure_ratio=math.inf, delta=20.0)
+    g, o = _pair(w, usp)
+    for _ in range(25):
+        g.step(1)
+        o.step(1)
+        assert g.info()["counters"][7] == o.counters()[4]
+    assert o.counters()[4] > 0
+    assert_particles_close(g.particles(), o.particles(), VSCALE, _cell_size(w))
+
+
+def test_flux_plane_across_y_fp64_parity(usp):
+    w = W.cavity(n=24, ppc=30, Kn=0.01, precision="fp64")
+    w["params"].update(flux_axis=2, flux_pos=0.37 * w["grid"]["hi"][1])
+    g, o = _pair(w, usp)
+    g.step(12)
+    o.step(12)
+    assert g.info()["counters"][7] == o.counters()[4]
+    assert o.counters()[4] != 0 or o.counters()[2] == 0
+
+
+@pytest.mark.parametrize("pipeline", ["plain", "fused"])
+def test_flux_plane_fp32_counts_change_of_side(usp, pipeline):
+    """FP32 paths (no oracle stream to match): in a closed box each step adds
+    to the count exactly the change in particles at or above the plane."""
+    w = W.cavity(n=32, ppc=40, Kn=0.01, precision="fp32", seed=5)
+    L = w["grid"]["hi"][0]
+    w["segments"] = [{"pos": 0.5 * L, "lo": 0.6 * L, "hi": L, "kind": "diffuse", "T": W.T0,
+                      "u": (0.0, 0.0, 0.0)}]
+    w["params"].update(flux_axis=1, flux_pos=0.5 * L, pipeline=pipeline)
+    p32 = float(np.float32(0.5 * L))
+    g = usp.Simulation(w).init_particles()
+    moved = 0
+    for _ in range(8):
+        before = int((g.particles()["pos"][:, 0] >= p32).sum())
+        c0 = g.info()["counters"][7]
+        g.step(1)
+        d = g.info()["counters"][7] - c0
+        assert d == int((g.particles()["pos"][:, 0] >= p32).sum()) - before
+        moved += abs(d)
+    assert moved > 0
+
+
+@pytest.mark.parametrize("axis,pos", [(1, 2.0), (2, 0.0), (3, 0.5), (2, 0.5)])
+def test_flux_plane_argument_errors(usp, axis, pos):
+    if axis == 2 and pos == 0.5:
+        w = W.homogeneous_box(ppc=10)            # periodic y
+        pos *= w["grid"]["hi"][1]
+    else:
+        w = W.cavity(n=8, ppc=5, precision="fp64")
+        pos *= w["grid"]["hi"][0]
+    w["params"].update(flux_axis=axis, flux_pos=pos)
+    with pytest.raises(usp.UspError) as e:
+        usp.Simulation(w)
+    assert e.value.status == -1
+
+
+@pytest.mark.parametrize("name", ["sod", "slit"])
+def test_fp64_gll_average_parity(usp, name):
+    """Kn_GLL from the Eq. 34 averages (steady-flow option): particles,
+    parameters and fields match the oracle as in the instantaneous reading."""
+    if name == "sod":
+        w = W.sod(ny=200, ppc_left=80, precision="fp64")
+    else:
+        w = W.slit(nx=40, ny=20, ppc=30, precision="fp64", pressure_ratio=math.inf, delta=20.0)
+    w["params"].update(gll_average=1, n_avg=10)
+    g, o = _pair(w, usp)
+    g.step(15)
+    o.step(15)
+    assert_particles_close(g.particles(), o.particles(), VSCALE, _cell_size(w))
+    pg, po = g.params(), o.params()
+    assert np.array_equal(pg[:, 14], po[:, 14])
+    sel = po[:, 14] > 0
+    assert np.allclose(pg[sel, 13], po[sel, 13], rtol=1e-10, atol=1e-13)   # P_ne
+    fa, oa = g.sample(averaged=True), o.fields(averaged=True)
+    assert np.all(np.abs(fa - oa) <= 1e-10 * np.maximum(np.abs(oa), np.abs(oa).max(1, keepdims=True) * 1e-3))

@@ -68,13 +68,14 @@ def _pne_from_fields(F, w, dt):
     n, T = F[0], F[4]
     um = np.sqrt(F[1] ** 2 + F[2] ** 2 + F[3] ** 2)
     valid = (n > 0) & (T > 0)
+    mu_ref = _mu_ref(w)
     out = np.ones(ny)
     for i in range(ny):
         if not valid[i]:
             continue
         rho = n[i] * g["mass"]
         p = rho * R * T[i]
-        mu = _mu_ref(w) * (T[i] / g["T_ref"]) ** g["omega"]
+        mu = mu_ref * (T[i] / g["T_ref"]) ** g["omega"]
         lam = 16.0 / (5.0 * math.sqrt(2.0 * math.pi)) * mu / math.sqrt(rho * p)
         a_s = math.sqrt(5.0 / 3.0 * R * T[i])
         kn = 0.0
