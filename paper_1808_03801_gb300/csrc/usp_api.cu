@@ -151,6 +151,7 @@ static Launch make_launch(usp_handle* h) {
     L.wq = (uint32_t*)(h->d_ntiles + 2);
     L.nsims = 1;
     L.dims = h->host.dim == 1 ? 1 : 2;
+    L.flux = h->host.flux_axis != 0;
     L.grid_p = persistent_grid(h->nptiles, h->grid_per_sm);
     L.grid_c = persistent_grid(h->nctiles, h->grid_per_sm);
     L.stream = h->stream;
@@ -1166,7 +1167,10 @@ static Launch batch_launch(usp_batch* b) {
     L.nsims = (int)b->members.size();
     L.dims = 0;
     for (auto* h : b->members) L.dims |= h->host.dim == 1 ? 1 : 2;
-    for (auto* h : b->members) L.slabs |= h->host.slab_count > 1;
+    for (auto* h : b->members) {
+        L.slabs |= h->host.slab_count > 1;
+        L.flux |= h->host.flux_axis != 0;
+    }
     // fixed persistent grids: the tile counts are read on the device, so the
     // captured graph stays valid while simulations come and go
     int per_sm = 1;

@@ -476,8 +476,10 @@ __device__ __forceinline__ void put_own(const SimDev& s, const Ctx& C, int q, ui
 }
 
 // kFullSlab: kFull for batches holding slabs of a decomposed domain (routes
-// particles that leave the slab; the plain kFull code carries no such check)
-enum { kFull = 0, kRelaxOnly = 1, kFullSlab = 2 };
+// particles that leave the slab; the plain kFull code carries no such check).
+// kFullFlux: kFull for batches where some simulation counts particles
+// through a plane (kFullSlab counts too)
+enum { kFull = 0, kRelaxOnly = 1, kFullSlab = 2, kFullFlux = 3 };
 
 template <int CAP, int DIM, int MODE>
 __device__ void g2_cell(const SimDev* __restrict__ sims, const SimDev& s, int cell, const Hdr& H, int p, uint32_t step,
@@ -708,7 +710,8 @@ __device__ void g2_cell(const SimDev* __restrict__ sims, const SimDev& s, int ce
                         atomicAdd(&s.dyn->counters[kCntRemoved], 1ull);
                     }
                 }
-                if (s.flux_axis) count_flux<float>(s, DIM == 2 ? S.x[j] : 0.0f, S.y[j], x, y);
+                if ((MODE == kFullFlux || MODE == kFullSlab) && s.flux_axis)
+                    count_flux<float>(s, DIM == 2 ? S.x[j] : 0.0f, S.y[j], x, y);
                 if (DIM == 2) S.x[j] = x;
                 S.y[j] = y; S.v0[j] = c[0]; S.v1[j] = c[1]; S.v2[j] = c[2];
                 S.sel[j] = ws;
@@ -1453,6 +1456,7 @@ void launch_fused_relax_stream(const Launch& L, int R, bool flush_only) {
         return;
     }
     if (L.slabs) launch_g2_R<kFullSlab>(L, R);
+    else if (L.flux) launch_g2_R<kFullFlux>(L, R);
     else launch_g2_R<kFull>(L, R);
 }
 
@@ -1478,6 +1482,9 @@ void fused_prepare_attributes() {
     set_g2_smem<128, kFullSlab>();
     set_g2_smem<256, kFullSlab>();
     set_g2_smem<kCapMax, kFullSlab>();
+    set_g2_smem<128, kFullFlux>();
+    set_g2_smem<256, kFullFlux>();
+    set_g2_smem<kCapMax, kFullFlux>();
     cudaGetLastError();
 }
 

@@ -196,6 +196,7 @@ struct Launch {
     int nsims;
     int dims;             // bit 0: some simulation is 1-D, bit 1: some is 2-D
     int slabs = 0;        // some simulation is a slab of a decomposed domain
+    int flux = 0;         // some simulation counts particles through a plane
     int grid_p, grid_c;   // persistent grid sizes
     cudaStream_t stream;
 };
