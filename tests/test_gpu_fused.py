@@ -418,3 +418,24 @@ def test_slit_reduced_mass_flow_case4(usp):
     assert r["lost"] == 0
     assert 1.40 < r["W"] < 1.50, r
     assert r["se"] < 0.01
+
+
+def test_poiseuille_large_dt_viscosity(usp):
+    """Table 3 case 4 (Kn = 0.001, dt = 5 tau_c, 100 cells of 10 lambda) from
+    rest to steady state.  The profile is the parabola of Eq. 38 scaled by
+    mu / mu_eff.  Without the weighted added particles of Table 2 steps 2, 4
+    and 7 the scheme splits streaming and relaxation to first order, so with
+    x = nu dt = 4 and R the stress left by one relaxation,
+        mu_eff / mu = (x / 2)(1 + R) / (1 - R) + rho (1 - e^-a) dy^2 / (12 dt mu),
+    the second term (3.1) because a relaxed particle takes its cell's mean
+    velocity.  USP: R = e^-a - (1 - e^-a) / 6 (a = nu_ES dt), 1.68 + 3.1;
+    P_ne = 0: R = e^-a - (1 - e^-a) 0.11 / 2, 2.07 + 3.1 -- velocity scales of
+    0.21 and 0.19 (measured 0.210 and 0.186).  The Eq. 33 correction must keep
+    USP above the P_ne = 0 scheme."""
+    from paper_1808_03801_gb300 import poiseuille
+    r = {m: poiseuille.run_case(4, m, ppc=200, steps=100000, sample_every=100) for m in ("usp", "sp")}
+    for m in r:
+        assert r[m]["lost"] == 0
+        assert r[m]["u_shape_l2"] < 0.05, r[m]        # a parabola
+    assert 0.18 < r["usp"]["u_scale"] < 0.245, r["usp"]
+    assert 0.16 < r["sp"]["u_scale"] < r["usp"]["u_scale"] - 0.01, r
