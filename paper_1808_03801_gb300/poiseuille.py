@@ -40,6 +40,14 @@ def navier_stokes(w: dict, mu: float, y: np.ndarray):
     return u, T
 
 
+def _slip_fit(u, u_ns):
+    """Relative L2 residual of u against a * u_ns + b (a parabola with slip)."""
+    A = np.stack([u_ns, np.ones_like(u_ns)], axis=1)
+    coef, *_ = np.linalg.lstsq(A, u, rcond=None)
+    fit = A @ coef
+    return float(np.linalg.norm(u - fit) / np.linalg.norm(fit))
+
+
 def run_case(case: int = 4, mode: str = "usp", ppc: int = 200, steps: int = 200000, sample_every: int = 100,
              avg_frac: float = 0.5, pipeline: str = "fused", seed: int = 1, cells: int | None = None) -> dict:
     w = W.poiseuille_case(case, ppc=ppc, mode=mode, seed=seed, cells=cells)
@@ -76,6 +84,7 @@ def run_case(case: int = 4, mode: str = "usp", ppc: int = 200, steps: int = 2000
             "ppc": ppc, "steps": steps, "samples": nsamp,
             "u_scale": u_scale, "u_rel_l2": float(np.linalg.norm(u - u_ns) / np.linalg.norm(u_ns)),
             "u_shape_l2": float(np.linalg.norm(u - u_scale * u_ns) / np.linalg.norm(u_scale * u_ns)),
+            "u_slip_fit_l2": _slip_fit(u, u_ns),
             "u_max": float(u.max()), "u_max_ns": float(u_ns.max()),
             "T_scale": T_scale, "dT_max": float(T.max() - Tw), "dT_max_ns": float(T_ns.max() - Tw),
             "n_particles": int(inf["n_particles"]), "lost": int(inf["counters"][5]),
