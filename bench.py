@@ -28,7 +28,7 @@ sys.path.insert(0, ROOT)
 METRIC = "particle-updates/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM = 6800.0
-KG2_DRAM_BYTES_PER_PARTICLE = 39.16   # profiles/k_g2_k_g1_sod_batch32_fused.md
+KG2_DRAM_BYTES_PER_PARTICLE = 39.22   # profiles/k_g2_k_g1_sod_batch32_fused.md
 
 
 def parse():
