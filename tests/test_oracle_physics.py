@@ -138,3 +138,62 @@ def test_couette_steady_shear_uniform_and_antisymmetric():
     assert avg < 0
     assert abs(slope * ny) < 0.1 * abs(avg)
     assert np.all(np.abs(pxy - avg) < 4 * se[8] + 0.02 * abs(avg))
+
+
+def _couette_sampled_stress_ratio(mode, fixed_pne=0.0, r=5.0, ny=50, ppc=300, relax_steps=1500, blocks=10,
+                                  block_steps=250, u_wall=100.0):
+    """Steady Couette (plates at -/+ u_wall, Kn = 0.01): mean and standard
+    error over time blocks of -p_xy / (mu du/dy) in the central 60 % of the
+    gap, and x = nu dt at the bulk state."""
+    w = W.couette(ny=ny, ppc=ppc, Kn=0.01, u_wall=u_wall, dt_over_tauc=r, omega=0.81, seed=7)
+    w["params"]["mode"] = mode
+    w["params"]["fixed_pne"] = fixed_pne
+    o = oracle.OracleSim(w).init_particles()
+    o.step(relax_steps)
+    H = w["grid"]["hi"][1]
+    y = (np.arange(ny) + 0.5) * H / ny
+    c = slice(int(0.2 * ny), int(0.8 * ny))
+    ratios, xs = [], []
+    for _ in range(blocks):
+        acc = np.zeros((16, ny))
+        nu = 0.0
+        for _ in range(block_steps):
+            o.step(1)
+            acc += o.fields()
+            nu += o.params()[c, 11].mean()
+        F = acc / block_steps
+        T = F[4][c].mean()
+        mu = o.mu_ref * (T / W.T0) ** 0.81
+        slope = np.polyfit(y[c], F[1][c], 1)[0]
+        ratios.append(-F[8][c].mean() / (mu * slope))
+        xs.append(nu / block_steps * o.dt)
+    ratios = np.array(ratios)
+    return ratios.mean(), ratios.std(ddof=1) / math.sqrt(blocks), float(np.mean(xs))
+
+
+def test_couette_sampled_stress_matches_splitting_closed_form():
+    """Streaming and relaxation alternate, so in steady shear the stress
+    sampled after a flight, sigma', obeys sigma'(1 - R) = -p gamma dt, with R
+    the fraction of stress one relaxation leaves (selection probability
+    1 - e^-a, a = nu_ES dt, Eq. 9; target stress (1 - 1/Pr) times sigma(t) of
+    Eq. 32).  P_ne = 0: sigma(t) = e^{-nu t} sigma' with t drawn from g_time
+    (Eqs. 29-30), so R = e^-a + (1 - e^-a)(1 - 1/Pr) E[e^{-nu t}] and the
+    sampled ratio is x / (1 - R), x = nu dt.  P_ne = 1: sigma(t) = sigma* =
+    sigma' / (1 + x/2) (Eq. 33), R = e^-a + (1 - e^-a)(1 - 1/Pr) / (1 + x/2),
+    and the sampled sigma* gives x / ((1 - R)(1 + x/2)).  A wrong factor in
+    Eq. 33 (e.g. Pr on the stress), the selection rate or the sampling point
+    moves these by more than the tolerance."""
+    Pr = 2.0 / 3.0
+    m_sp, se_sp, x = _couette_sampled_stress_ratio("sp")
+    a = Pr * x
+    nes = Pr
+    k_sp = nes / (nes - 1.0) * (math.exp((nes - 1.0) * x) - 1.0) / (math.exp(a) - 1.0)   # E[e^{-nu t}]
+    R_sp = math.exp(-a) + (1 - math.exp(-a)) * (1 - 1 / Pr) * k_sp
+    want_sp = x / (1 - R_sp)
+    assert abs(m_sp - want_sp) < 4 * se_sp + 0.01 * want_sp, (m_sp, se_sp, want_sp)
+    m_u, se_u, x = _couette_sampled_stress_ratio("fixed", fixed_pne=1.0)
+    a = Pr * x
+    R_u = math.exp(-a) + (1 - math.exp(-a)) * (1 - 1 / Pr) / (1 + x / 2)
+    want_u = x / ((1 - R_u) * (1 + x / 2))
+    assert abs(m_u - want_u) < 4 * se_u + 0.01 * want_u, (m_u, se_u, want_u)
+    assert want_sp / want_u > 3.0   # the Eq. 33 correction is what separates them
