@@ -441,3 +441,18 @@ def test_poiseuille_large_dt_viscosity(usp):
         assert r[m]["u_shape_l2"] < 0.2, r[m]
     assert 0.18 < r["usp"]["u_scale"] < 0.245, r["usp"]
     assert 0.16 < r["sp"]["u_scale"] < r["usp"]["u_scale"] - 0.01, r
+
+
+def test_couette_transport_follows_splitting_closed_form(usp):
+    """Couette shear at dt = 5 tau_c (Kn = 0.01, 1000 ppc): the sampled Eq. 33
+    stress over mu du/dy equals the closed form of alternating flight and
+    relaxation -- x / (1 - R) = 4.07 with P_ne = 0, x / ((1 - R)(1 + x/2)) =
+    1.23 for USP with Kn_GLL averaged (P_ne ~ 1) -- and USP stays within a
+    third of the P_ne = 0 error."""
+    from paper_1808_03801_gb300 import couette
+    sp = couette.run("shear", 5.0, "sp", ppc=1000, min_samples=5000)
+    us = couette.run("shear", 5.0, "usp", ppc=1000, min_samples=5000, gll_average=1)
+    assert sp["lost"] == 0 and us["lost"] == 0
+    assert abs(sp["ratio"] - 4.07) < 0.15, sp
+    assert abs(us["ratio"] - 1.23) < 0.06, us
+    assert us["ratio"] - 1.0 < (sp["ratio"] - 1.0) / 3.0
