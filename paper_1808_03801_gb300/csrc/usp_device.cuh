@@ -330,7 +330,10 @@ struct GradState {
     double n, T, umag, a_sound, lambda;
 };
 
-__device__ __forceinline__ bool gll_averaged(const SimDev& s) { return s.gll_average && s.dyn->nsamples > 0; }
+// plain pipeline only: the snapshot exists for handles created with gll_average
+__device__ __forceinline__ bool gll_averaged(const SimDev& s) {
+    return s.gll_average && s.gavg != nullptr && s.dyn->nsamples > 0;
+}
 
 // plain pipeline: k_moments copies the averaged n, T, |u| of its cell into
 // gavg ([3][K]) before k_params updates the averages, so that the stencil
