@@ -24,7 +24,7 @@ FIELD_NAMES = ["n", "u0", "u1", "u2", "T", "pxx", "pyy", "pzz", "pxy", "pxz", "p
                "q0", "q1", "q2", "Pne", "Nc"]
 PH_STREAM, PH_RESERVOIR, PH_SORT, PH_MOMENTS, PH_PARAMS, PH_RELAX, PH_SAMPLE = range(7)
 _BC = {"diffuse": 0, "specular": 1, "periodic": 2, "reservoir": 3}
-_MODE = {"usp": 0, "sp": 1, "fixed": 2}
+_MODE = {"usp": 0, "sp": 1, "fixed": 2, "spesbgk": 3}
 MAXSEG = 4
 
 
@@ -46,6 +46,7 @@ class _Config(ctypes.Structure):
         ("ppc_ref", ctypes.c_int), ("n_avg", ctypes.c_int), ("mode", ctypes.c_int),
         ("fixed_pne", ctypes.c_double), ("reservoir_cols", ctypes.c_int),
         ("flux_axis", ctypes.c_int), ("flux_pos", ctypes.c_double), ("gll_average", ctypes.c_int),
+        ("selection", ctypes.c_int), ("es_sampler", ctypes.c_int),
     ]
 
 
@@ -145,6 +146,8 @@ def make_config(w: dict) -> _Config:
     c.fixed_pne, c.reservoir_cols = pr["fixed_pne"], pr["reservoir_cols"]
     c.flux_axis, c.flux_pos = int(pr.get("flux_axis", 0)), float(pr.get("flux_pos", 0.0))
     c.gll_average = int(pr.get("gll_average", 0))
+    c.selection = {"bernoulli": 0, "fixed_count": 1}[pr.get("selection", "bernoulli")]
+    c.es_sampler = {"cholesky": 0, "gallis_torczynski": 1}[pr.get("es_sampler", "cholesky")]
     return c
 
 

@@ -145,6 +145,8 @@ orc_sim* orc_create(const orc_config* cfg) {
     if (cfg->body_accel[1] != 0 || (cfg->dim == 2 && cfg->body_accel[0] != 0)) return NULL;
     /* the counting plane lies strictly inside the domain, across an axis
      * whose faces are not periodic */
+    if (cfg->mode < ORC_MODE_USP || cfg->mode > ORC_MODE_SPESBGK) return NULL;
+    if (cfg->selection < 0 || cfg->selection > 1 || cfg->es_sampler < 0 || cfg->es_sampler > 1) return NULL;
     if (cfg->flux_axis < 0 || cfg->flux_axis > 2) return NULL;
     if (cfg->flux_axis) {
         int a = cfg->flux_axis - 1;
@@ -627,7 +629,7 @@ static void params_phase(orc_sim* s) {
         cell_params* P = &s->par[cell];
         if (!P->valid) continue;
         double pne;
-        if (c->mode == ORC_MODE_SP) pne = 0.0;
+        if (c->mode == ORC_MODE_SP || c->mode == ORC_MODE_SPESBGK) pne = 0.0;
         else if (c->mode == ORC_MODE_FIXED_PNE) pne = c->fixed_pne;
         else {
             /* a cell whose own stencil state is missing (never sampled as
@@ -701,9 +703,23 @@ static double sample_time(double U, double nu_es, double dt) {
     return dt + log(U + (1.0 - U) * exp(-a)) / nu_es;
 }
 
+typedef struct {
+    double key;
+    int64_t pos;
+} key_pos;
+
+static int cmp_key_pos(const void* a, const void* b) {
+    const key_pos* x = (const key_pos*)a;
+    const key_pos* y = (const key_pos*)b;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    return x->pos < y->pos ? -1 : (x->pos > y->pos);
+}
+
 static void relax_phase(orc_sim* s) {
     int64_t i = 0;
     double* cold = NULL;
+    double* ukey = NULL;
+    key_pos* order = NULL;
     int* sel = NULL;
     int64_t cap = 0;
     while (i < s->np) {
@@ -717,33 +733,68 @@ static void relax_phase(orc_sim* s) {
             cap = n;
             cold = (double*)realloc(cold, (size_t)cap * 3 * sizeof(double));
             sel = (int*)realloc(sel, (size_t)cap * sizeof(int));
+            ukey = (double*)realloc(ukey, (size_t)cap * sizeof(double));
+            order = (key_pos*)realloc(order, (size_t)cap * sizeof(key_pos));
         }
         P->n_relaxed = 0;
         if (!P->valid) { i = j; continue; }
+        const orc_config* c = &s->cfg;
+        /* selection: Bernoulli per particle, or the fixed count of Eq. 9 */
+        for (int64_t k = i; k < j; ++k) {
+            uint32_t w[4];
+            draw(s, s->p[k].pid, s->step, P_RELAX, 0, w);
+            ukey[k - i] = orc_u01(w[0]);
+            sel[k - i] = ukey[k - i] < P->p_relax;
+        }
+        if (c->selection == ORC_SELECT_FIXED_COUNT) {
+            /* Eq. 9: the ns particles with the smallest keys (ties: lower
+             * position first), ns the nearest integer to N_c (1 - e^-a) */
+            int64_t ns = (int64_t)floor((double)n * P->p_relax + 0.5);
+            for (int64_t r = 0; r < n; ++r) { order[r].key = ukey[r]; order[r].pos = r; sel[r] = 0; }
+            qsort(order, (size_t)n, sizeof(key_pos), cmp_key_pos);
+            for (int64_t r = 0; r < ns; ++r) sel[order[r].pos] = 1;
+        }
         int nr = 0;
         for (int64_t k = i; k < j; ++k) {
             particle* q = &s->p[k];
             int64_t r = k - i;
-            uint32_t w[4];
-            draw(s, q->pid, s->step, P_RELAX, 0, w);
-            sel[r] = orc_u01(w[0]) < P->p_relax;
             if (!sel[r]) continue;
             ++nr;
+            uint32_t w[4];
+            draw(s, q->pid, s->step, P_RELAX, 0, w);
             for (int d = 0; d < 3; ++d) cold[3 * r + d] = q->c[d];
             double t = sample_time(orc_u01(w[1]), P->nu_es, s->dt);
-            double sfac = P->pne + (1.0 - P->pne) * exp(-P->nu * t);   /* Eq. 32 */
+            /* Eq. 32; SP-ESBGK holds the target for the whole step (Eq. 8b) */
+            double sfac = c->mode == ORC_MODE_SPESBGK ? 1.0 : P->pne + (1.0 - P->pne) * exp(-P->nu * t);
             uint32_t v[4];
             draw(s, q->pid, s->step, P_RELAX, 1, v);
             double z[6];
             box_muller(w[2], w[3], &z[0], &z[1]);
             box_muller(v[0], v[1], &z[2], &z[3]);
             box_muller(v[2], v[3], &z[4], &z[5]);
-            /* covariance theta I + s (1 - 1/Pr) sigma* / rho = s L L^T + (1 - s) theta I */
-            const double* L = P->L;
-            double a = sqrt(sfac), bb = sqrt((1.0 - sfac) * M->theta);
-            double C0 = a * (L[0] * z[0]) + bb * z[3];
-            double C1 = a * (L[1] * z[0] + L[2] * z[1]) + bb * z[4];
-            double C2 = a * (L[3] * z[0] + L[4] * z[1] + L[5] * z[2]) + bb * z[5];
+            double C0, C1, C2;
+            if (c->es_sampler == ORC_SAMPLER_GALLIS_TORCZYNSKI) {
+                /* Eq. 10: one thermal component per (cosine) Box-Muller pair;
+                 * Eq. 11: C = S C*, S = I - (1 - Pr)/(2 Pr) (P/theta - I), with
+                 * P/theta - I = s sigma* / (rho theta) at the time instant */
+                double st = sqrt(M->theta);
+                double cs[3] = {st * z[0], st * z[2], st * z[4]};
+                double beta = (1.0 - c->Pr) / (2.0 * c->Pr) * sfac / M->theta;
+                const double* g = P->sig_star;   /* xx, yy, zz, xy, xz, yz (per unit density) */
+                double S[3][3] = {{1.0 - beta * g[0], -beta * g[3], -beta * g[4]},
+                                  {-beta * g[3], 1.0 - beta * g[1], -beta * g[5]},
+                                  {-beta * g[4], -beta * g[5], 1.0 - beta * g[2]}};
+                C0 = S[0][0] * cs[0] + S[0][1] * cs[1] + S[0][2] * cs[2];
+                C1 = S[1][0] * cs[0] + S[1][1] * cs[1] + S[1][2] * cs[2];
+                C2 = S[2][0] * cs[0] + S[2][1] * cs[1] + S[2][2] * cs[2];
+            } else {
+                /* covariance theta I + s (1 - 1/Pr) sigma* / rho = s L L^T + (1 - s) theta I */
+                const double* L = P->L;
+                double a = sqrt(sfac), bb = sqrt((1.0 - sfac) * M->theta);
+                C0 = a * (L[0] * z[0]) + bb * z[3];
+                C1 = a * (L[1] * z[0] + L[2] * z[1]) + bb * z[4];
+                C2 = a * (L[3] * z[0] + L[4] * z[1] + L[5] * z[2]) + bb * z[5];
+            }
             q->c[0] = M->u[0] + C0;
             q->c[1] = M->u[1] + C1;
             q->c[2] = M->u[2] + C2;
@@ -787,6 +838,8 @@ static void relax_phase(orc_sim* s) {
     }
     free(cold);
     free(sel);
+    free(ukey);
+    free(order);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -28,7 +28,12 @@ extern "C" {
 #endif
 
 enum { ORC_BC_DIFFUSE = 0, ORC_BC_SPECULAR = 1, ORC_BC_PERIODIC = 2, ORC_BC_RESERVOIR = 3 };
-enum { ORC_MODE_USP = 0, ORC_MODE_SP = 1, ORC_MODE_FIXED_PNE = 2 };
+/* ORC_MODE_SPESBGK: the SP-ESBGK step of Sec. 2 (Eq. 8b, Table 1): the
+ * Gaussian target is held at the post-convection state for the whole step
+ * (no time instant, no Eq. 33 division) */
+enum { ORC_MODE_USP = 0, ORC_MODE_SP = 1, ORC_MODE_FIXED_PNE = 2, ORC_MODE_SPESBGK = 3 };
+enum { ORC_SELECT_BERNOULLI = 0, ORC_SELECT_FIXED_COUNT = 1 };
+enum { ORC_SAMPLER_CHOLESKY = 0, ORC_SAMPLER_GALLIS_TORCZYNSKI = 1 };
 enum { ORC_NFIELDS = 16 };
 #define ORC_MAXSEG 4
 
@@ -68,6 +73,13 @@ typedef struct {
      * averaging that Sec. 3 applies to steady flows to cut statistical
      * noise; 0: from the instantaneous moments */
     int gll_average;
+    /* selection: ORC_SELECT_BERNOULLI (each particle relaxes with 1 - e^-a)
+     * or ORC_SELECT_FIXED_COUNT (Eq. 9: the N_s = nearest-int(N_c (1 - e^-a))
+     * particles of the cell with the smallest selection uniforms);
+     * es_sampler: ORC_SAMPLER_CHOLESKY (Gaussian through the Cholesky factor)
+     * or ORC_SAMPLER_GALLIS_TORCZYNSKI (thermal velocities of Eq. 10
+     * transformed by S of Eq. 11) */
+    int selection, es_sampler;
 } orc_config;
 
 typedef struct {

@@ -211,6 +211,10 @@ def make_structs(w: dict, pipeline: str | None = None):
     segs = (WallSegment * MAXSEG)()
     for i, s in enumerate(w.get("segments", [])):
         segs[i] = WallSegment(s["pos"], s["lo"], s["hi"], BC[s["kind"]], s["T"], (c_double * 3)(*s["u"]))
+    if pr.get("selection", "bernoulli") != "bernoulli" or pr.get("es_sampler", "cholesky") != "cholesky":
+        raise ValueError("fixed-count selection (Eq. 9) and the Gallis-Torczynski sampler (Eq. 11) exist in "
+                         "the oracle only; the CUDA library relaxes with the Bernoulli draw and the Cholesky "
+                         "Gaussian")
     pipe = pipeline or pr.get("pipeline", "plain")
     params = Params(pr["Kn"], pr["L_ref"], pr["n_ref"], pr["dt"], pr["dt_over_tauc"],
                     (c_double * 3)(*pr["body_accel"]), pr["ppc_ref"], pr["n_avg"], MODE[pr["mode"]],

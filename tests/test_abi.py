@@ -88,3 +88,14 @@ def test_struct_layouts_match_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for f in py._fields_:
             assert got[(cname, f[0])] == getattr(py, f[0]).offset, (cname, f[0])
+
+
+@pytest.mark.parametrize("key,value", [("selection", "fixed_count"), ("es_sampler", "gallis_torczynski"),
+                                       ("mode", "spesbgk")])
+def test_oracle_only_ablations_fail_loudly(key, value):
+    """The SP-ESBGK ablations exist in the oracle only: the binding refuses
+    them instead of running something else."""
+    w = W.couette(ny=10, ppc=10)
+    w["params"][key] = value
+    with pytest.raises((ValueError, KeyError)):
+        _create_rc(w)
