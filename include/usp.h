@@ -56,6 +56,15 @@ extern "C" {
 #define USP_MODE_USP 0       /* P_ne from the gradient-length local Knudsen number, Eq. 16 */
 #define USP_MODE_SP 1        /* P_ne = 0: the SP-ESBGK scheme (Appendix B limit) */
 #define USP_MODE_FIXED_PNE 2 /* P_ne = params.fixed_pne everywhere */
+#define USP_MODE_SPESBGK 3   /* the SP-ESBGK step of Sec. 2 (Eq. 8b): the Gaussian target held at the
+                                post-convection state (no time instant, no Eq. 33 division); plain pipeline */
+
+/* relaxation selection and sampler (the SP-ESBGK ablations of Sec. 2; plain pipeline only) */
+#define USP_SELECT_BERNOULLI 0        /* each particle relaxes with probability 1 - exp(-nu_ES dt) */
+#define USP_SELECT_FIXED_COUNT 1      /* Eq. 9: the nearest integer to N_c (1 - exp(-nu_ES dt)) particles
+                                         of the cell with the smallest selection words */
+#define USP_SAMPLER_CHOLESKY 0        /* ES Gaussian through the Cholesky factor of its covariance */
+#define USP_SAMPLER_GALLIS_TORCZYNSKI 1 /* Eq. 10 thermal velocities transformed by S of Eq. 11 */
 
 /* particle storage precision */
 #define USP_FP64 0       /* positions and velocities stored and streamed in FP64 */
@@ -157,7 +166,14 @@ typedef struct {
  *                  exists -- the time averaging the paper applies to steady
  *                  flows to cut statistical noise; a cell whose averaged
  *                  state is empty has Kn_GLL = 0.  0 (default): from the
- *                  instantaneous moments of the step. */
+ *                  instantaneous moments of the step.
+ *   selection, es_sampler: USP_SELECT_* and USP_SAMPLER_* (0, 0 = the
+ *                  defaults); the others, and USP_MODE_SPESBGK, need the
+ *                  plain pipeline (INVALID_ARG otherwise).  With the
+ *                  Gallis-Torczynski sampler, usp_get_params slots 4-9 hold
+ *                  B = ((1 - Pr)/(2 Pr)) sigma* / (rho theta) (xx, yy, zz, xy,
+ *                  xz, yz; S = I - s B at the time instant of Eq. 32)
+ *                  instead of the Cholesky factor. */
 typedef struct {
     double Kn, L_ref, n_ref;
     double dt, dt_over_tauc;
@@ -172,6 +188,7 @@ typedef struct {
     int flux_axis;
     double flux_pos;
     int gll_average;
+    int selection, es_sampler;
 } usp_params;
 
 /* A box of initial gas at number density n, temperature T, velocity u. */

@@ -226,7 +226,11 @@ extern "C" int usp_create(const usp_gas* gas, const usp_grid* grid, const usp_bc
     if (!(prm->n_ref > 0) || prm->ppc_ref < 1 || prm->n_avg < 1) return USP_ERR_INVALID_ARG;
     if (gas->mu_ref == 0 && !(prm->Kn > 0 && prm->L_ref > 0)) return USP_ERR_INVALID_ARG;
     if (!(prm->dt > 0) && !(prm->dt_over_tauc > 0)) return USP_ERR_INVALID_ARG;
-    if (prm->mode < 0 || prm->mode > 2) return USP_ERR_INVALID_ARG;
+    if (prm->mode < 0 || prm->mode > 3) return USP_ERR_INVALID_ARG;
+    if (prm->selection < 0 || prm->selection > 1 || prm->es_sampler < 0 || prm->es_sampler > 1)
+        return USP_ERR_INVALID_ARG;
+    if ((prm->mode == USP_MODE_SPESBGK || prm->selection || prm->es_sampler) && prm->pipeline != USP_PIPE_PLAIN)
+        return USP_ERR_INVALID_ARG;
     if (prm->precision != USP_FP64 && prm->precision != USP_FP32_MIXED) return USP_ERR_INVALID_ARG;
     if (prm->pipeline != USP_PIPE_PLAIN && prm->pipeline != USP_PIPE_FUSED) return USP_ERR_INVALID_ARG;
     if (prm->pipeline == USP_PIPE_FUSED && prm->precision != USP_FP32_MIXED) return USP_ERR_INVALID_ARG;
@@ -326,6 +330,8 @@ extern "C" int usp_create(const usp_gas* gas, const usp_grid* grid, const usp_bc
     s.flux_pos = prm->flux_pos;
     s.f_flux_pos = (float)prm->flux_pos;
     s.gll_average = prm->gll_average != 0;
+    s.selection = prm->selection;
+    s.es_sampler = prm->es_sampler;
     for (int d = 0; d < 3; ++d) s.body[d] = prm->body_accel[d];
     for (int f = 0; f < 4; ++f) {
         s.face[f].kind = faces[f].kind;

@@ -408,12 +408,26 @@ template <class T>
 __device__ __forceinline__ void es_draw(const SimDev& s, const CellRelax& R, uint32_t pid, uint32_t step,
                                         const uint4& w, T* C) {
     const T t = sample_time<T>(u01<T>(w.y), (T)R.nu_es, (T)s.dt);
-    const T sf = (T)R.pne + (T)(1.0 - R.pne) * exp(-(T)R.nu * t);
+    // Eq. 32; the SP-ESBGK step holds the target for the whole step (Eq. 8b)
+    const T sf = s.mode == kModeSPESBGK ? (T)1 : (T)R.pne + (T)(1.0 - R.pne) * exp(-(T)R.nu * t);
     const uint4 v = draw(s, pid, step, kRelax, 1);
     T z[6];
     box_muller<T>(w.z, w.w, z[0], z[1]);
     box_muller<T>(v.x, v.y, z[2], z[3]);
     box_muller<T>(v.z, v.w, z[4], z[5]);
+    if (s.es_sampler) {
+        // Eq. 10: one thermal component per (cosine) Box-Muller pair; Eq. 11:
+        // C = S C*, S = I - s B, B = ((1 - Pr)/(2 Pr)) sigma*/(rho theta) in
+        // the L slots (xx, yy, zz, xy, xz, yz)
+        const T st = dev_sqrt<T>((T)R.theta);
+        const T c0 = st * z[0], c1 = st * z[2], c2 = st * z[4];
+        const T b00 = sf * (T)R.L[0], b11 = sf * (T)R.L[1], b22 = sf * (T)R.L[2];
+        const T b01 = sf * (T)R.L[3], b02 = sf * (T)R.L[4], b12 = sf * (T)R.L[5];
+        C[0] = ((T)1 - b00) * c0 - b01 * c1 - b02 * c2;
+        C[1] = -b01 * c0 + ((T)1 - b11) * c1 - b12 * c2;
+        C[2] = -b02 * c0 - b12 * c1 + ((T)1 - b22) * c2;
+        return;
+    }
     const T a = dev_sqrt<T>(sf), b = dev_sqrt<T>(((T)1 - sf) * (T)R.theta);
     C[0] = a * ((T)R.L[0] * z[0]) + b * z[3];
     C[1] = a * ((T)R.L[1] * z[0] + (T)R.L[2] * z[1]) + b * z[4];

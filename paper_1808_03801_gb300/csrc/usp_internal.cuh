@@ -19,7 +19,7 @@ constexpr double kGammaMono = 5.0 / 3.0;
 // Philox purposes (third counter word); the first two words are (pid, step).
 enum : uint32_t { kInit = 0, kRelax = 1, kWall = 2, kInject = 3 };
 enum { kBcDiffuse = 0, kBcSpecular = 1, kBcPeriodic = 2, kBcReservoir = 3 };
-enum { kModeUSP = 0, kModeSP = 1, kModeFixed = 2 };
+enum { kModeUSP = 0, kModeSP = 1, kModeFixed = 2, kModeSPESBGK = 3 };
 
 // counters (u64, device)
 enum { kCntChol = 0, kCntClamp = 1, kCntRemoved = 2, kCntInjected = 3, kCntRelaxed = 4, kCntOverflow = 5,
@@ -80,6 +80,8 @@ struct alignas(16) SimDev {
     int flux_axis;
     double flux_pos;
     int gll_average;      // Kn_GLL from the Eq. 34 averages once a sample exists
+    int selection;        // 1: fixed count of Eq. 9 (plain pipeline)
+    int es_sampler;       // 1: Gallis-Torczynski, Eqs. 10-11 (plain pipeline)
     double body[3];
     uint32_t key0, key1;
     int64_t cap;

@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(128) k_params(const SimDev* __restrict__ sims,
             pr[3] = L.theta;
             if (L.valid) {
                 double pne;
-                if (s.mode == kModeSP) pne = 0.0;
+                if (s.mode == kModeSP || s.mode == kModeSPESBGK) pne = 0.0;
                 else if (s.mode == kModeFixed) pne = s.fixed_pne;
                 else {
                     // gradient-length local Knudsen number (Eqs. 17-18): central
@@ -396,6 +396,11 @@ __global__ void __launch_bounds__(128) k_params(const SimDev* __restrict__ sims,
                     atomicAdd(&s.dyn->counters[kCntChol], 1ull);
                 }
                 pr[4] = l00; pr[5] = l10; pr[6] = l11; pr[7] = l20; pr[8] = l21; pr[9] = l22;
+                if (s.es_sampler) {
+                    // Eq. 11: B = ((1 - Pr)/(2 Pr)) sigma*/(rho theta); S = I - s B
+                    const double beta = (1.0 - s.Pr) / (2.0 * s.Pr) / L.theta;
+                    for (int k = 0; k < 6; ++k) pr[4 + k] = beta * sig[k];
+                }
                 pr[10] = -expm1(-s.Pr * L.nu * s.dt);                       // Eqs. 8b, 9
                 pr[11] = L.nu;
                 pr[12] = s.Pr * L.nu;
@@ -427,6 +432,22 @@ __global__ void __launch_bounds__(128) k_params(const SimDev* __restrict__ sims,
 // ---------------------------------------------------------------------------
 // K7: relaxation of each cell with conservation of momentum and energy
 // ---------------------------------------------------------------------------
+// is the particle at slot i of the cell [b, e) relaxed?  Bernoulli: its
+// selection word against the probability; fixed count (Eq. 9): its rank
+// among the cell's selection words below ns
+template <class T>
+__device__ __forceinline__ bool selected(const SimDev& s, const PView<T>& B, uint32_t b, uint32_t e, uint32_t i,
+                                         uint32_t wx, T pth, uint32_t ns, uint32_t step) {
+    if (!s.selection) return u01<T>(wx) < pth;
+    if (ns == 0) return false;
+    uint32_t rank = 0;
+    for (uint32_t j = b; j < e && rank < ns; ++j) {
+        const uint32_t xj = draw(s, B.pid[j], step, kRelax, 0).x;
+        rank += (xj < wx || (xj == wx && j < i)) ? 1u : 0u;
+    }
+    return rank < ns;
+}
+
 template <class T>
 __global__ void __launch_bounds__(256) k_relax(const SimDev* __restrict__ sims, const int2* __restrict__ tiles,
                                                const int* __restrict__ ntiles) {
@@ -463,10 +484,13 @@ __global__ void __launch_bounds__(256) k_relax(const SimDev* __restrict__ sims, 
             const T pth = (T)R.p_relax;
             // pass 1: sums over the relaxed subset (velocities relative to the cell mean)
             double nr = 0, so[3] = {0, 0, 0}, eo = 0, sn[3] = {0, 0, 0}, en = 0;
+            // Eq. 9 fixed count: the ns particles with the smallest selection
+            // words (ties: lower position first)
+            const uint32_t ns = s.selection ? (uint32_t)floor((double)(e - b) * R.p_relax + 0.5) : 0u;
             for (uint32_t i = b + lane; i < e; i += 32) {
                 const uint32_t pid = B.pid[i];
                 const uint4 w = draw(s, pid, step, kRelax, 0);
-                if (!(u01<T>(w.x) < pth)) continue;
+                if (!selected<T>(s, B, b, e, i, w.x, pth, ns, step)) continue;
                 T C[3];
                 es_draw<T>(s, R, pid, step, w, C);
                 const double o0 = (double)B.c0[i] - R.u[0], o1 = (double)B.c1[i] - R.u[1],
@@ -498,7 +522,7 @@ __global__ void __launch_bounds__(256) k_relax(const SimDev* __restrict__ sims, 
                     for (uint32_t i = b + lane; i < e; i += 32) {
                         const uint32_t pid = B.pid[i];
                         const uint4 w = draw(s, pid, step, kRelax, 0);
-                        if (!(u01<T>(w.x) < pth)) continue;
+                        if (!selected<T>(s, B, b, e, i, w.x, pth, ns, step)) continue;
                         T C[3];
                         es_draw<T>(s, R, pid, step, w, C);
                         B.c0[i] = (T)(uo[0] + alpha * ((double)C[0] - mn[0]));

@@ -24,7 +24,9 @@ NPRM = 16
 FIELD_NAMES = ["n", "u0", "u1", "u2", "T", "pxx", "pyy", "pzz", "pxy", "pxz", "pyz", "q0", "q1", "q2",
                "Pne", "Nc"]
 BC = {"diffuse": 0, "specular": 1, "periodic": 2, "reservoir": 3}
-MODE = {"usp": 0, "sp": 1, "fixed": 2}
+MODE = {"usp": 0, "sp": 1, "fixed": 2, "spesbgk": 3}
+SELECTION = {"bernoulli": 0, "fixed_count": 1}
+SAMPLER = {"cholesky": 0, "gallis_torczynski": 1}
 PRECISION = {"fp64": 0, "fp32": 1}
 PIPELINE = {"plain": 0, "fused": 1}
 MAXSEG = 4
@@ -58,7 +60,8 @@ class Params(ctypes.Structure):
                 ("n_avg", c_int), ("mode", c_int), ("fixed_pne", c_double), ("reservoir_cols", c_int),
                 ("precision", c_int), ("pipeline", c_int), ("capacity_factor", c_double),
                 ("slab_count", c_int), ("slab_index", c_int), ("slab_group", c_int),
-                ("flux_axis", c_int), ("flux_pos", c_double), ("gll_average", c_int)]
+                ("flux_axis", c_int), ("flux_pos", c_double), ("gll_average", c_int),
+                ("selection", c_int), ("es_sampler", c_int)]
 
 
 class Region(ctypes.Structure):
@@ -211,10 +214,6 @@ def make_structs(w: dict, pipeline: str | None = None):
     segs = (WallSegment * MAXSEG)()
     for i, s in enumerate(w.get("segments", [])):
         segs[i] = WallSegment(s["pos"], s["lo"], s["hi"], BC[s["kind"]], s["T"], (c_double * 3)(*s["u"]))
-    if pr.get("selection", "bernoulli") != "bernoulli" or pr.get("es_sampler", "cholesky") != "cholesky":
-        raise ValueError("fixed-count selection (Eq. 9) and the Gallis-Torczynski sampler (Eq. 11) exist in "
-                         "the oracle only; the CUDA library relaxes with the Bernoulli draw and the Cholesky "
-                         "Gaussian")
     pipe = pipeline or pr.get("pipeline", "plain")
     params = Params(pr["Kn"], pr["L_ref"], pr["n_ref"], pr["dt"], pr["dt_over_tauc"],
                     (c_double * 3)(*pr["body_accel"]), pr["ppc_ref"], pr["n_avg"], MODE[pr["mode"]],
@@ -222,7 +221,8 @@ def make_structs(w: dict, pipeline: str | None = None):
                     float(pr.get("capacity_factor", 0.0)), int(pr.get("slab_count", 0)),
                     int(pr.get("slab_index", 0)), int(pr.get("slab_group", 0)),
                     int(pr.get("flux_axis", 0)), float(pr.get("flux_pos", 0.0)),
-                    int(pr.get("gll_average", 0)))
+                    int(pr.get("gll_average", 0)), SELECTION[pr.get("selection", "bernoulli")],
+                    SAMPLER[pr.get("es_sampler", "cholesky")])
     return gas, grid, faces, segs, len(w.get("segments", [])), params
 
 

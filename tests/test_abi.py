@@ -92,10 +92,10 @@ def test_struct_layouts_match_header(tmp_path):
 
 @pytest.mark.parametrize("key,value", [("selection", "fixed_count"), ("es_sampler", "gallis_torczynski"),
                                        ("mode", "spesbgk")])
-def test_oracle_only_ablations_fail_loudly(key, value):
-    """The SP-ESBGK ablations exist in the oracle only: the binding refuses
-    them instead of running something else."""
-    w = W.couette(ny=10, ppc=10)
+def test_ablations_need_the_plain_pipeline(key, value):
+    """The SP-ESBGK ablations run on the plain pipeline; the fused one
+    rejects them (INVALID_ARG) instead of running something else."""
+    w = W.sod(ny=10, ppc_left=10)
     w["params"][key] = value
-    with pytest.raises((ValueError, KeyError)):
-        _create_rc(w)
+    w["params"]["pipeline"] = "fused"
+    assert _create_rc(w) == -1

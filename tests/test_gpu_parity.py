@@ -303,3 +303,35 @@ def test_fp64_gll_average_parity(usp, name):
     assert np.allclose(pg[sel, 13], po[sel, 13], rtol=1e-10, atol=1e-13)   # P_ne
     fa, oa = g.sample(averaged=True), o.fields(averaged=True)
     assert np.all(np.abs(fa - oa) <= 1e-10 * np.maximum(np.abs(oa), np.abs(oa).max(1, keepdims=True) * 1e-3))
+
+
+@pytest.mark.parametrize("name,opts", [
+    ("cavity", dict(selection="fixed_count")),
+    ("sod", dict(mode="spesbgk", es_sampler="gallis_torczynski")),
+    ("slit", dict(mode="spesbgk", selection="fixed_count", es_sampler="gallis_torczynski")),
+])
+def test_fp64_ablation_parity(usp, name, opts):
+    """SP-ESBGK ablations on the plain FP64 path (fixed-count selection of
+    Eq. 9, the Gallis-Torczynski sampler of Eqs. 10-11, the SP-ESBGK step of
+    Eq. 8b): per particle against the oracle, relaxed counts bit-exact."""
+    if name == "cavity":
+        w = W.cavity(n=24, ppc=30, Kn=0.01, precision="fp64")
+    elif name == "sod":
+        w = W.sod(ny=200, ppc_left=80, precision="fp64")
+    else:
+        w = W.slit(nx=40, ny=20, ppc=30, precision="fp64")
+    w["params"].update(opts)
+    g, o = _pair(w, usp)
+    g.step(10)
+    o.step(10)
+    assert_particles_close(g.particles(), o.particles(), VSCALE, _cell_size(w))
+    pg, po = g.params(), o.params()
+    assert np.array_equal(pg[:, 14], po[:, 14])
+    assert np.array_equal(pg[:, 15], po[:, 15])
+    assert po[:, 15].sum() > 0
+    sel = po[:, 14] > 0
+    assert np.allclose(pg[sel, 10:14], po[sel, 10:14], rtol=1e-10, atol=1e-300)
+    fg, fo = g.sample(), o.fields()
+    scale = np.maximum(np.abs(fo), np.abs(fo).max(axis=1, keepdims=True) * 1e-3)
+    assert np.all(np.abs(fg - fo) <= 1e-10 * scale + 1e-300)
+    assert g.info()["counters"][0] == o.counters()[0]
