@@ -197,3 +197,55 @@ def test_couette_sampled_stress_matches_splitting_closed_form():
     want_u = x / ((1 - R_u) * (1 + x / 2))
     assert abs(m_u - want_u) < 4 * se_u + 0.01 * want_u, (m_u, se_u, want_u)
     assert want_sp / want_u > 3.0   # the Eq. 33 correction is what separates them
+
+
+def _thermal_couette_heat_ratio(mode, fixed_pne=0.0, r=5.0, ny=50, ppc=300, relax_steps=1500, blocks=10,
+                                block_steps=250, dT=50.0):
+    """Steady thermal Couette (plates at T0 +/- dT, Kn = 0.01): mean and
+    standard error over time blocks of -q_y / (kappa dT/dy) in the central
+    60 % of the gap (kappa = 15/4 k/m mu(T)), and x = nu dt in the bulk."""
+    w = W.couette(ny=ny, ppc=ppc, Kn=0.01, u_wall=0.0, dt_over_tauc=r, omega=0.81, seed=8)
+    w["faces"][2]["T"] = W.T0 + dT
+    w["faces"][3]["T"] = W.T0 - dT
+    w["params"]["mode"] = mode
+    w["params"]["fixed_pne"] = fixed_pne
+    o = oracle.OracleSim(w).init_particles()
+    o.step(relax_steps)
+    H = w["grid"]["hi"][1]
+    y = (np.arange(ny) + 0.5) * H / ny
+    c = slice(int(0.2 * ny), int(0.8 * ny))
+    ratios, xs = [], []
+    for _ in range(blocks):
+        acc = np.zeros((16, ny))
+        nu = 0.0
+        for _ in range(block_steps):
+            o.step(1)
+            acc += o.fields()
+            nu += o.params()[c, 11].mean()
+        F = acc / block_steps
+        T = F[4][c].mean()
+        kappa = 15.0 / 4.0 * KB_M * o.mu_ref * (T / W.T0) ** 0.81
+        slope = np.polyfit(y[c], F[4][c], 1)[0]
+        ratios.append(-F[12][c].mean() / (kappa * slope))
+        xs.append(nu / block_steps * o.dt)
+    ratios = np.array(ratios)
+    return ratios.mean(), ratios.std(ddof=1) / math.sqrt(blocks), float(np.mean(xs))
+
+
+def test_thermal_couette_heat_flux_matches_splitting_closed_form():
+    """In a temperature gradient a free flight builds heat flux at
+    -(5/2)(k/m) p dT/dy per unit time and a relaxation leaves e^-a of it
+    (relaxed particles are Gaussian, Eq. 8b; a = nu_ES dt), so the heat flux
+    sampled after a flight is (5/2)(k/m) p dt / (1 - e^-a) times -dT/dy: over
+    kappa = (15/4)(k/m) mu that is (2/3) x / (1 - e^-a) with x = nu dt.
+    USP samples q* = that / (1 + x Pr / 2) (Eq. 33 with P_ne = 1).  A heat
+    flux corrected without Pr, or relaxed at nu instead of nu_ES, misses."""
+    Pr = 2.0 / 3.0
+    m_sp, se_sp, x = _thermal_couette_heat_ratio("sp")
+    want_sp = (2.0 / 3.0) * x / (1.0 - math.exp(-Pr * x))
+    assert abs(m_sp - want_sp) < 4 * se_sp + 0.03 * want_sp, (m_sp, se_sp, want_sp)
+    m_u, se_u, x = _thermal_couette_heat_ratio("fixed", fixed_pne=1.0)
+    want_u = (2.0 / 3.0) * x / (1.0 - math.exp(-Pr * x)) / (1.0 + x * Pr / 2.0)
+    assert abs(m_u - want_u) < 4 * se_u + 0.03 * want_u, (m_u, se_u, want_u)
+    wrong = (2.0 / 3.0) * x / (1.0 - math.exp(-Pr * x)) / (1.0 + x / 2.0)   # no Pr in the q* factor
+    assert abs(m_u - wrong) > 4 * se_u + 0.03 * want_u
