@@ -149,3 +149,23 @@ def test_count_with_reservoir_faces_counts_exits_at_the_face():
             o.phase(ph)
     assert removed > 0                          # some flights did end on a reservoir face
     assert o.counters()[4] > 0                  # net flow toward the vacuum
+
+
+def test_reduced_mass_flow_is_one_for_free_molecular_effusion():
+    """The product's Eq. 41 normalisation (usp.reduced_mass_flow, host
+    arithmetic only) applied to the oracle's effusion count through an open
+    plane of height H gives W = 1: Mdot_fm = a p_1 / (sqrt(pi) v_1) is the
+    free-molecular flow, and the helper's symmetric doubling is matched by
+    taking a = 2H."""
+    from paper_1808_03801_gb300 import usp as U
+    w, L, H = _effusion_box()
+    o = oracle.OracleSim(w).init_particles()
+    o.phase(0)
+    count = int(o.counters()[4])
+    w["faces"][0] = dict(w["faces"][0], n=W.N0)   # the gas state the flow comes from
+    w["slit_width"] = 2.0 * H
+    Wr = U.reduced_mass_flow(w, count, 1, o.dt)
+    # the particles per unit area of the filled half set the expected count
+    n_left = sum(1 for x in o.particles()["pos"][:, 0] if x < 0.0) + count
+    expected = n_left / (L * H) * H * o.dt * math.sqrt(KB * W.T0 / W.M_AR / (2.0 * math.pi))
+    assert abs(Wr - 1.0) < 4.5 / math.sqrt(expected), Wr
