@@ -57,7 +57,7 @@ extern "C" {
 #define USP_MODE_SP 1        /* P_ne = 0: the SP-ESBGK scheme (Appendix B limit) */
 #define USP_MODE_FIXED_PNE 2 /* P_ne = params.fixed_pne everywhere */
 #define USP_MODE_SPESBGK 3   /* the SP-ESBGK step of Sec. 2 (Eq. 8b): the Gaussian target held at the
-                                post-convection state (no time instant, no Eq. 33 division); plain pipeline */
+                                post-convection state (no time instant, no Eq. 33 division) */
 
 /* relaxation selection and sampler (the SP-ESBGK ablations of Sec. 2; plain pipeline only) */
 #define USP_SELECT_BERNOULLI 0        /* each particle relaxes with probability 1 - exp(-nu_ES dt) */
@@ -168,8 +168,8 @@ typedef struct {
  *                  state is empty has Kn_GLL = 0.  0 (default): from the
  *                  instantaneous moments of the step.
  *   selection, es_sampler: USP_SELECT_* and USP_SAMPLER_* (0, 0 = the
- *                  defaults); the others, and USP_MODE_SPESBGK, need the
- *                  plain pipeline (INVALID_ARG otherwise).  With the
+ *                  defaults); the others need the plain pipeline
+ *                  (INVALID_ARG otherwise).  With the
  *                  Gallis-Torczynski sampler, usp_get_params slots 4-9 hold
  *                  B = ((1 - Pr)/(2 Pr)) sigma* / (rho theta) (xx, yy, zz, xy,
  *                  xz, yz; S = I - s B at the time instant of Eq. 32)

@@ -229,8 +229,7 @@ extern "C" int usp_create(const usp_gas* gas, const usp_grid* grid, const usp_bc
     if (prm->mode < 0 || prm->mode > 3) return USP_ERR_INVALID_ARG;
     if (prm->selection < 0 || prm->selection > 1 || prm->es_sampler < 0 || prm->es_sampler > 1)
         return USP_ERR_INVALID_ARG;
-    if ((prm->mode == USP_MODE_SPESBGK || prm->selection || prm->es_sampler) && prm->pipeline != USP_PIPE_PLAIN)
-        return USP_ERR_INVALID_ARG;
+    if ((prm->selection || prm->es_sampler) && prm->pipeline != USP_PIPE_PLAIN) return USP_ERR_INVALID_ARG;
     if (prm->precision != USP_FP64 && prm->precision != USP_FP32_MIXED) return USP_ERR_INVALID_ARG;
     if (prm->pipeline != USP_PIPE_PLAIN && prm->pipeline != USP_PIPE_FUSED) return USP_ERR_INVALID_ARG;
     if (prm->pipeline == USP_PIPE_FUSED && prm->precision != USP_FP32_MIXED) return USP_ERR_INVALID_ARG;

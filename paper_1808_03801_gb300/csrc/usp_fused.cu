@@ -1110,7 +1110,7 @@ __global__ void __launch_bounds__(128) k_params_f(const SimDev* __restrict__ sim
                 const float nu = pf / mu;
                 const float lam = 1.2766152f * mu / sqrtf(rho * pf);     // Eq. 36: 16 / (5 sqrt(2 pi))
                 float pne;
-                if (s.mode == kModeSP) pne = 0.0f;
+                if (s.mode == kModeSP || s.mode == kModeSPESBGK) pne = 0.0f;
                 else if (s.mode == kModeFixed) pne = (float)s.fixed_pne;
                 else {
                     // the cell's own stencil state: instantaneous, or the
@@ -1193,7 +1193,9 @@ __global__ void __launch_bounds__(128) k_params_f(const SimDev* __restrict__ sim
                 pr[4] = (float)l00; pr[5] = (float)l10; pr[6] = (float)l11;
                 pr[7] = (float)l20; pr[8] = (float)l21; pr[9] = (float)l22;
                 pr[10] = -expm1f(-nues * (float)s.dt);                                        // Eqs. 8b, 9
-                pr[11] = nu;
+                // the decay rate of Eq. 32; the SP-ESBGK step holds its target
+                // for the whole step (Eq. 8b): with P_ne = 0 a rate of 0 gives s = 1
+                pr[11] = s.mode == kModeSPESBGK ? 0.0f : nu;
                 pr[12] = nues;
                 pr[13] = pne;
                 pr[14] = 1.0f;

@@ -90,11 +90,11 @@ def test_struct_layouts_match_header(tmp_path):
             assert got[(cname, f[0])] == getattr(py, f[0]).offset, (cname, f[0])
 
 
-@pytest.mark.parametrize("key,value", [("selection", "fixed_count"), ("es_sampler", "gallis_torczynski"),
-                                       ("mode", "spesbgk")])
+@pytest.mark.parametrize("key,value", [("selection", "fixed_count"), ("es_sampler", "gallis_torczynski")])
 def test_ablations_need_the_plain_pipeline(key, value):
-    """The SP-ESBGK ablations run on the plain pipeline; the fused one
-    rejects them (INVALID_ARG) instead of running something else."""
+    """Fixed-count selection and the Gallis-Torczynski sampler run on the
+    plain pipeline; the fused one rejects them (INVALID_ARG) instead of
+    running something else."""
     w = W.sod(ny=10, ppc_left=10)
     w["params"][key] = value
     w["params"]["pipeline"] = "fused"

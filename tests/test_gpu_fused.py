@@ -91,10 +91,11 @@ def test_fused_periodic_box_conserves_momentum_energy(usp):
     assert g.info()["counters"][4] > 0      # relaxations happened
 
 
-@pytest.mark.parametrize("mode", ["usp", "sp"])
+@pytest.mark.parametrize("mode", ["usp", "sp", "spesbgk"])
 def test_fused_homogeneous_relaxation_closed_form(usp, mode):
     """The expectation of one relaxation step (derived from Eqs. 8b, 29-33)
-    holds for the FP32 sampler: sigma' = sigma [e^-a + (1 - e^-a)(1 - 1/Pr) kappa]."""
+    holds for the FP32 sampler: sigma' = sigma [e^-a + (1 - e^-a)(1 - 1/Pr) kappa]
+    (kappa = 1 for the SP-ESBGK step, whose target is held for the step)."""
     n = 1_000_000
     w = _fused(W.homogeneous_box(ppc=n, dt_over_tauc=5.0, mode=mode))
     pos, vel, pid = W.bimaxwellian(n, seed=21)
@@ -112,9 +113,12 @@ def test_fused_homogeneous_relaxation_closed_form(usp, mode):
     if mode == "usp":
         kappa = 1.0 / (1.0 + 0.5 * nu * prm_dt)
         f1, f2 = 1.0 + 0.5 * prm_dt * nu, 1.0 + 0.5 * prm_dt * nu  # sampled stress is sigma* (Eq. 33)
-    else:
+    elif mode == "sp":
         d = (nu_es - nu) * prm_dt
         kappa = a * math.expm1(d) / (d * math.expm1(a))
+        f1 = f2 = 1.0
+    else:
+        kappa = 1.0
         f1 = f2 = 1.0
     r = math.exp(-a) + (1 - math.exp(-a)) * (1 - 1 / W.PR_MONO) * kappa
     rho = F[0, 0] * W.M_AR
