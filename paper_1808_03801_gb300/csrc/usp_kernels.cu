@@ -4,13 +4,15 @@
 // captured in a CUDA graph.
 //
 // Stage order of one step n (Table 2 of the paper, unit particle weights):
-//   k_stream   advection + boundaries, new cell, cell histogram     (Table 2 step 3)
+//   k_stream   advection + boundaries, new cell, cell histogram,    (Table 2 step 3)
+//              net count through the counting plane                 (Eq. 41)
 //   k_scan     exclusive scan of the histogram                      (counting sort)
 //   k_scatter  particles to their sorted slots                      (counting sort)
 //   k_inject   refill of reservoir buffer cells
 //   k_moments  per-cell sums of shifted velocities                  (Eq. 1)
 //   k_params   per-cell P_ne, sigma*, q*, Cholesky, fields, Eq. 34  (Eqs. 16-18, 33, 35-36, 6c)
-//   k_relax    Bernoulli relaxation, ES sampling, conservation      (Eqs. 8b, 9, 27, 29-32)
+//   k_relax    Bernoulli or fixed-count selection, ES Gaussian or   (Eqs. 8b, 9, 27, 29-32,
+//              Gallis-Torczynski sampling, conservation              10-11)
 //   k_finish   advance the step counter and swap buffers
 #include "usp_device.cuh"
 
