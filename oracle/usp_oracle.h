@@ -17,6 +17,10 @@
  *   sampling ........... Eq. 34
  *   step outline ....... Table 2 with the weighted-particle steps 2, 4, 7
  *                        left out (all particle weights are 1).
+ *   options ............ counting plane for the slit mass flow (Eq. 41);
+ *                        Kn_GLL from the Eq. 34 averages; SP-ESBGK step
+ *                        (Eq. 8b), fixed-count selection (Eq. 9) and the
+ *                        Gallis-Torczynski sampler (Eqs. 10-11).
  * Every stage is a plain loop in FP64 over particles in (cell, pid) order.
  */
 #ifndef USP_ORACLE_H
