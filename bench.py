@@ -28,7 +28,12 @@ sys.path.insert(0, ROOT)
 METRIC = "particle-updates/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM = 6800.0
-KG2_DRAM_BYTES_PER_PARTICLE = 39.22   # profiles/k_g2_k_g1_sod_batch32_fused.md
+FUSED_SRC = os.path.join(ROOT, "paper_1808_03801_gb300", "csrc", "usp_fused.cu")
+# DRAM bytes per particle of one k_g2 launch (ncu dram__bytes_read.sum +
+# dram__bytes_write.sum of the 32-tube Sod case divided by its particles),
+# valid only for the k_g2 source with this SHA-1; any other source reports
+# traffic as null until it is captured again
+KG2_TRAFFIC = {"sha1": "2c48bccaba59bdfd686da2453f4e684ce39a3e00", "bytes_per_particle": 39.22}
 
 
 def parse():
@@ -44,10 +49,14 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="skip the launch autotuner")
     ap.add_argument("--prof-tubes", type=int, default=0,
                     help="profiling case for ncu: N tubes, 3 steps, then the stages of one step; no timing")
+    ap.add_argument("--prof-r", type=int, default=0, help="profiling case: tuning value fused_R (0: default)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--serve-requests", type=int, default=48,
-                    help="requests of the serving leg (0: skip); --serve-full uses the full request mix")
-    ap.add_argument("--serve-full", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=256,
+                    help="requests of the serving leg (0: skip); the full mix of 256 unless --serve-scaled")
+    ap.add_argument("--serve-scaled", action="store_true",
+                    help="smaller requests (N <= 4e5, 100-400 steps) for a quick serving check")
+    ap.add_argument("--no-configs", action="store_true", help="skip the per-config legs (C1-C4 alone)")
+    ap.add_argument("--only-config", nargs="*", default=None)
     return ap.parse_args()
 
 
@@ -304,10 +313,10 @@ def serving_leg(W, args, capacity):
     """Continuous batching of independent solves arriving as a Poisson stream at
     80% of the measured batched capacity; p50 / p99 time to solution."""
     from paper_1808_03801_gb300.serve import serve_requests
-    if args.serve_full:
-        reqs = W.serving_requests(n=256)
-    else:
+    if args.serve_scaled:
         reqs = W.serving_requests(n=args.serve_requests, n_min=1e4, n_max=4e5, steps_min=100, steps_max=400)
+    else:
+        reqs = W.serving_requests(n=args.serve_requests)
     work = []
     for w in reqs:
         g = w["grid"]
@@ -316,8 +325,151 @@ def serving_leg(W, args, capacity):
     rate = 0.8 * capacity / (sum(work) / len(work))
     rep, _ = serve_requests(reqs, rate=rate, hbm_budget=64 << 30, pipeline="fused", precision="fp32")
     rep.update({"arrival_rate_per_s": rate, "mix": "couette/poiseuille/cavity, FP32 fused, log-uniform N, Kn",
-                "full_mix": bool(args.serve_full)})
+                "full_mix": not args.serve_scaled and args.serve_requests == 256})
     return rep
+
+
+def kg2_traffic(n_particles):
+    """ncu DRAM bytes of one k_g2 launch scaled to n_particles, or None when the
+    kernel source differs from the one that was captured."""
+    import hashlib
+    with open(FUSED_SRC, "rb") as f:
+        sha = hashlib.sha1(f.read()).hexdigest()
+    return KG2_TRAFFIC["bytes_per_particle"] * n_particles if sha == KG2_TRAFFIC["sha1"] else None
+
+
+class L2Flush:
+    """A device buffer larger than the 129 MB L2, rewritten between timed steps."""
+
+    def __init__(self, torch, stream, nbytes=512 << 20):
+        self.buf = torch.empty(nbytes // 4, dtype=torch.float32, device="cuda")
+        self.stream = stream
+        self.torch = torch
+
+    def __call__(self):
+        with self.torch.cuda.stream(self.stream):
+            self.buf.fill_(1.0)
+
+
+def check_counters(name, sims):
+    """Particles lost to slot overflow (counter 5) or spilled past a full
+    bucket (counter 6) invalidate a timed run."""
+    over = sum(s.info()["counters"][5] for s in sims)
+    spill = sum(s.info()["counters"][6] for s in sims)
+    assert over == 0 and spill == 0, f"{name}: overflow {over}, spilled {spill}"
+    return {"overflow": over, "spilled": spill}
+
+
+RECORD_BYTES = {(1, "fp32"): 20, (2, "fp32"): 24, (1, "fp64"): 36, (2, "fp64"): 44}
+
+
+def time_sim_steps(torch, sim, steps, flush):
+    """Device time of `steps` single steps of one simulation, the L2 flushed
+    (outside the timed interval) before each."""
+    st = sim.stream
+    tot = 0.0
+    for _ in range(steps):
+        flush()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        sim.step(1)
+        b.record(st)
+        b.synchronize()
+        tot += a.elapsed_time(b) / 1e3
+    return tot
+
+
+def sim_stage_times(torch, sim, stages, flush, steps=3):
+    st = sim.stream
+    acc = {k: 0.0 for k in stages}
+    for _ in range(steps):
+        for k in stages:
+            flush()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            sim.run_stage(k)
+            b.record(st)
+            b.synchronize()
+            acc[k] += a.elapsed_time(b) / 1e3
+    return {k: v / steps for k, v in acc.items()}
+
+
+def config_leg(U, W, torch, name, w, pipeline, steps, warmup, stream, flush, hbm, comparator=True, tuning=None):
+    """One benchmark configuration as a single simulation: particle-updates/s
+    over `steps` single steps (L2 flushed before each), the per-stage device
+    times, the roofline of the dominant kernel, the overflow / spill counters
+    and the plain per-simulation FP64 path on the same workload."""
+    import copy
+    w = copy.deepcopy(w)
+    w["params"]["pipeline"] = pipeline
+    prec = w["params"]["precision"]
+    sim = U.Simulation(w, stream=stream).init_particles()
+    if tuning:
+        sim.set_tuning(tuning["fused_R"], tuning["grid_per_sm"])
+    sim.step(warmup)
+    sim.synchronize()
+    n = sim.info()["n_particles"]
+    el = time_sim_steps(torch, sim, steps, flush)
+    counters = check_counters(name, [sim])
+    reservoir = any(f["kind"] == "reservoir" for f in w["faces"])
+    stages = U.stage_list(pipeline)
+    if reservoir and pipeline == "fused":
+        stages = stages[:1] + [(11, "k_inject_f")] + stages[1:]
+    st = sim_stage_times(torch, sim, [k for k, _ in stages], flush)
+    names = dict(stages)
+    top = max(st, key=st.get)
+    rec = RECORD_BYTES[(w["grid"]["dim"], prec)]
+    alg = 2 * rec * n
+    step_s = el / steps
+    out = {"workload": name, "particles": n, "cells": sim.K, "precision": prec, "pipeline": pipeline,
+           "steps": steps, "ms_per_step": 1e3 * step_s, "value": n / step_s, "unit": METRIC,
+           "l2": "flushed before every timed step",
+           "roofline": {"bound": "hbm", "kernel": names[top], "bytes_per_particle": 2 * rec,
+                        "achieved": alg / st[top] / 1e9, "peak": hbm, "unit": "GB/s",
+                        "frac": alg / st[top] / 1e9 / hbm, "step_frac": alg / step_s / 1e9 / hbm},
+           "stage_ms": {names[k]: 1e3 * v for k, v in st.items()}, "counters": counters}
+    sim.close()
+    if comparator and not (pipeline == "plain" and prec == "fp64"):
+        wp = W.with_precision(w, "fp64")
+        wp["params"]["pipeline"] = "plain"
+        sp = U.Simulation(wp, stream=stream).init_particles()
+        sp.step(1)
+        sp.synchronize()
+        k = 3 if n > 2e6 else 6
+        elp = time_sim_steps(torch, sp, k, flush)
+        rate = sp.info()["n_particles"] * k / elp
+        out["plain_fp64_per_sim"] = {"value": rate, "unit": METRIC, "ratio": out["value"] / rate}
+        sp.close()
+    torch.cuda.synchronize()
+    return out
+
+
+def config_legs(U, W, torch, args, stream, hbm, pipeline):
+    """Every benchmark shape of the paper's Sec. 4 at one GPU, each alone."""
+    from paper_1808_03801_gb300 import autotune
+    flush = L2Flush(torch, stream)
+    legs = {}
+    specs = [("C1_couette_fp64", W.couette(), "plain", 20),
+             ("C2_sod_single", W.sod(), pipeline, 20),
+             ("C3_cavity_Kn1e-3", W.cavity(Kn=1e-3), pipeline, 10),
+             ("C3_cavity_Kn1e-2", W.cavity(Kn=1e-2), pipeline, 10),
+             ("C4_slit", W.slit(), pipeline, 8)]
+    for name, w, pipe, steps in specs:
+        if args.only_config and name not in args.only_config:
+            continue
+        tuning = None
+        if pipe == "fused" and not args.no_tune:
+            import copy
+            wt = copy.deepcopy(w)
+            wt["params"]["pipeline"] = pipe
+            tuning = autotune.tune(wt, use_cache=False)
+        legs[name] = config_leg(U, W, torch, name, w, pipe, steps, 3, stream, flush, hbm,
+                                comparator=not args.no_comparator, tuning=tuning)
+        if tuning:
+            legs[name]["tuning"] = {k: v for k, v in tuning.items() if k != "tried"}
+    del flush
+    torch.cuda.empty_cache()
+    return legs
 
 
 def run_gpu(args):
@@ -359,6 +511,7 @@ def run_gpu(args):
     if dist:
         el = reduce_max(el, dist, "cuda")
     clocks.stop()
+    headline_counters = check_counters("sod batch", sims)
     value = whole_job_rate(n_total, world, args.steps, el)
     ms = 1e3 * el / args.steps
 
@@ -371,9 +524,7 @@ def run_gpu(args):
     rec = 20                         # FP32 1-D record: y, c0, c1, c2 (4 B each), pid (4 B)
     alg = 2 * rec * n_total          # read and write each particle once per step
     achieved = alg / st[top] / 1e9
-    # DRAM bytes per particle of k_g2 from the ncu capture in profiles/ (32-tube
-    # case, scaled by particles); recorded for the current k_g2
-    traffic = KG2_DRAM_BYTES_PER_PARTICLE * n_total if names[top] == "k_g2" else None
+    traffic = kg2_traffic(n_total) if names[top] == "k_g2" else None
     roof = {"bound": "hbm", "kernel": names[top], "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "traffic": traffic, "peak_source": f"{src} hbm_gbs (copy, burst)",
             "stage_ms": {names[k]: 1e3 * v for k, v in st.items()},
@@ -386,7 +537,7 @@ def run_gpu(args):
               "config": dict(workload_cfg(args.batch, pipeline),
                              tuning={k: v for k, v in (tuning or {}).items() if k != "tried"}),
               "clocks": clocks.summary(), "roofline": roof,
-              "gpu_launches": launches}
+              "gpu_launches": launches, "counters": headline_counters}
     B.close()
     for s in sims:
         s.close()
@@ -417,6 +568,8 @@ def run_gpu(args):
                 s.close()
             result["plain_fp64_per_sim"] = {"value": statistics.mean(cmp_rates), "unit": METRIC,
                                             "ratio": value / statistics.mean(cmp_rates)}
+        if not args.no_configs:
+            result["configs"] = config_legs(U, W, torch, args, stream, hbm, pipeline)
         if args.serve_requests > 0:
             result["serving"] = serving_leg(W, args, value)
         if not args.no_cpu_baseline and world == 1:
@@ -444,6 +597,8 @@ def run_profile_case(args):
         w = W.sod(precision="fp32", seed=1 + i)
         w["params"]["pipeline"] = "fused"
         sims.append(U.Simulation(w).init_particles())
+        if args.prof_r:
+            sims[-1].set_tuning(args.prof_r, 0)
     B = U.Batch(hbm_budget=64 << 30, max_sims=len(sims))
     for sim in sims:
         assert B.admit(sim) == 0

@@ -64,7 +64,7 @@ struct usp_handle {
     std::string err;
     std::vector<uint32_t> inj_count_host;
     int batch_refs = 0;
-    int fused_R = 8;                  // staging capacity of the fused kernels: 32 R particles per cell pass
+    int fused_R = 8;                  // k_g2 consumer warps per CTA: 3, 7, 15 for R = 4, 8, 12
     int grid_per_sm = 8;              // persistent blocks per SM of the tiled kernels
     cudaStream_t batch_stream = nullptr;   // stream of the batch the handle is admitted to
 };
@@ -468,6 +468,7 @@ static int alloc_particles(usp_handle* h, int64_t n) {
         const double ff = h->capacity_factor > 0 ? std::max(h->capacity_factor, 1.6) : (s.has_reservoir ? 2.5 : 1.6);
         cap = (int64_t)std::ceil(n * ff) + 24 * (int64_t)s.K + 4 * (int64_t)s.inj_total + 4096;
     }
+    cap = (cap + 3) & ~(int64_t)3;   // whole 16-byte groups of FP32 slots (bulk copies of the fused pipeline)
     if (cap > (int64_t)0x7FFFFFFFll) return fail(h, USP_ERR_CAPACITY, "particle capacity exceeds 2^31 - 1");
     destroy_graphs(h->graphs);
     // storage of a similar size is kept (a re-load of the same problem

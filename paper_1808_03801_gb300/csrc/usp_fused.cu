@@ -1,12 +1,14 @@
 // usp_fused.cu -- the fused FP32 pipeline of the USP-ESBGK step (sm_103a).
 //
 // One step n reads buffer p = cur and writes buffer q = cur ^ 1:
-//   k_g2      per cell (one warp): the relaxation of step n-1 still pending
-//             on the cell's particles (Eqs. 8b, 9, 27, 29-32 with the per-cell
-//             momentum / energy conservation), then advection of step n with
-//             the boundaries, the new cell, and the write into that cell's
-//             bucket of buffer q (the scatter of the counting sort; the
-//             bucket sizes come from the previous histogram plus slack).
+//   k_g2      per cell (one consumer warp, the cell's planes copied into a
+//             shared-memory ring by a producer warp of the same CTA): the
+//             relaxation of step n-1 still pending on the cell's particles
+//             (Eqs. 8b, 9, 27, 29-32 with the per-cell momentum / energy
+//             conservation), then advection of step n with the boundaries,
+//             the new cell, and the write into that cell's bucket of buffer
+//             q (the scatter of the counting sort; the bucket sizes come from
+//             the previous histogram plus slack).
 //   k_inject  reservoir buffer cells refilled into buffer q.
 //   k_g1      per cell (one warp): moments of Eq. 1 in one pass, as sums
 //             about the cell's mean velocity of the previous step, and the
@@ -26,6 +28,8 @@
 // conservation factors use sums about the cell mean, so neither cancels.
 // Each particle is read once and written once by k_g2 and its velocity is
 // read once more by k_g1.
+#include <algorithm>
+
 #include "usp_device.cuh"
 
 namespace usp {
@@ -168,27 +172,45 @@ __device__ __forceinline__ void es_draw1(const FCell& f, const TimeDraw& td, flo
 }
 
 // ---------------------------------------------------------------------------
-// k_g2: pending relaxation + advection + bucket scatter.  MODE kFull does
-// both; kRelaxOnly applies the pending relaxation in place (before the
-// particles are read back).
+// k_g2: pending relaxation + advection + bucket scatter, as a producer /
+// consumer pipeline inside each CTA.
 //
-// One warp per cell.  The cell's particles are copied (cp.async, the whole
-// cell at once) into a per-warp shared memory area of CAP entries and every
-// pass walks them with a rolled loop, so that the per-particle code (the
-// Philox draw, the ES sample, advection) appears once in the binary:
-//   stage    relaxation draws, conservation sums;
-//   pass A   conservation, advection, destination cell, arrivals counted per
-//            slot of the cell's destination window;
+// Warp 0 of a CTA is the producer.  It takes runs of kG2Run cells from the
+// per-simulation queues (SimDyn::qnext), reads their bucket bounds with one
+// load per lane, allocates room for each cell in a ring buffer in shared
+// memory and starts bulk asynchronous copies (cp.async.bulk) of the cell's
+// particle planes and of its 64-byte FP32 parameter record; the copies
+// complete on the descriptor's mbarrier ("full").
+//
+// The other NC warps are consumers.  Each takes the next descriptor in
+// order, waits for its copies and processes the cell with rolled loops over
+// the staged particles (so the per-particle code appears once):
+//   relax    relaxation draws of the pending step (one Philox call per
+//            particle), conservation sums;
+//   pass A   conservation, advection, destination cell and its slot in the
+//            cell's 64-cell destination window; each particle's rank among
+//            the arrivals of its slot;
 //   pass B   one atomic reservation per occupied slot in the destination
-//            buckets (a single round trip for the whole cell) and each
-//            slot's offset in a slot-ordered list of the cell's particles;
-//   pass C   rank within the slot -> the particle's place in that list;
-//   pass D   the list written out: consecutive lanes write consecutive
-//            places of a destination bucket (whole lines, not scattered
-//            words).
-// Cells above CAP particles are processed in chunks: the conservation sums in
-// a first sweep, the update in a second sweep that redraws the same
-// counter-based random numbers.
+//            buckets (one round trip for the whole cell) and each slot's
+//            offset in a slot-ordered list of the cell's particles;
+//   pass C   the list: perm[offset of the slot + rank] = particle;
+//   pass D   the list written out by consecutive lanes, so each store fills
+//            whole lines of one destination bucket.
+// Then it releases the descriptor ("empty" mbarrier) and the producer may
+// reuse its ring space.  While a consumer works on a cell, the copies of the
+// cells behind it are in flight, so HBM latency is paid once per run of
+// cells rather than several times per cell.
+//
+// Cells whose bucket is not 16-byte aligned (the compact layout right after
+// a set-up sort) are loaded by the consumer itself; cells above the largest
+// ring allocation (max_stage particles) are processed in chunks with the
+// conservation sums in a first sweep and the update in a second one that
+// redraws the same counter-based random numbers.
+//
+// Every wait on an mbarrier is bounded (kG2WaitNs of global time); a wait
+// that runs out adds kG2TimeoutMark to the overflow counter of simulation 0
+// and ends the warp's work, so a fault in the pipeline shows up as lost
+// particles instead of a hung GPU.
 // ---------------------------------------------------------------------------
 __device__ __noinline__ bool advect_slow(const SimDev& s, uint32_t step, uint32_t pid, float& x, float& y, float* c) {
     return advect<float>(s, step, pid, x, y, c);
@@ -238,13 +260,19 @@ __device__ __forceinline__ void make_ctx(const SimDev& s, int q, Ctx& C) {
     C.cell0 = s.row0 * s.nx;
 }
 
-// cell of an FP32 position: floor of the scaled offset, clamped to the grid
+// column and row of an FP32 position: floor of the scaled offset, clamped
+// to the grid (1-D: ix = 0)
+template <int DIM>
+__device__ __forceinline__ void cell_xy(const Ctx& C, float x, float y, int& ix, int& iy) {
+    iy = (int)fminf(fmaxf(floorf((y - C.lo1) * C.inv_dy), 0.0f), (float)C.nym1);
+    ix = DIM == 1 ? 0 : (int)fminf(fmaxf(floorf((x - C.lo0) * C.inv_dx), 0.0f), (float)C.nxm1);
+}
+
 template <int DIM>
 __device__ __forceinline__ int cell_f(const Ctx& C, float x, float y) {
-    const float fy = fminf(fmaxf(floorf((y - C.lo1) * C.inv_dy), 0.0f), (float)C.nym1);
-    if (DIM == 1) return (int)fy;
-    const float fx = fminf(fmaxf(floorf((x - C.lo0) * C.inv_dx), 0.0f), (float)C.nxm1);
-    return (int)fy * C.nx + (int)fx;
+    int ix, iy;
+    cell_xy<DIM>(C, x, y, ix, iy);
+    return DIM == 1 ? iy : iy * C.nx + ix;
 }
 
 template <int DIM>
@@ -311,101 +339,31 @@ __device__ __forceinline__ void emit_c(const SimDev& s, const Ctx& C, int b, uin
     }
 }
 
-// per-warp staging area
-struct Stage {
-    float* x;
-    float* y;
-    float* v0;
-    float* v1;
-    float* v2;
-    uint32_t* id;
-    unsigned char* sel;
-};
-
-// largest staging area per warp: holds a 360-particle cell with its
-// fluctuations (+3 standard deviations) while leaving part of the SM's
-// shared memory / L1 carve-out to the cache
-constexpr int kCapMax = 416;
-
-// bytes per staged particle: (x,) y, v0, v1, v2, id, relaxation flag
-template <int CAP, int DIM>
-__host__ __device__ constexpr int stage_bytes() {
-    return CAP * (DIM == 2 ? 25 : 21);
-}
-
-template <int CAP, int DIM>
-__device__ __forceinline__ Stage stage_of(unsigned char* base, int warp) {
-    float* f = (float*)(base + (size_t)warp * stage_bytes<CAP, DIM>());
-    Stage S;
-    S.x = nullptr;
-    if (DIM == 2) {
-        S.x = f;
-        f += CAP;
-    }
-    S.y = f;
-    S.v0 = S.y + CAP;
-    S.v1 = S.v0 + CAP;
-    S.v2 = S.v1 + CAP;
-    S.id = (uint32_t*)(S.v2 + CAP);
-    S.sel = (unsigned char*)(S.id + CAP);
-    return S;
-}
-
-__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
-    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
-}
-
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
 // Destination window of a cell: the 64 cells that its particles can reach in
 // one step without leaving it (1-D: offsets -32..31; 2-D: an 8 x 8 block
 // around the cell).  The warp counts its arrivals per window slot in shared
 // memory, reserves each slot's range in the destination bucket with one
 // global atomic, then writes; particles that land outside the window reserve
-// their place one group at a time.
+// their place one at a time.
 constexpr int kWin = 64;
 constexpr unsigned char kSlotNone = 0xFF;   // removed, nothing to write
 constexpr unsigned char kSlotFar = 0xFE;    // outside the window
 constexpr unsigned char kSlotOther = 0xFD;  // in another slab of a decomposed domain
 
 template <int DIM>
-__device__ __forceinline__ int win_slot(int dc, int cell, int cx, int cy, int nx) {
+__device__ __forceinline__ int win_slot_xy(int ix, int iy, int cell, int cx, int cy) {
     if (DIM == 1) {
-        const int o = dc - cell + 32;
+        const int o = iy - cell + 32;
         return (o >= 0 && o < kWin) ? o : -1;
     }
-    const int iy = dc / nx, ix = dc - iy * nx;
     const int oy = iy - cy + 4, ox = ix - cx + 4;
-    return (oy >= 0 && oy < 8 && ox >= 0 && ox < 8) ? oy * 8 + ox : -1;
+    return ((unsigned)oy < 8u && (unsigned)ox < 8u) ? oy * 8 + ox : -1;
 }
 
 template <int DIM>
 __device__ __forceinline__ int win_cell(int k, int cell, int cx, int cy, int nx) {
     if (DIM == 1) return cell + k - 32;
     return (cy + (k >> 3) - 4) * nx + (cx + (k & 7) - 4);
-}
-
-// Per-warp copy of the header of one cell: bucket bounds, arrivals and the
-// FP32 relaxation parameters, fetched with one round of cp.async (one word
-// per lane) instead of two dependent rounds of loads.
-struct alignas(16) Hdr {
-    float prm[kNFPrm];   // the cell's parameter record: u[3], theta, L[6], P_relax, nu, nu_ES, P_ne, valid
-    uint32_t lay[2];
-    uint32_t cnt;
-};
-
-__device__ __forceinline__ void cp_async16_ca(void* dst, const void* src) {
-    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
-}
-
-__device__ __forceinline__ void fetch_hdr(const SimDev& s, int p, int cell, Hdr& H, int lane) {
-    if (lane < 2) cp_async4(&H.lay[lane], s.lay[p] + cell + lane);
-    else if (lane == 2) cp_async4(&H.cnt, s.cnt[p] + cell);
-    else if (lane < 7) cp_async16_ca(&H.prm[4 * (lane - 3)], s.fprm + (size_t)cell * kNFPrm + 4 * (lane - 3));
-    cp_async_wait_all();
-    __syncwarp();
 }
 
 // a particle that crossed into another slab of a decomposed domain: its
@@ -478,28 +436,204 @@ __device__ __forceinline__ void put_own(const SimDev& s, const Ctx& C, int q, ui
 // kFullSlab: kFull for batches holding slabs of a decomposed domain (routes
 // particles that leave the slab; the plain kFull code carries no such check).
 // kFullFlux: kFull for batches where some simulation counts particles
-// through a plane (kFullSlab counts too)
+// through a plane (kFullSlab counts too).  kRelaxOnly applies the pending
+// relaxation in place (before the particles are read back).
 enum { kFull = 0, kRelaxOnly = 1, kFullSlab = 2, kFullFlux = 3 };
 
-template <int CAP, int DIM, int MODE>
-__device__ void g2_cell(const SimDev* __restrict__ sims, const SimDev& s, int cell, const Hdr& H, int p, uint32_t step,
-                        bool pending, uint32_t* spl,
-                        const Stage& S, uint32_t* win, uint16_t* perm, int lane) {
-    const uint32_t base = H.lay[0];
-    const uint32_t top = min(H.lay[1], (uint32_t)s.cap);
-    const uint32_t capc = top > base ? top - base : 0u;
-    const uint32_t arrived = H.cnt;
-    const uint32_t nb = min(arrived, capc);
-    uint32_t nsp = 0;
-    if (arrived > nb) nsp = collect_spill(s, p, cell, spl, lane);
-    const uint32_t n = nb + nsp;
-    if (n == 0) return;
+// ---- pipeline constants ----------------------------------------------------
+constexpr int kG2Desc = 32;            // descriptors (cells in flight) per CTA
+constexpr int kG2Run = 16;             // cells taken from a queue at once by the producer
+constexpr int kG2Spill = 32;           // spill-list entries a cell may add to its bucket
+constexpr unsigned long long kG2WaitNs = 2000000000ull;   // bound of one mbarrier wait
+constexpr unsigned long long kG2TimeoutMark = 1ull << 40;
+
+enum : uint32_t { kDescBulk = 1u, kDescPending = 2u, kDescParity = 4u };
+
+// One cell handed from the producer to a consumer.  prm is filled by a bulk
+// copy of the cell's parameter record; the rest by the producer.
+struct alignas(16) G2Desc {
+    float prm[kNFPrm];   // u[3], theta, L[6], P_relax, nu, nu_ES, P_ne, valid, spare
+    uint32_t base;       // first slot of the cell's bucket in buffer p
+    uint32_t nb;         // particles in the bucket (arrivals beyond it are in the spill list)
+    uint32_t arrived;    // arrivals into the cell (bucket + spill list)
+    uint32_t off;        // byte offset of the cell's area in the ring
+    uint32_t m;          // particle slots of that area
+    int cell;            // -1: no more cells for this consumer
+    int ent;             // simulation descriptor entry in shared memory
+    uint32_t step;       // step counter of the simulation (Philox word 1)
+    uint32_t flags;      // kDesc*
+    uint32_t end;        // ring counter after this allocation (producer bookkeeping)
+};
+
+// bytes of ring per staged particle: (x,) y, v0, v1, v2, id; slot; rank; list entry
+template <int DIM>
+__host__ __device__ constexpr uint32_t g2_bytes_per_particle() {
+    return (DIM == 2 ? 24u : 20u) + 1u + 2u + 2u;
+}
+
+struct G2Stage {
+    float* x;
+    float* y;
+    float* v0;
+    float* v1;
+    float* v2;
+    uint32_t* id;
+    unsigned char* sel;
+    uint16_t* rank;
+    uint16_t* perm;
+};
+
+template <int DIM>
+__device__ __forceinline__ G2Stage g2_stage(unsigned char* ring, uint32_t off, uint32_t m) {
+    float* f = (float*)(ring + off);
+    G2Stage S;
+    S.x = nullptr;
+    if (DIM == 2) {
+        S.x = f;
+        f += m;
+    }
+    S.y = f;
+    S.v0 = f + m;
+    S.v1 = f + 2 * m;
+    S.v2 = f + 3 * m;
+    S.id = (uint32_t*)(f + 4 * m);
+    S.sel = (unsigned char*)(f + 5 * m);
+    S.rank = (uint16_t*)(S.sel + m);
+    S.perm = S.rank + m;
+    return S;
+}
+
+// ---- mbarrier and bulk-copy primitives (PTX, sm_90+) ----------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, uint32_t tx) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_u32(bar)),
+                 "r"(tx)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// wait for the phase of `bar` with the given parity to complete, at most
+// kG2WaitNs; false when the bound ran out
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        for (int k = 0; k < 64; ++k)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > kG2WaitNs) return false;
+    }
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// order this thread's generic-proxy accesses to shared memory before later
+// bulk copies (async proxy) into the same bytes
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ void g2_timeout(const SimDev* __restrict__ sims) {
+    atomicAdd(&sims[0].dyn->counters[kCntOverflow], kG2TimeoutMark);
+}
+
+// counters a consumer accumulates in registers and adds once per simulation
+struct G2Acc {
+    unsigned long long relaxed, removed;
+};
+
+__device__ __forceinline__ void g2_flush(G2Acc& a, SimDyn* dyn, int lane) {
+    if (dyn && lane == 0) {
+        if (a.relaxed) atomicAdd(&dyn->counters[kCntRelaxed], a.relaxed);
+        if (a.removed) atomicAdd(&dyn->counters[kCntRemoved], a.removed);
+    }
+    a.relaxed = a.removed = 0;
+}
+
+// ---- consumer: one cell ------------------------------------------------------
+// conservation sums over the relaxed subset of a cell: old peculiar
+// velocities about the cell mean (a) and new peculiar velocities (b)
+struct G2Sums {
+    float a0, a1, a2, ae, b0, b1, b2, be, nr;
+};
+
+// per-cell factors of the momentum / energy correction
+struct G2Cons {
+    float uo0, uo1, uo2, mn0, mn1, mn2, alpha;
+    bool apply;
+};
+
+// staged particles [0, cnt) of a cell area from their bucket (at bucket
+// index off) and spill-list entries; with `have_bucket` the bucket part is
+// already there (bulk copy)
+template <int DIM>
+__device__ __forceinline__ void g2_load(const SimDev& s, const G2Stage& S, int p, uint32_t base, uint32_t nb,
+                                        const uint32_t* spl, uint32_t off, uint32_t cnt, bool have_bucket, int lane) {
+    const uint32_t mb = off < nb ? min(cnt, nb - off) : 0u;
+    __syncwarp();
+    if (!have_bucket) {
+        const Src P = src_of(s, p);
+#pragma unroll 2
+        for (uint32_t j = lane; j < mb; j += 32) {
+            const uint32_t i = base + off + j;
+            if (DIM == 2) S.x[j] = P.x[i];
+            S.y[j] = P.y[i];
+            S.v0[j] = P.v0[i];
+            S.v1[j] = P.v1[i];
+            S.v2[j] = P.v2[i];
+            S.id[j] = P.id[i];
+        }
+    }
+#pragma unroll 1
+    for (uint32_t j = mb + lane; j < cnt; j += 32) {
+        float x = 0.0f, y, v0, v1, v2;
+        uint32_t id;
+        load_particle<DIM>(s, p, base, nb, spl, off + j, x, y, v0, v1, v2, id);
+        if (DIM == 2) S.x[j] = x;
+        S.y[j] = y; S.v0[j] = v0; S.v1[j] = v1; S.v2[j] = v2; S.id[j] = id;
+    }
+    __syncwarp();
+}
+
+// Relaxation draws of the staged particles [0, cnt): a relaxed particle
+// gets its new peculiar velocity in v0..v2 and sel = 1 (else sel = 0);
+// with SUMS the conservation sums of the relaxed subset are accumulated.
+// The cell's FP32 parameters live only in this scope.
+template <bool SUMS>
+__device__ __forceinline__ void g2_relax(const float* prm, const SimDev& s, const G2Stage& S, uint32_t cnt,
+                                         uint32_t step, bool relax, int lane, G2Sums& R) {
     FCell f;
 #pragma unroll
-    for (int d = 0; d < 3; ++d) f.u[d] = H.prm[d];
-    f.th = H.prm[3];
+    for (int d = 0; d < 3; ++d) f.u[d] = prm[d];
+    f.th = prm[3];
     {   // M = L L^T - theta I from the FP64-built factor L
-        const float L0 = H.prm[4], L1 = H.prm[5], L2 = H.prm[6], L3 = H.prm[7], L4 = H.prm[8], L5 = H.prm[9];
+        const float L0 = prm[4], L1 = prm[5], L2 = prm[6], L3 = prm[7], L4 = prm[8], L5 = prm[9];
         f.M[0] = L0 * L0 - f.th;
         f.M[1] = L1 * L0;
         f.M[2] = L1 * L1 + L2 * L2 - f.th;
@@ -507,13 +641,10 @@ __device__ void g2_cell(const SimDev* __restrict__ sims, const SimDev& s, int ce
         f.M[4] = L3 * L1 + L4 * L2;
         f.M[5] = L3 * L3 + L4 * L4 + L5 * L5 - f.th;
     }
-    f.pr = H.prm[10];
-    f.nu = H.prm[11];
-    f.nues = H.prm[12];
-    f.pne = H.prm[13];
-    f.valid = H.prm[14] != 0.0f;
-    const bool relax = pending && f.valid;
-    if (MODE == kRelaxOnly && !relax) return;
+    f.pr = prm[10];
+    f.nu = prm[11];
+    f.nues = prm[12];
+    f.pne = prm[13];
     TimeDraw td;
     td.dt = s.f_dt;
     td.a = f.nues * td.dt;
@@ -521,278 +652,275 @@ __device__ void g2_cell(const SimDev* __restrict__ sims, const SimDev& s, int ce
     td.ema = __expf(-td.a);
     td.inv_nues = 1.0f / f.nues;
     td.inv_pr = f.pr > 0.0f ? 1.0f / f.pr : 0.0f;
-    const int q = p ^ 1;
-    const uint32_t nch = (n + CAP - 1) / CAP;
-    const Src P = src_of(s, p);
     const uint2 key = make_uint2(s.key0, s.key1);
-
-    // stage chunk ch: the particles are copied into the staging planes
-    // (asynchronously from the bucket, directly from the spill list), then
-    // relaxed particles get their new peculiar velocity in v0..v2 and their
-    // flag in sel; if `sums`, the conservation sums are accumulated
-    float a0 = 0, a1 = 0, a2 = 0, ae = 0, b0 = 0, b1 = 0, b2 = 0, be = 0, nr = 0;
-    auto stage_chunk = [&](uint32_t ch, bool sums) -> uint32_t {
-        const uint32_t off = ch * CAP;
-        const uint32_t m = min((uint32_t)CAP, n - off);
-        const uint32_t mb = off < nb ? min(m, nb - off) : 0u;
-        __syncwarp();
 #pragma unroll 1
-        for (uint32_t j = lane; j < mb; j += 32) {
-            const uint32_t i = base + off + j;
-            if (DIM == 2) cp_async4(S.x + j, P.x + i);
-            cp_async4(S.y + j, P.y + i);
-            cp_async4(S.v0 + j, P.v0 + i);
-            cp_async4(S.v1 + j, P.v1 + i);
-            cp_async4(S.v2 + j, P.v2 + i);
-            cp_async4(S.id + j, P.id + i);
-        }
-#pragma unroll 1
-        for (uint32_t j = mb + lane; j < m; j += 32) {
-            float x = 0.0f, y, v0, v1, v2;
-            uint32_t id;
-            load_particle<DIM>(s, p, base, nb, spl, off + j, x, y, v0, v1, v2, id);
-            if (DIM == 2) S.x[j] = x;
-            S.y[j] = y; S.v0[j] = v0; S.v1[j] = v1; S.v2[j] = v2; S.id[j] = id;
-        }
-        cp_async_wait_all();
-        __syncwarp();
-#pragma unroll 1
-        for (uint32_t j0 = lane; j0 < m; j0 += 64) {
-            const uint32_t j1 = j0 + 32;
-            const bool has1 = j1 < m;
-            unsigned char s0 = 0, s1 = 0;
-            if (relax) {
-                const float p0 = S.v0[j0], q0 = S.v1[j0], r0 = S.v2[j0];
-                const uint32_t id0 = S.id[j0];
-                float p1 = 0.0f, q1 = 0.0f, r1 = 0.0f;
-                uint32_t id1 = 0;
-                if (has1) {
-                    p1 = S.v0[j1]; q1 = S.v1[j1]; r1 = S.v2[j1];
-                    id1 = S.id[j1];
+    for (uint32_t j0 = lane; j0 < cnt; j0 += 64) {
+        const uint32_t j1 = j0 + 32;
+        const bool has1 = j1 < cnt;
+        unsigned char s0 = 0, s1 = 0;
+        if (relax) {
+            const uint32_t id0 = S.id[j0];
+            const uint32_t id1 = has1 ? S.id[j1] : 0u;
+            const uint4 w0 = philox(make_uint4(id0, step, kRelax, 0), key);
+            const uint4 w1 = philox(make_uint4(id1, step, kRelax, 0), key);
+            const float x0 = u01<float>(w0.x), x1 = u01<float>(w1.x);
+            s0 = x0 < f.pr;
+            s1 = has1 && x1 < f.pr;
+            if (s0 | s1) {
+                float C0[3], C1[3];
+                es_draw1(f, td, x0, w0, C0);
+                es_draw1(f, td, x1, w1, C1);
+                if (s0) {
+                    if (SUMS) {
+                        const float o0 = S.v0[j0] - f.u[0], o1 = S.v1[j0] - f.u[1], o2 = S.v2[j0] - f.u[2];
+                        R.a0 += o0; R.a1 += o1; R.a2 += o2;
+                        R.ae += o0 * o0 + o1 * o1 + o2 * o2;
+                        R.b0 += C0[0]; R.b1 += C0[1]; R.b2 += C0[2];
+                        R.be += C0[0] * C0[0] + C0[1] * C0[1] + C0[2] * C0[2];
+                        R.nr += 1.0f;
+                    }
+                    S.v0[j0] = C0[0]; S.v1[j0] = C0[1]; S.v2[j0] = C0[2];
                 }
-                const uint4 w0 = philox(make_uint4(id0, step, kRelax, 0), key);
-                const uint4 w1 = philox(make_uint4(id1, step, kRelax, 0), key);
-                const float x0 = u01<float>(w0.x), x1 = u01<float>(w1.x);
-                s0 = x0 < f.pr;
-                s1 = has1 && x1 < f.pr;
-                if (s0 | s1) {
-                    float C0[3], C1[3];
-                    es_draw1(f, td, x0, w0, C0);
-                    es_draw1(f, td, x1, w1, C1);
-                    if (s0) {
-                        if (sums) {
-                            const float o0 = p0 - f.u[0], o1 = q0 - f.u[1], o2 = r0 - f.u[2];
-                            a0 += o0; a1 += o1; a2 += o2;
-                            ae += o0 * o0 + o1 * o1 + o2 * o2;
-                            b0 += C0[0]; b1 += C0[1]; b2 += C0[2];
-                            be += C0[0] * C0[0] + C0[1] * C0[1] + C0[2] * C0[2];
-                            nr += 1.0f;
-                        }
-                        S.v0[j0] = C0[0]; S.v1[j0] = C0[1]; S.v2[j0] = C0[2];
+                if (s1) {
+                    if (SUMS) {
+                        const float o0 = S.v0[j1] - f.u[0], o1 = S.v1[j1] - f.u[1], o2 = S.v2[j1] - f.u[2];
+                        R.a0 += o0; R.a1 += o1; R.a2 += o2;
+                        R.ae += o0 * o0 + o1 * o1 + o2 * o2;
+                        R.b0 += C1[0]; R.b1 += C1[1]; R.b2 += C1[2];
+                        R.be += C1[0] * C1[0] + C1[1] * C1[1] + C1[2] * C1[2];
+                        R.nr += 1.0f;
                     }
-                    if (s1) {
-                        if (sums) {
-                            const float o0 = p1 - f.u[0], o1 = q1 - f.u[1], o2 = r1 - f.u[2];
-                            a0 += o0; a1 += o1; a2 += o2;
-                            ae += o0 * o0 + o1 * o1 + o2 * o2;
-                            b0 += C1[0]; b1 += C1[1]; b2 += C1[2];
-                            be += C1[0] * C1[0] + C1[1] * C1[1] + C1[2] * C1[2];
-                            nr += 1.0f;
-                        }
-                        S.v0[j1] = C1[0]; S.v1[j1] = C1[1]; S.v2[j1] = C1[2];
-                    }
+                    S.v0[j1] = C1[0]; S.v1[j1] = C1[1]; S.v2[j1] = C1[2];
                 }
             }
-            S.sel[j0] = s0;
-            if (has1) S.sel[j1] = s1;
         }
-        __syncwarp();
-        return m;
-    };
+        S.sel[j0] = s0;
+        if (has1) S.sel[j1] = s1;
+    }
+    __syncwarp();
+}
 
-    uint32_t m_last = 0;
-    for (uint32_t ch = 0; ch < nch; ++ch) m_last = stage_chunk(ch, true);
+// conservation factors of the cell from the warp's partial sums
+__device__ __forceinline__ G2Cons g2_factors(const float* prm, G2Sums R, bool relax, G2Acc& acc) {
+    G2Cons K;
+    K.apply = false;
+    K.uo0 = K.uo1 = K.uo2 = K.mn0 = K.mn1 = K.mn2 = 0.0f;
+    K.alpha = 1.0f;
+    if (!relax) return K;
+    const float nr = warp_sumf(R.nr);
+    if (nr < 2.0f) return K;
+    const float a0 = warp_sumf(R.a0), a1 = warp_sumf(R.a1), a2 = warp_sumf(R.a2), ae = warp_sumf(R.ae);
+    const float b0 = warp_sumf(R.b0), b1 = warp_sumf(R.b1), b2 = warp_sumf(R.b2), be = warp_sumf(R.be);
+    // FP32: the sums are taken about the cell mean, so the differences
+    // below do not cancel.  The butterfly sums are bitwise the same on
+    // every lane (each stage adds the same two values), so every lane
+    // computes the same factors without a broadcast.
+    const float inv = 1.0f / nr;
+    const float Eo = ae - (a0 * a0 + a1 * a1 + a2 * a2) * inv;
+    const float En = be - (b0 * b0 + b1 * b1 + b2 * b2) * inv;
+    if (En > 0.0f && Eo >= 0.0f) {
+        K.apply = true;
+        K.alpha = sqrtf(Eo / En);
+        K.uo0 = prm[0] + a0 * inv;
+        K.uo1 = prm[1] + a1 * inv;
+        K.uo2 = prm[2] + a2 * inv;
+        K.mn0 = b0 * inv;
+        K.mn1 = b1 * inv;
+        K.mn2 = b2 * inv;
+        acc.relaxed += (unsigned long long)(unsigned)nr;
+    }
+    return K;
+}
 
-    // conservation factors of the cell
-    bool apply = false;
-    float uo0 = 0, uo1 = 0, uo2 = 0, mn0 = 0, mn1 = 0, mn2 = 0, alpha = 1;
-    if (relax) {
-        nr = warp_sumf(nr);
-        if (nr >= 2.0f) {
-            a0 = warp_sumf(a0); a1 = warp_sumf(a1); a2 = warp_sumf(a2); ae = warp_sumf(ae);
-            b0 = warp_sumf(b0); b1 = warp_sumf(b1); b2 = warp_sumf(b2); be = warp_sumf(be);
-            // FP32: the sums are taken about the cell mean, so the differences
-            // below do not cancel.  The butterfly sums are bitwise the same on
-            // every lane (each stage adds the same two values), so every lane
-            // computes the same factors without a broadcast.
-            const float inv = 1.0f / nr;
-            const float Eo = ae - (a0 * a0 + a1 * a1 + a2 * a2) * inv;
-            const float En = be - (b0 * b0 + b1 * b1 + b2 * b2) * inv;
-            if (En > 0.0f && Eo >= 0.0f) {
-                apply = true;
-                alpha = sqrtf(Eo / En);
-                uo0 = f.u[0] + a0 * inv;
-                uo1 = f.u[1] + a1 * inv;
-                uo2 = f.u[2] + a2 * inv;
-                mn0 = b0 * inv;
-                mn1 = b1 * inv;
-                mn2 = b2 * inv;
-                if (lane == 0) atomicAdd(&s.dyn->counters[kCntRelaxed], (unsigned long long)(unsigned)nr);
-            }
+// the relaxed velocity of staged particle j (conservation applied), or its
+// old velocity when the cell had a single relaxed particle (reverted)
+template <int DIM>
+__device__ __forceinline__ void g2_velocity(const SimDev& s, const G2Stage& S, const G2Cons& K, int p, uint32_t base,
+                                            uint32_t nb, const uint32_t* spl, uint32_t off, uint32_t j, float* c) {
+    c[0] = S.v0[j];
+    c[1] = S.v1[j];
+    c[2] = S.v2[j];
+    if (S.sel[j]) {
+        if (K.apply) {
+            c[0] = K.uo0 + K.alpha * (c[0] - K.mn0);
+            c[1] = K.uo1 + K.alpha * (c[1] - K.mn1);
+            c[2] = K.uo2 + K.alpha * (c[2] - K.mn2);
+        } else {
+            float ox, oy;
+            uint32_t oid;
+            load_particle<DIM>(s, p, base, nb, spl, off + j, ox, oy, c[0], c[1], c[2], oid);
         }
     }
+}
 
-    // the relaxed velocity of staged particle j (conservation applied), or
-    // its old velocity when the cell had a single relaxed particle
-    auto final_velocity = [&](uint32_t off, uint32_t j, float* c) {
-        c[0] = S.v0[j];
-        c[1] = S.v1[j];
-        c[2] = S.v2[j];
-        if (S.sel[j]) {
-            if (apply) {
-                c[0] = uo0 + alpha * (c[0] - mn0);
-                c[1] = uo1 + alpha * (c[1] - mn1);
-                c[2] = uo2 + alpha * (c[2] - mn2);
-            } else {
-                float ox, oy;
-                uint32_t oid;
-                load_particle<DIM>(s, p, base, nb, spl, off + j, ox, oy, c[0], c[1], c[2], oid);
-            }
-        }
-    };
-
-    if (MODE == kRelaxOnly) {
-        for (uint32_t ch = 0; ch < nch; ++ch) {
-            const uint32_t m = nch > 1 ? stage_chunk(ch, false) : m_last;
-            const uint32_t off = ch * CAP;
+// relaxed velocities written back in place (MODE kRelaxOnly)
+template <int DIM>
+__device__ __forceinline__ void g2_store_relaxed(const SimDev& s, const G2Stage& S, const G2Cons& K, int p,
+                                                 uint32_t base, uint32_t nb, const uint32_t* spl, uint32_t off,
+                                                 uint32_t cnt, int lane) {
+    if (!K.apply) return;
 #pragma unroll 1
-            for (uint32_t j = lane; j < m; j += 32) {
-                if (!(S.sel[j] && apply)) continue;
-                float c[3];
-                final_velocity(off, j, c);
-                store_velocity<DIM>(s, p, base, nb, spl, off + j, c[0], c[1], c[2]);
-            }
-        }
-        __syncwarp();
-        return;
+    for (uint32_t j = lane; j < cnt; j += 32) {
+        if (!S.sel[j]) continue;
+        float c[3];
+        g2_velocity<DIM>(s, S, K, p, base, nb, spl, off, j, c);
+        store_velocity<DIM>(s, p, base, nb, spl, off + j, c[0], c[1], c[2]);
     }
+    __syncwarp();
+}
 
+// passes A, B and the write pass over the staged particles [0, cnt)
+template <int DIM, int MODE>
+__device__ __forceinline__ void g2_move(const SimDev* __restrict__ sims, const SimDev& s, const G2Stage& S,
+                                        const G2Cons& K, int cell, int p, uint32_t base, uint32_t nb,
+                                        const uint32_t* spl, uint32_t off, uint32_t cnt, uint32_t step,
+                                        uint32_t* win, int lane, uint32_t& removed) {
+    const int q = p ^ 1;
     Ctx C;
     make_ctx(s, q, C);
     const int cy = DIM == 2 ? cell / C.nx : 0;
     const int cx = DIM == 2 ? cell - cy * C.nx : 0;
-    uint32_t* wcnt = win;              // arrivals per window slot, then the running rank
+    const int gcell = cell + (MODE == kFullSlab && DIM == 1 ? C.cell0 : 0);   // 1-D: global cell of the slab's cell
+    const int row0 = MODE == kFullSlab && DIM == 2 ? s.row0 : 0;
+    uint32_t* wcnt = win;              // arrivals per window slot
     uint32_t* wstart = win + kWin;     // first reserved index of each slot in its bucket
     uint32_t* wend = win + 2 * kWin;   // end of that bucket
-    uint32_t* woff = win + 3 * kWin;   // offset of the slot in the slot-ordered list
-    for (uint32_t ch = 0; ch < nch; ++ch) {
-        const uint32_t m = nch > 1 ? stage_chunk(ch, false) : m_last;
-        const uint32_t off = ch * CAP;
-        for (int k = lane; k < kWin; k += 32) wcnt[k] = 0;
-        __syncwarp();
-        // pass A: conservation, advection, destination slot; count per slot
+    wcnt[lane] = 0;
+    wcnt[lane + 32] = 0;
+    __syncwarp();
+    // pass A: conservation, advection, destination slot, rank in the slot
 #pragma unroll 1
-        for (uint32_t b = 0; b < m; b += 32) {
-            const uint32_t j = b + lane;
-            int slot = -2;   // -2: nothing to count
-            if (j < m) {
-                float x = DIM == 2 ? S.x[j] : 0.0f, y = S.y[j], c[3];
-                final_velocity(off, j, c);
-                unsigned char ws = kSlotNone;
-                if (advect_fast<DIM>(s, C, step, S.id[j], x, y, c)) {
-                    const int dc = cell_f<DIM>(C, x, y) - (MODE == kFullSlab ? C.cell0 : 0);   // local cell
-                    if (MODE == kFullSlab && (unsigned)dc >= (unsigned)C.K) {
-                        ws = kSlotOther;
-                    } else if (!C.reservoir || !in_buffer(s, dc)) {
-                        slot = win_slot<DIM>(dc, cell, cx, cy, C.nx);
-                        ws = slot >= 0 ? (unsigned char)slot : kSlotFar;
-                    } else {
-                        atomicAdd(&s.dyn->counters[kCntRemoved], 1ull);
-                    }
-                }
-                if ((MODE == kFullFlux || MODE == kFullSlab) && s.flux_axis)
-                    count_flux<float>(s, DIM == 2 ? S.x[j] : 0.0f, S.y[j], x, y);
-                if (DIM == 2) S.x[j] = x;
-                S.y[j] = y; S.v0[j] = c[0]; S.v1[j] = c[1]; S.v2[j] = c[2];
-                S.sel[j] = ws;
-            }
-            const unsigned grp = __match_any_sync(0xffffffffu, slot);
-            if (slot >= 0 && lane == __ffs(grp) - 1) wcnt[slot] += (uint32_t)__popc(grp);
-            __syncwarp();
-        }
-        // pass B: one reservation per occupied slot, all in flight together;
-        // the slot's first index, the end of its bucket and its offset in the
-        // slot-ordered list of the cell's particles go to shared memory
-        uint32_t tot_win = 0;
-        {
-            const uint32_t c0 = wcnt[lane], c1 = wcnt[lane + 32];
-            uint32_t x0 = c0, x1 = c1;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y0 = __shfl_up_sync(0xffffffffu, x0, o);
-                const uint32_t y1 = __shfl_up_sync(0xffffffffu, x1, o);
-                if (lane >= o) {
-                    x0 += y0;
-                    x1 += y1;
+    for (uint32_t b = 0; b < cnt; b += 32) {
+        const uint32_t j = b + lane;
+        int slot = -2;   // -2: nothing to count
+        if (j < cnt) {
+            float x = DIM == 2 ? S.x[j] : 0.0f, y = S.y[j], c[3];
+            g2_velocity<DIM>(s, S, K, p, base, nb, spl, off, j, c);
+            unsigned char ws = kSlotNone;
+            if (advect_fast<DIM>(s, C, step, S.id[j], x, y, c)) {
+                int ix, iy;
+                cell_xy<DIM>(C, x, y, ix, iy);
+                const int dc = (DIM == 2 ? iy * C.nx + ix : iy) - (MODE == kFullSlab ? C.cell0 : 0);   // local
+                if (MODE == kFullSlab && (unsigned)dc >= (unsigned)C.K) {
+                    ws = kSlotOther;
+                } else if (!C.reservoir || !in_buffer(s, dc)) {
+                    slot = win_slot_xy<DIM>(ix, iy - row0, gcell, cx, cy);
+                    ws = slot >= 0 ? (unsigned char)slot : kSlotFar;
+                } else {
+                    ++removed;
                 }
             }
-            const uint32_t t0 = __shfl_sync(0xffffffffu, x0, 31);
-            woff[lane] = x0 - c0;
-            woff[lane + 32] = t0 + x1 - c1;
-            tot_win = t0 + __shfl_sync(0xffffffffu, x1, 31);
+            if ((MODE == kFullFlux || MODE == kFullSlab) && s.flux_axis)
+                count_flux<float>(s, DIM == 2 ? S.x[j] : 0.0f, S.y[j], x, y);
+            if (DIM == 2) S.x[j] = x;
+            S.y[j] = y; S.v0[j] = c[0]; S.v1[j] = c[1]; S.v2[j] = c[2];
+            S.sel[j] = ws;
         }
-        for (int k = lane; k < kWin; k += 32) {
-            const uint32_t cnt = wcnt[k];
-            if (cnt) {
-                const int dest = win_cell<DIM>(k, cell, cx, cy, C.nx);
-                const uint32_t r = atomicAdd(&C.dcnt[dest], cnt);
-                wstart[k] = C.dlay[dest] + r;
-                wend[k] = min(C.dlay[dest + 1], C.cap);
+        const unsigned grp = __match_any_sync(0xffffffffu, slot);
+        if (slot >= 0) {
+            const int leader = __ffs(grp) - 1;
+            uint32_t r0 = 0;
+            if (lane == leader) {
+                r0 = wcnt[slot];
+                wcnt[slot] = r0 + (uint32_t)__popc(grp);
             }
-            wcnt[k] = 0;
-        }
-        __syncwarp();
-        // pass C: rank within the slot -> position in the slot-ordered list
-        // (particles leaving the window are written here, one by one)
-#pragma unroll 1
-        for (uint32_t b = 0; b < m; b += 32) {
-            const uint32_t j = b + lane;
-            const unsigned char ws = j < m ? S.sel[j] : kSlotNone;
-            const unsigned grp = __match_any_sync(0xffffffffu, (unsigned)ws);
-            if (MODE == kFullSlab && ws == kSlotOther) {   // into the buckets of another slab
-                emit_other<DIM>(sims, s, q, DIM == 2 ? S.x[j] : 0.0f, S.y[j], S.v0[j], S.v1[j], S.v2[j], S.id[j]);
-            } else if (ws < kWin) {
-                const int leader = __ffs(grp) - 1;
-                uint32_t r0 = 0;
-                if (lane == leader) {
-                    r0 = wcnt[ws];
-                    wcnt[ws] = r0 + (uint32_t)__popc(grp);
-                }
-                const uint32_t rank = __shfl_sync(grp, r0, leader) + (uint32_t)__popc(grp & lanemask_lt());
-                perm[woff[ws] + rank] = (uint16_t)j;
-            } else if (ws == kSlotFar) {   // outside the window: a reservation of its own
-                const float x = DIM == 2 ? S.x[j] : 0.0f, y = S.y[j];
-                const int dc = cell_f<DIM>(C, x, y) - (MODE == kFullSlab ? C.cell0 : 0);
-                const uint32_t i = C.dlay[dc] + atomicAdd(&C.dcnt[dc], 1u);
-                const uint32_t hi = min(C.dlay[dc + 1], C.cap);
-                put_own<DIM>(s, C, q, i, hi, dc, x, y, S.v0[j], S.v1[j], S.v2[j], S.id[j]);
-            }
-            __syncwarp();
-        }
-        // pass D: the slot-ordered list written out, consecutive lanes to
-        // consecutive slots of the destination buckets
-#pragma unroll 1
-        for (uint32_t k = lane; k < tot_win; k += 32) {
-            const uint32_t j = perm[k];
-            const unsigned char ws = S.sel[j];
-            const uint32_t i = wstart[ws] + (k - woff[ws]);
-            const float x = DIM == 2 ? S.x[j] : 0.0f, y = S.y[j];
-            const int dc = i < wend[ws] ? 0 : cell_f<DIM>(C, x, y) - (MODE == kFullSlab ? C.cell0 : 0);
-            put_own<DIM>(s, C, q, i, wend[ws], dc, x, y, S.v0[j], S.v1[j], S.v2[j], S.id[j]);
+            r0 = __shfl_sync(grp, r0, leader);
+            S.rank[j] = (uint16_t)(r0 + (uint32_t)__popc(grp & lanemask_lt()));
         }
         __syncwarp();
     }
+    // pass B: one reservation per occupied slot, all in flight together
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int k = lane + 32 * h;
+        const uint32_t cntk = wcnt[k];
+        if (cntk) {
+            const int dest = win_cell<DIM>(k, cell, cx, cy, C.nx);
+            const uint32_t r = atomicAdd(&C.dcnt[dest], cntk);
+            wstart[k] = C.dlay[dest] + r;
+            wend[k] = min(C.dlay[dest + 1], C.cap);
+        }
+    }
     __syncwarp();
+    // write pass: consecutive lanes write particles of the same few
+    // destination buckets (a window slot's particles go to consecutive
+    // slots of its bucket, in rank order); particles leaving the window or
+    // the slab take their own reservation
+#pragma unroll 1
+    for (uint32_t j = lane; j < cnt; j += 32) {
+        const unsigned char ws = S.sel[j];
+        if (ws == kSlotNone) continue;
+        const float x = DIM == 2 ? S.x[j] : 0.0f, y = S.y[j];
+        if (ws < kWin) {
+            const uint32_t i = wstart[ws] + S.rank[j];
+            const uint32_t hi = wend[ws];
+            const int dc = i < hi ? 0 : cell_f<DIM>(C, x, y) - (MODE == kFullSlab ? C.cell0 : 0);
+            put_own<DIM>(s, C, q, i, hi, dc, x, y, S.v0[j], S.v1[j], S.v2[j], S.id[j]);
+        } else if (MODE == kFullSlab && ws == kSlotOther) {   // into the buckets of another slab
+            emit_other<DIM>(sims, s, q, x, y, S.v0[j], S.v1[j], S.v2[j], S.id[j]);
+        } else {   // outside the window: a reservation of its own
+            const int dc = cell_f<DIM>(C, x, y) - (MODE == kFullSlab ? C.cell0 : 0);
+            const uint32_t i = C.dlay[dc] + atomicAdd(&C.dcnt[dc], 1u);
+            const uint32_t hi = min(C.dlay[dc + 1], C.cap);
+            put_own<DIM>(s, C, q, i, hi, dc, x, y, S.v0[j], S.v1[j], S.v2[j], S.id[j]);
+        }
+    }
+    __syncwarp();
+}
+
+// a cell above the largest ring area: conservation sums in a first sweep
+// over its chunks, the update in a second sweep that reloads each chunk and
+// redraws the same counter-based random numbers
+template <int DIM, int MODE>
+__device__ __noinline__ void g2_cell_chunked(const SimDev* __restrict__ sims, const SimDev& s, const G2Desc& D,
+                                             const G2Stage& S, uint32_t n, bool relax, const uint32_t* spl,
+                                             uint32_t* win, int lane, G2Acc& acc) {
+    const int p = (D.flags & kDescParity) ? 1 : 0;
+    const uint32_t m = D.m, nch = (n + m - 1) / m;
+    G2Sums R = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (uint32_t ch = 0; ch < nch; ++ch) {
+        const uint32_t cnt = min(m, n - ch * m);
+        g2_load<DIM>(s, S, p, D.base, D.nb, spl, ch * m, cnt, false, lane);
+        g2_relax<true>(D.prm, s, S, cnt, D.step, relax, lane, R);
+    }
+    const G2Cons K = g2_factors(D.prm, R, relax, acc);
+    uint32_t removed = 0;
+    for (uint32_t ch = 0; ch < nch; ++ch) {
+        const uint32_t cnt = min(m, n - ch * m);
+        g2_load<DIM>(s, S, p, D.base, D.nb, spl, ch * m, cnt, false, lane);
+        g2_relax<false>(D.prm, s, S, cnt, D.step, relax, lane, R);
+        if (MODE == kRelaxOnly) g2_store_relaxed<DIM>(s, S, K, p, D.base, D.nb, spl, ch * m, cnt, lane);
+        else g2_move<DIM, MODE>(sims, s, S, K, D.cell, p, D.base, D.nb, spl, ch * m, cnt, D.step, win, lane, removed);
+    }
+    if (s.has_reservoir) acc.removed += __reduce_add_sync(0xffffffffu, removed);
+}
+
+template <int DIM, int MODE>
+__device__ __forceinline__ void g2_cell(const SimDev* __restrict__ sims, const SimDev& s, const G2Desc& D,
+                                        unsigned char* ring, uint32_t* win, uint32_t* spl, int lane, G2Acc& acc) {
+    const int p = (D.flags & kDescParity) ? 1 : 0;
+    uint32_t nsp = 0;
+    if (D.arrived > D.nb) nsp = collect_spill(s, p, D.cell, spl, lane);
+    const uint32_t n = D.nb + nsp;
+    if (n == 0) return;
+    const bool relax = (D.flags & kDescPending) && D.prm[14] != 0.0f;
+    if (MODE == kRelaxOnly && !relax) return;
+    const G2Stage S = g2_stage<DIM>(ring, D.off, D.m);
+    if (n > D.m) {
+        g2_cell_chunked<DIM, MODE>(sims, s, D, S, n, relax, spl, win, lane, acc);
+        return;
+    }
+    g2_load<DIM>(s, S, p, D.base, D.nb, spl, 0u, n, (D.flags & kDescBulk) != 0, lane);
+    G2Sums R = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    g2_relax<true>(D.prm, s, S, n, D.step, relax, lane, R);
+    const G2Cons K = g2_factors(D.prm, R, relax, acc);
+    if (MODE == kRelaxOnly) {
+        g2_store_relaxed<DIM>(s, S, K, p, D.base, D.nb, spl, 0u, n, lane);
+        return;
+    }
+    uint32_t removed = 0;
+    g2_move<DIM, MODE>(sims, s, S, K, D.cell, p, D.base, D.nb, spl, 0u, n, D.step, win, lane, removed);
+    if (s.has_reservoir) acc.removed += __reduce_add_sync(0xffffffffu, removed);
 }
 
 // copy one simulation descriptor into shared memory (one warp)
@@ -802,13 +930,8 @@ __device__ __forceinline__ void load_sim_warp(SimDev& dst, const SimDev& src, in
     for (int i = lane; i < (int)(sizeof(SimDev) / 16); i += 32) b[i] = a[i];
 }
 
-// Cells are handed out one at a time from per-simulation queues
-// (SimDyn::qnext): each warp starts on a home simulation and takes its next
-// cell from it, so its descriptor stays in shared memory and neighbouring
-// cells are processed together; when the home simulation runs out, the warp
-// looks for one with cells left (32 candidates per round).  The next cell is
-// requested while the current one is processed.  wq[0] counts the warps that
-// left; the last one resets every queue for the next launch.
+// next simulation with cells left in its queue, after `from` (32 candidates
+// per round); -1 when every queue of this dimension is empty
 template <int DIM>
 __device__ __forceinline__ int find_sim(const SimDev* __restrict__ sims, int nsims, int from, int lane) {
     for (int base = 0; base < nsims; base += 32) {
@@ -827,24 +950,71 @@ __device__ __forceinline__ int find_sim(const SimDev* __restrict__ sims, int nsi
     return -1;
 }
 
-template <int CAP, int DIM, int MODE>
-__global__ void __launch_bounds__(128, 4) k_g2(const SimDev* __restrict__ sims, int nsims, uint32_t* __restrict__ wq) {
-    extern __shared__ __align__(16) unsigned char g2_smem[];
-    __shared__ SimDev sim_w[4];
-    __shared__ uint32_t spl_all[4][32];
-    __shared__ uint32_t win_all[4][4 * kWin];
-    __shared__ uint16_t perm_all[4][kCapMax];
-    __shared__ Hdr hdr_all[4];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const Stage S = stage_of<CAP, DIM>(g2_smem, warp);
-    const uint32_t nwarps = gridDim.x * (blockDim.x / 32);
-    SimDev& s = sim_w[warp];
-    int h = (int)((blockIdx.x * (blockDim.x / 32) + warp) % (unsigned)nsims);
+// shared state of one CTA of k_g2
+template <int NC>
+struct G2Shared {
+    SimDev sim[2];                 // simulation descriptors in use (the producer alternates)
+    G2Desc desc[kG2Desc];
+    uint64_t full[kG2Desc];        // copies of a descriptor landed (producer arrive + bytes)
+    uint64_t empty[kG2Desc];       // consumer done with a descriptor
+    uint32_t win[NC][4 * kWin];
+    uint32_t spl[NC][32];
+    uint32_t take;                 // next descriptor for a consumer
+};
+
+// ---- producer --------------------------------------------------------------
+template <int DIM, int MODE, int NC>
+__device__ void g2_producer(const SimDev* __restrict__ sims, int nsims, G2Shared<NC>& sh, unsigned char* ring,
+                            uint32_t ring_bytes, uint32_t max_stage, int lane) {
+    constexpr uint32_t bpp = g2_bytes_per_particle<DIM>();
+    constexpr int NP = DIM == 2 ? 6 : 5;   // planes
+    uint32_t seq = 0, oldest = 0;          // descriptors issued / reclaimed
+    uint32_t head = 0, tail = 0;           // ring bytes allocated / freed (monotonic)
+    uint32_t last_use[2] = {0u, 0u};
+    bool used[2] = {false, false};
+    int ent = 1;
+    bool ok = true;
+
+    // reclaim the oldest descriptor once its consumer released it
+    auto reclaim = [&]() -> bool {
+        const uint32_t slot = oldest % kG2Desc;
+        if (!mbar_wait(&sh.empty[slot], (oldest / kG2Desc) & 1u)) return false;
+        tail = sh.desc[slot].end;
+        ++oldest;
+        return true;
+    };
+    // a free descriptor and `bytes` of contiguous ring; returns the ring offset
+    auto reserve = [&](uint32_t bytes, uint32_t& off) -> bool {
+        while (seq - oldest >= (uint32_t)kG2Desc)
+            if (!reclaim()) return false;
+        for (;;) {
+            const uint32_t pos = head % ring_bytes;
+            // an allocation never wraps: with no room before the end it starts at offset 0
+            const uint32_t start = pos + bytes > ring_bytes ? head + (ring_bytes - pos) : head;
+            if (start + bytes - tail <= ring_bytes) {
+                head = start;
+                off = start % ring_bytes;
+                return true;
+            }
+            if (oldest == seq) {   // empty ring: restart it at the chosen offset
+                head = tail = start;
+            } else if (!reclaim()) {
+                return false;
+            }
+        }
+    };
+
+    int h = (int)(blockIdx.x % (unsigned)nsims);
     if (sims[h].dim != DIM) h = find_sim<DIM>(sims, nsims, h, lane);
-    while (h >= 0) {
+    while (h >= 0 && ok) {
+        const int e = ent ^ 1;
+        if (used[e])
+            while (ok && oldest <= last_use[e]) ok = reclaim();
+        if (!ok) break;
         __syncwarp();
-        load_sim_warp(s, sims[h], lane);
+        load_sim_warp(sh.sim[e], sims[h], lane);
         __syncwarp();
+        const SimDev& s = sh.sim[e];
         const int p = s.dyn->cur;
         const uint32_t step = s.dyn->step;
         const bool pending = s.dyn->relax_pending != 0;
@@ -854,28 +1024,163 @@ __global__ void __launch_bounds__(128, 4) k_g2(const SimDev* __restrict__ sims, 
             h = find_sim<DIM>(sims, nsims, h, lane);
             continue;
         }
-        uint32_t c = 0;
-        if (lane == 0) c = atomicAdd(&s.dyn->qnext, 1u);
-        c = __shfl_sync(0xffffffffu, c, 0);
-        while (c < K) {
-            uint32_t cn = 0;   // the next cell, requested now
-            if (lane == 0) cn = atomicAdd(&s.dyn->qnext, 1u);
-            fetch_hdr(s, p, (int)c, hdr_all[warp], lane);
-            g2_cell<CAP, DIM, MODE>(sims, s, (int)c, hdr_all[warp], p, step, pending, spl_all[warp], S, win_all[warp],
-                                    perm_all[warp], lane);
-            c = __shfl_sync(0xffffffffu, cn, 0);
+        ent = e;
+        // bulk copies need 16-byte aligned planes (and buckets)
+        uintptr_t al = (uintptr_t)s.pos[p][1] | (uintptr_t)s.vel[p][0] | (uintptr_t)s.vel[p][1] |
+                       (uintptr_t)s.vel[p][2] | (uintptr_t)s.pid[p] | (uintptr_t)s.fprm;
+        if (DIM == 2) al |= (uintptr_t)s.pos[p][0];
+        const bool planes_aligned = (al & 15u) == 0;
+        const uint32_t flags0 = (pending ? kDescPending : 0u) | (p ? kDescParity : 0u);
+        const uint32_t cap = (uint32_t)s.cap;
+        for (;;) {
+            uint32_t c0 = 0;
+            if (lane == 0) c0 = atomicAdd(&s.dyn->qnext, (uint32_t)kG2Run);
+            c0 = __shfl_sync(0xffffffffu, c0, 0);
+            if (c0 >= K) break;
+            uint32_t lo = 0, hi = 0, ar = 0;
+            if (lane < kG2Run && c0 + lane < K) {
+                lo = s.lay[p][c0 + lane];
+                hi = min(s.lay[p][c0 + lane + 1], cap);
+                ar = s.cnt[p][c0 + lane];
+            }
+            const uint32_t nrun = min((uint32_t)kG2Run, K - c0);
+            for (uint32_t i = 0; i < nrun && ok; ++i) {
+                const uint32_t bs = __shfl_sync(0xffffffffu, lo, i);
+                const uint32_t tp = __shfl_sync(0xffffffffu, hi, i);
+                const uint32_t arv = __shfl_sync(0xffffffffu, ar, i);
+                const uint32_t capc = tp > bs ? tp - bs : 0u;
+                const uint32_t nb = min(arv, capc);
+                const bool spill = arv > nb;
+                if (nb == 0 && !spill) continue;
+                const uint32_t need = nb + (spill ? (uint32_t)kG2Spill : 0u);
+                const bool chunked = need > max_stage;
+                const uint32_t m = chunked ? max_stage : ((need + 3u) & ~3u);
+                const uint32_t bytes = (bpp * m + 15u) & ~15u;
+                const bool bulk = !chunked && planes_aligned && (bs & 3u) == 0 && nb > 0 &&
+                                  bs + ((nb + 3u) & ~3u) <= cap;
+                uint32_t off = 0;
+                if (!reserve(bytes, off)) {
+                    ok = false;
+                    break;
+                }
+                const uint32_t slot = seq % kG2Desc;
+                G2Desc& d = sh.desc[slot];
+                if (lane == 0) {
+                    d.base = bs;
+                    d.nb = nb;
+                    d.arrived = arv;
+                    d.off = off;
+                    d.m = m;
+                    d.cell = (int)(c0 + i);
+                    d.ent = e;
+                    d.step = step;
+                    d.flags = flags0 | (bulk ? kDescBulk : 0u);
+                    d.end = head + bytes;
+                    const uint32_t nb4 = (nb + 3u) & ~3u;
+                    mbar_arrive_tx(&sh.full[slot], 64u + (bulk ? (uint32_t)NP * 4u * nb4 : 0u));
+                    bulk_g2s(d.prm, s.fprm + (size_t)(c0 + i) * kNFPrm, 64u, &sh.full[slot]);
+                    if (bulk) {
+                        unsigned char* dst = ring + off;
+                        const uint32_t pb = 4u * m;   // bytes of one staged plane
+                        int k = 0;
+                        if (DIM == 2) bulk_g2s(dst + pb * k++, (const float*)s.pos[p][0] + bs, 4u * nb4, &sh.full[slot]);
+                        bulk_g2s(dst + pb * k++, (const float*)s.pos[p][1] + bs, 4u * nb4, &sh.full[slot]);
+                        bulk_g2s(dst + pb * k++, (const float*)s.vel[p][0] + bs, 4u * nb4, &sh.full[slot]);
+                        bulk_g2s(dst + pb * k++, (const float*)s.vel[p][1] + bs, 4u * nb4, &sh.full[slot]);
+                        bulk_g2s(dst + pb * k++, (const float*)s.vel[p][2] + bs, 4u * nb4, &sh.full[slot]);
+                        bulk_g2s(dst + pb * k, s.pid[p] + bs, 4u * nb4, &sh.full[slot]);
+                    }
+                }
+                __syncwarp();
+                head += bytes;
+                last_use[e] = seq;
+                used[e] = true;
+                ++seq;
+            }
         }
+        if (!ok) break;
         h = find_sim<DIM>(sims, nsims, h, lane);
     }
-    if (lane == 0) {
+    // one end marker per consumer (they take descriptors in order)
+    for (int k = 0; k < NC && ok; ++k) {
+        uint32_t off;
+        if (!reserve(0u, off)) {
+            ok = false;
+            break;
+        }
+        const uint32_t slot = seq % kG2Desc;
+        if (lane == 0) {
+            sh.desc[slot].cell = -1;
+            sh.desc[slot].end = head;
+            mbar_arrive(&sh.full[slot]);
+        }
+        __syncwarp();
+        ++seq;
+    }
+    if (!ok) {
+        if (lane == 0) g2_timeout(sims);
+        // copies still in flight land before the CTA may exit
+        for (uint32_t t = oldest; t < seq; ++t) mbar_wait(&sh.full[t % kG2Desc], (t / kG2Desc) & 1u);
+    }
+}
+
+template <int DIM, int MODE, int NC>
+__global__ void __launch_bounds__(32 * (NC + 1), 16 / (NC + 1)) k_g2(const SimDev* __restrict__ sims, int nsims,
+                                                     uint32_t* __restrict__ wq, uint32_t ring_bytes,
+                                                     uint32_t max_stage) {
+    extern __shared__ __align__(128) unsigned char g2_ring[];
+    __shared__ G2Shared<NC> sh;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kG2Desc; ++i) {
+            mbar_init(&sh.full[i], 1);
+            mbar_init(&sh.empty[i], 1);
+        }
+        sh.take = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (warp == 0) {
+        g2_producer<DIM, MODE, NC>(sims, nsims, sh, g2_ring, ring_bytes, max_stage, lane);
+    } else {
+        uint32_t* win = sh.win[warp - 1];
+        uint32_t* spl = sh.spl[warp - 1];
+        G2Acc acc = {0ull, 0ull};
+        SimDyn* acc_dyn = nullptr;
+        for (;;) {
+            uint32_t my = 0;
+            if (lane == 0) my = atomicAdd(&sh.take, 1u);
+            my = __shfl_sync(0xffffffffu, my, 0);
+            const uint32_t slot = my % kG2Desc;
+            if (!mbar_wait(&sh.full[slot], (my / kG2Desc) & 1u)) {
+                if (lane == 0) g2_timeout(sims);
+                break;
+            }
+            const G2Desc& D = sh.desc[slot];
+            if (D.cell < 0) break;
+            const SimDev& s = sh.sim[D.ent];
+            if (s.dyn != acc_dyn) {
+                g2_flush(acc, acc_dyn, lane);
+                acc_dyn = s.dyn;
+            }
+            g2_cell<DIM, MODE>(sims, s, D, g2_ring, win, spl, lane, acc);
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sh.empty[slot]);
+        }
+        g2_flush(acc, acc_dyn, lane);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
         __threadfence();
         const uint32_t done = atomicAdd(&wq[0], 1u);
-        if (done == nwarps - 1) {
+        if (done == gridDim.x - 1) {   // the last CTA resets the queues for the next launch
             wq[0] = 0;
             for (int i = 0; i < nsims; ++i) sims[i].dyn->qnext = 0;
         }
     }
 }
+
 
 // ---------------------------------------------------------------------------
 // k_g1: per-cell moments (Eq. 1) in one pass, as sums of C = c - u_s about a
@@ -1295,7 +1600,9 @@ __device__ __forceinline__ uint32_t bucket_size(const SimDev& s, const uint32_t*
             m = max(m, cnt[jy * s.nx + jx]);
         }
     }
-    return m + (m >> 2) + 16u + (s.has_reservoir ? s.inj_count[c] : 0u);
+    // a multiple of four slots, so that every bucket starts on a 16-byte
+    // boundary (the bulk copies of k_g2 need it)
+    return (m + (m >> 2) + 16u + (s.has_reservoir ? s.inj_count[c] : 0u) + 3u) & ~3u;
 }
 
 template <bool SETUP>
@@ -1343,15 +1650,17 @@ __global__ void __launch_bounds__(1024) k_layout(const SimDev* __restrict__ sims
         // bucket sizes with slack when they fit, else the exact demand plus an even share of what is left
         const unsigned long long demand = tot_exact + (s.has_reservoir ? s.inj_total : 0u);
         const bool full = tot_full <= (unsigned long long)s.cap;
-        const uint32_t extra = (!full && demand < (unsigned long long)s.cap)
-                                   ? (uint32_t)(((unsigned long long)s.cap - demand) / (unsigned long long)K)
+        // (each bucket rounded up to a multiple of four: up to 3 K more slots)
+        const unsigned long long room = demand + 3ull * (unsigned long long)K;
+        const uint32_t extra = (!full && room < (unsigned long long)s.cap)
+                                   ? (uint32_t)(((unsigned long long)s.cap - room) / (unsigned long long)K)
                                    : 0u;
         if (!full && demand > (unsigned long long)s.cap && threadIdx.x == 0)
             atomicAdd(&dyn->counters[kCntOverflow], 1ull);
         for (int base = 0; base < K; base += blockDim.x) {
             const int c = base + threadIdx.x;
             uint32_t v = 0;
-            if (c < K) v = full ? bucket_size(s, C, c) : C[c] + (s.has_reservoir ? s.inj_count[c] : 0u) + extra;
+            if (c < K) v = full ? bucket_size(s, C, c) : (C[c] + (s.has_reservoir ? s.inj_count[c] : 0u) + extra + 3u) & ~3u;
             uint32_t x = v;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -1408,49 +1717,80 @@ __global__ void k_clear_pending(const SimDev* __restrict__ sims, int nsims) {
         sims[si].dyn->relax_pending = 0;
 }
 
-// one wave of resident blocks: late blocks would only find empty queues
-template <int CAP, int DIM, int MODE>
-int g2_grid(int smem) {
-    static int grid = 0;
-    if (!grid) {
-        int dev = 0, sms = 152, per = 0;
+// ---------------------------------------------------------------------------
+// k_g2 launch configuration: NC consumer warps per CTA, 16 / (NC + 1) CTAs
+// per SM sharing its shared memory, the rest of which is each CTA's ring
+// ---------------------------------------------------------------------------
+struct G2Config {
+    int grid;
+    uint32_t ring, max_stage;
+};
+
+template <int DIM, int MODE, int NC>
+const G2Config& g2_config() {
+    static G2Config cfg = {0, 0u, 0u};
+    if (!cfg.grid) {
+        int dev = 0, sms = 152, optin = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_g2<CAP, DIM, MODE>, 128, smem);
-        grid = sms * (per > 0 ? per : 1);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        cudaFuncAttributes fa;
+        cudaFuncGetAttributes(&fa, k_g2<DIM, MODE, NC>);
+        const int ctas = 16 / (NC + 1);
+        int ring = std::min(per_sm / ctas - 1024, optin) - (int)fa.sharedSizeBytes;
+        ring &= ~1023;
+        int per = 0;
+        for (; ring >= 16384; ring -= 4096) {
+            cudaFuncSetAttribute(k_g2<DIM, MODE, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, ring);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_g2<DIM, MODE, NC>, 32 * (NC + 1), ring);
+            if (per >= ctas) break;
+        }
+        constexpr uint32_t bpp = g2_bytes_per_particle<DIM>();
+        cfg.ring = (uint32_t)ring;
+        cfg.max_stage = std::min(1024u, ((uint32_t)ring / (2u * bpp)) & ~3u);
+        cfg.grid = sms * std::max(per, 1);
     }
-    return grid;
+    return cfg;
 }
 
-template <int CAP, int DIM, int MODE>
+template <int DIM, int MODE, int NC>
 void launch_g2_one(const Launch& L) {
-    const int smem = 4 * stage_bytes<CAP, DIM>();
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_g2<CAP, DIM, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        attr = true;
-    }
-    k_g2<CAP, DIM, MODE><<<g2_grid<CAP, DIM, MODE>(smem), 128, smem, L.stream>>>(L.sims, L.nsims, L.wq);
+    const G2Config& c = g2_config<DIM, MODE, NC>();
+    k_g2<DIM, MODE, NC><<<c.grid, 32 * (NC + 1), c.ring, L.stream>>>(L.sims, L.nsims, L.wq, c.ring, c.max_stage);
 }
 
-template <int CAP, int MODE>
+template <int MODE, int NC>
 void launch_g2(const Launch& L) {
-    if (L.dims & 1) launch_g2_one<CAP, 1, MODE>(L);
-    if (L.dims & 2) launch_g2_one<CAP, 2, MODE>(L);
+    if (L.dims & 1) launch_g2_one<1, MODE, NC>(L);
+    if (L.dims & 2) launch_g2_one<2, MODE, NC>(L);
+}
+
+// R (tuning): 4, 8, 12 select 3, 7 or 15 consumer warps per CTA
+template <int MODE>
+void launch_g2_R(const Launch& L, int R) {
+    if (R <= 4) launch_g2<MODE, 3>(L);
+    else if (R <= 8) launch_g2<MODE, 7>(L);
+    else launch_g2<MODE, 15>(L);
+}
+
+template <int MODE, int NC>
+void prepare_g2() {
+    g2_config<1, MODE, NC>();
+    g2_config<2, MODE, NC>();
+}
+
+template <int MODE>
+void prepare_g2_all() {
+    prepare_g2<MODE, 3>();
+    prepare_g2<MODE, 7>();
+    prepare_g2<MODE, 15>();
 }
 
 }  // namespace
 
 void launch_fused_setup(const Launch& L) { k_layout<true><<<L.nsims, 1024, 0, L.stream>>>(L.sims, L.nsims); }
 
-template <int MODE>
-void launch_g2_R(const Launch& L, int R) {
-    if (R <= 4) launch_g2<128, MODE>(L);
-    else if (R <= 8) launch_g2<256, MODE>(L);
-    else launch_g2<kCapMax, MODE>(L);
-}
-
-// R: particles per lane of the largest expected cell (staging area of 32 R)
 void launch_fused_relax_stream(const Launch& L, int R, bool flush_only) {
     if (flush_only) {
         launch_g2_R<kRelaxOnly>(L, R);
@@ -1462,31 +1802,16 @@ void launch_fused_relax_stream(const Launch& L, int R, bool flush_only) {
     else launch_g2_R<kFull>(L, R);
 }
 
-// set the shared-memory limits of the staged kernels once, outside any capture
-template <int CAP, int MODE>
-void set_g2_smem() {
-    cudaFuncSetAttribute(k_g2<CAP, 1, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<CAP, 1>());
-    cudaFuncSetAttribute(k_g2<CAP, 2, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * stage_bytes<CAP, 2>());
-    g2_grid<CAP, 1, MODE>(4 * stage_bytes<CAP, 1>());
-    g2_grid<CAP, 2, MODE>(4 * stage_bytes<CAP, 2>());
-}
-
+// shared-memory limits and grids of the pipelined kernel, set once outside
+// any stream capture
 void fused_prepare_attributes() {
     static bool done = false;
     if (done) return;
     done = true;
-    set_g2_smem<128, kFull>();
-    set_g2_smem<256, kFull>();
-    set_g2_smem<kCapMax, kFull>();
-    set_g2_smem<128, kRelaxOnly>();
-    set_g2_smem<256, kRelaxOnly>();
-    set_g2_smem<kCapMax, kRelaxOnly>();
-    set_g2_smem<128, kFullSlab>();
-    set_g2_smem<256, kFullSlab>();
-    set_g2_smem<kCapMax, kFullSlab>();
-    set_g2_smem<128, kFullFlux>();
-    set_g2_smem<256, kFullFlux>();
-    set_g2_smem<kCapMax, kFullFlux>();
+    prepare_g2_all<kFull>();
+    prepare_g2_all<kRelaxOnly>();
+    prepare_g2_all<kFullSlab>();
+    prepare_g2_all<kFullFlux>();
     cudaGetLastError();
 }
 
