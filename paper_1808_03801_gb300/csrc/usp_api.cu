@@ -83,6 +83,7 @@ struct usp_batch {
     int nptiles = 0, nctiles = 0;
     Graphs graphs;
     int graph_nsims = -1;             // nsims the graphs were captured with
+    int lay_tiles = 1;                // layout tiles of the largest member seen (grid of the layout kernels)
     bool dirty = true;
     int precision = -1, pipeline = -1;
     std::string err;
@@ -154,6 +155,7 @@ static Launch make_launch(usp_handle* h) {
     L.flux = h->host.flux_axis != 0;
     L.grid_p = persistent_grid(h->nptiles, h->grid_per_sm);
     L.grid_c = persistent_grid(h->nctiles, h->grid_per_sm);
+    L.lay_tiles = (h->host.K + kLayTile - 1) / kLayTile;
     L.stream = h->stream;
     return L;
 }
@@ -393,6 +395,7 @@ extern "C" int usp_create(const usp_gas* gas, const usp_grid* grid, const usp_bc
         CALLOC(floc, float, 4 * (size_t)K);
         for (int b = 0; b < 2; ++b) {
             CALLOC(lay[b], uint32_t, K + 1);
+            if (b == 0) { CALLOC(lay_part, unsigned long long, 3 * (size_t)((K + kLayTile - 1) / kLayTile) + 2); }
             CALLOC(cnt[b], uint32_t, K);
             CALLOC(sp_pos[b][0], float, kSpillCap);
             CALLOC(sp_pos[b][1], float, kSpillCap);
@@ -1147,6 +1150,13 @@ static int batch_rebuild(usp_batch* b) {
         regraph = true;
     }
     if ((int)sims.size() != b->graph_nsims) regraph = true;
+    for (auto* h : b->members) {
+        const int t = (h->host.K + kLayTile - 1) / kLayTile;
+        if (t > b->lay_tiles) {   // the layout grid only grows: extra blocks find no tile
+            b->lay_tiles = t;
+            regraph = true;
+        }
+    }
     b->nptiles = (int)pt.size();
     b->nctiles = (int)ct.size();
     int nt[2] = {b->nptiles, b->nctiles};
@@ -1183,6 +1193,7 @@ static Launch batch_launch(usp_batch* b) {
     for (auto* h : b->members) per_sm = std::max(per_sm, h->grid_per_sm);
     L.grid_p = persistent_grid(1 << 30, per_sm);
     L.grid_c = persistent_grid(1 << 30, per_sm);
+    L.lay_tiles = b->lay_tiles;
     L.stream = b->stream;
     return L;
 }

@@ -1709,6 +1709,178 @@ __global__ void __launch_bounds__(1024) k_layout(const SimDev* __restrict__ sims
     }
 }
 
+// ---------------------------------------------------------------------------
+// Per-step layout of the next write, over tiles of kLayTile cells so that a
+// large domain is laid out by many blocks at once:
+//   k_lay_sum   per tile: sums of the bucket sizes with slack (bucket_size),
+//               of the counts rounded up to four slots (tight) and of the
+//               exact counts;
+//   k_lay_scan  per simulation: the choice between slack and tight buckets
+//               (tight ones get an even share of the spare slots, a multiple
+//               of four), the exclusive scan of the tile sums into tile
+//               offsets, the totals, and the end of the step;
+//   k_lay_put   per tile: the bucket offsets of its cells and cleared counts.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t tight_size(const SimDev& s, const uint32_t* C, int c) {
+    return (C[c] + (s.has_reservoir ? s.inj_count[c] : 0u) + 3u) & ~3u;
+}
+
+// sum over a block of 1024 threads (every thread gets the total)
+__device__ __forceinline__ unsigned long long block_sum_1024(unsigned long long v, unsigned long long* sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    v = threadIdx.x < 32 ? sh[threadIdx.x] : 0ull;
+    if (threadIdx.x < 32) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) sh[32] = v;
+    }
+    __syncthreads();
+    return sh[32];
+}
+
+// exclusive scan over a block of 1024 threads; *total receives the sum
+__device__ __forceinline__ unsigned long long block_scan_1024(unsigned long long v, unsigned long long* sh,
+                                                              unsigned long long* total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    __syncthreads();
+    if (lane == 31) sh[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        unsigned long long t = sh[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        sh[lane] = t;   // inclusive warp totals
+    }
+    __syncthreads();
+    *total = sh[31];
+    return (w ? sh[w - 1] : 0ull) + x - v;
+}
+
+__global__ void __launch_bounds__(kLayTile) k_lay_sum(const SimDev* __restrict__ sims) {
+    __shared__ unsigned long long sh[33];
+    const SimDev& s = sims[blockIdx.y];
+    const int K = s.K;
+    const int T = (K + kLayTile - 1) / kLayTile;
+    const int src = s.dyn->cur ^ 1;   // counts of the buffer this step wrote
+    const uint32_t* C = s.cnt[src];
+    for (int t = blockIdx.x; t < T; t += gridDim.x) {
+        const int c = t * kLayTile + threadIdx.x;
+        unsigned long long f = 0, g = 0, e = 0;
+        if (c < K) {
+            f = bucket_size(s, C, c);
+            g = tight_size(s, C, c);
+            e = C[c];
+        }
+        f = block_sum_1024(f, sh);
+        g = block_sum_1024(g, sh);
+        e = block_sum_1024(e, sh);
+        if (threadIdx.x == 0) {
+            s.lay_part[3 * t] = f;
+            s.lay_part[3 * t + 1] = g;
+            s.lay_part[3 * t + 2] = e;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kLayTile) k_lay_scan(const SimDev* __restrict__ sims, int nsims) {
+    __shared__ unsigned long long sh[33];
+    __shared__ unsigned long long carry;
+    for (int si = blockIdx.x; si < nsims; si += gridDim.x) {
+        const SimDev& s = sims[si];
+        SimDyn* dyn = s.dyn;
+        const int K = s.K;
+        const int T = (K + kLayTile - 1) / kLayTile;
+        const int cur = dyn->cur;
+        unsigned long long P = 0, G = 0, E = 0;
+        for (int t = threadIdx.x; t < T; t += blockDim.x) {
+            P += s.lay_part[3 * t];
+            G += s.lay_part[3 * t + 1];
+            E += s.lay_part[3 * t + 2];
+        }
+        const unsigned long long tot_full = block_sum_1024(P, sh);
+        const unsigned long long tot_tight = block_sum_1024(G, sh);
+        const unsigned long long tot_exact = block_sum_1024(E, sh);
+        const unsigned long long cap = (unsigned long long)s.cap;
+        const bool full = tot_full <= cap;
+        const unsigned long long extra =
+            (!full && tot_tight < cap) ? ((cap - tot_tight) / (unsigned long long)K) & ~3ull : 0ull;
+        const unsigned long long demand = tot_exact + (s.has_reservoir ? s.inj_total : 0u);
+        if (threadIdx.x == 0) {
+            carry = 0;
+            if (!full && demand > cap) atomicAdd(&dyn->counters[kCntOverflow], 1ull);
+        }
+        __syncthreads();
+        for (int base = 0; base < T; base += blockDim.x) {
+            const int t = base + threadIdx.x;
+            unsigned long long v = 0;
+            if (t < T) {
+                const int cells = min(kLayTile, K - t * kLayTile);
+                v = full ? s.lay_part[3 * t] : s.lay_part[3 * t + 1] + extra * (unsigned long long)cells;
+            }
+            unsigned long long tot;
+            const unsigned long long x = block_scan_1024(v, sh, &tot);
+            if (t < T) s.lay_part[3 * t] = carry + x;   // tile offset
+            __syncthreads();
+            if (threadIdx.x == 0) carry += tot;
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            s.lay_part[3 * T] = full ? 1ull : 0ull;
+            s.lay_part[3 * T + 1] = extra;
+            s.lay[cur][K] = (uint32_t)min(carry, 0xFFFFFFFFull);
+            dyn->n = (uint32_t)min(tot_exact, 0xFFFFFFFFull);
+            dyn->sp_n[cur] = 0;
+            dyn->lay_dst = (uint32_t)cur;
+            // end of the step
+            if (s.has_reservoir) {
+                dyn->next_pid += s.inj_total;
+                dyn->counters[kCntInjected] += s.inj_total;
+            }
+            dyn->cur = cur ^ 1;
+            dyn->step += 1;
+            dyn->nsamples += 1;
+            dyn->relax_pending = 1;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kLayTile) k_lay_put(const SimDev* __restrict__ sims) {
+    __shared__ unsigned long long sh[33];
+    const SimDev& s = sims[blockIdx.y];
+    const int K = s.K;
+    const int T = (K + kLayTile - 1) / kLayTile;
+    const int dst = (int)s.dyn->lay_dst;
+    const uint32_t* C = s.cnt[dst ^ 1];
+    const bool full = s.lay_part[3 * T] != 0;
+    const uint32_t extra = (uint32_t)s.lay_part[3 * T + 1];
+    for (int t = blockIdx.x; t < T; t += gridDim.x) {
+        const int c = t * kLayTile + threadIdx.x;
+        unsigned long long v = 0;
+        if (c < K) v = full ? bucket_size(s, C, c) : tight_size(s, C, c) + extra;
+        unsigned long long tot;
+        const unsigned long long x = block_scan_1024(v, sh, &tot);
+        if (c < K) {
+            s.lay[dst][c] = (uint32_t)min(s.lay_part[3 * t] + x, 0xFFFFFFFFull);
+            s.cnt[dst][c] = 0;
+        }
+        __syncthreads();
+    }
+}
+
 // end of a fused step (mode 0) or after a flush of the pending relaxation (mode 1)
 // clears the pending relaxation once it has been applied in place before a
 // read-back (the end of a step is part of k_layout)
@@ -1827,7 +1999,12 @@ void launch_fused_moments(const Launch& L, int R) {
 
 void launch_fused_params(const Launch& L) { k_params_f<<<L.grid_c, 32, 0, L.stream>>>(L.sims, L.ctiles, L.nctiles); }
 
-void launch_fused_layout(const Launch& L) { k_layout<false><<<L.nsims, 1024, 0, L.stream>>>(L.sims, L.nsims); }
+void launch_fused_layout(const Launch& L) {
+    const dim3 grid((unsigned)std::min(L.lay_tiles, 1024), (unsigned)L.nsims);
+    k_lay_sum<<<grid, kLayTile, 0, L.stream>>>(L.sims);
+    k_lay_scan<<<L.nsims, kLayTile, 0, L.stream>>>(L.sims, L.nsims);
+    k_lay_put<<<grid, kLayTile, 0, L.stream>>>(L.sims);
+}
 
 
 }  // namespace usp

@@ -49,7 +49,7 @@ struct SimDyn {
     int relax_pending;  // fused pipeline: the relaxation of the last step is still to be applied
     uint32_t sp_n[2];   // fused pipeline: entries in the spill lists
     uint32_t qnext;     // fused pipeline: next cell handed out by k_g2 (zero between launches)
-    uint32_t qpad;
+    uint32_t lay_dst;   // fused pipeline: buffer whose bucket layout the layout kernels build
     unsigned long long counters[8];
 };
 
@@ -105,6 +105,7 @@ struct alignas(16) SimDev {
     // fused pipeline (FP32 storage): slack-bucket layout per buffer parity
     uint32_t* lay[2];     // K + 1 bucket offsets of buffer b
     uint32_t* cnt[2];     // K arrivals into buffer b (bucket + spilled)
+    unsigned long long* lay_part;   // 3 per kLayTile-cell tile + 2: tile sums, then tile offsets (layout kernels)
     float* sp_pos[2][2];  // spill lists (kSpillCap entries) per parity
     float* sp_vel[2][3];
     uint32_t* sp_pid[2];
@@ -200,6 +201,7 @@ struct Launch {
     int slabs = 0;        // some simulation is a slab of a decomposed domain
     int flux = 0;         // some simulation counts particles through a plane
     int grid_p, grid_c;   // persistent grid sizes
+    int lay_tiles = 1;    // layout tiles (kLayTile cells) of the largest simulation
     cudaStream_t stream;
 };
 
@@ -207,6 +209,7 @@ constexpr int kPTile = 2048;  // particles per tile
 constexpr int kCTile = 32;    // cells per tile (balances the per-cell kernels across SMs)
 constexpr int kSpillCap = 4096;  // spill entries per parity (fused pipeline)
 constexpr int kNFPrm = 16;       // u[3], theta, L[6], P_relax, nu, nu_ES, P_ne, valid, spare
+constexpr int kLayTile = 1024;   // cells per block of the layout kernels (fused pipeline)
 
 void launch_stream(const Launch& L, bool fp64);
 void launch_scan(const Launch& L, bool with_inj = true);

@@ -265,7 +265,7 @@ def test_fused_stages_compose_a_step(usp):
     a.step(1)
     for k, _ in usp.stage_list("fused"):
         b.run_stage(k)
-    assert usp.launches_per_step("fused") == 4
+    assert usp.launches_per_step("fused") == 6   # k_g2, k_g1, k_params_f and three layout kernels
     ia, ib = a.info(), b.info()
     assert ia["step"] == ib["step"] == 1
     from tests._util import by_pid
