@@ -331,9 +331,11 @@ int usp_batch_run_stage(usp_batch* b, int stage);
  *     loading the library holds until the process exits; the call clears
  *     it on the GPU before use and calls no cudaMalloc, cudaFree or other
  *     allocating routine.
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *   - Every call looks up the array's device address on the current device
+ *     (cudaGetSymbolAddress, which allocates nothing), so the entry point
+ *     stays valid after cudaDeviceReset; the first call on a device also
+ *     loads the module there, so make that first call before any stream
+ *     capture.
  *   - Every call shares the array: calls whose work overlaps on the GPU
  *     (different streams without ordering, several host threads) race and
  *     give wrong results; order them on one stream.

@@ -13,7 +13,6 @@
 #include "usp_internal.cuh"
 
 #include <algorithm>
-#include <mutex>
 
 namespace {
 
@@ -21,9 +20,6 @@ namespace {
 // holds these 2 MB until the process exits
 static __device__ __align__(256) uint32_t g_sort_scratch[2 * (USP_STATIC_MAX_CELLS + 1)];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-uint32_t* g_scratch_addr[kMaxDevices] = {nullptr};
 
 struct GridF64 {
     int dim, nx, ny, K;
@@ -93,24 +89,18 @@ __global__ void k_static_scatter(GridF64 g, int64_t n, const double* __restrict_
     }
 }
 
-// device address of the scratch array for the current device, looked up once
+// device address of the scratch array on the current device.  Looked up on
+// every call (the lookup allocates nothing): a cached address would dangle
+// after cudaDeviceReset, which unloads the module and places the array anew
+// on the next use.
 int scratch_address(uint32_t** out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    uint32_t* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress((void**)&p, g_sort_scratch);
+    if (e != cudaSuccess || !p) {
         cudaGetLastError();
         return USP_ERR_CUDA;
     }
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[dev]) {
-        uint32_t* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress((void**)&p, g_sort_scratch);
-        if (e != cudaSuccess || !p) {
-            cudaGetLastError();
-            return USP_ERR_CUDA;
-        }
-        g_scratch_addr[dev] = p;
-    }
-    *out = g_scratch_addr[dev];
+    *out = p;
     return USP_OK;
 }
 

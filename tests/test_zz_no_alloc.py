@@ -61,3 +61,42 @@ def test_static_cell_sort_matches_handle_sort_twice():
 
     too_big = U.Grid(2, 1024, 1024, (ctypes.c_double * 2)(0.0, 0.0), (ctypes.c_double * 2)(1.0, 1.0))
     assert L.usp_cell_sort_static(ctypes.byref(too_big), 0, None, start.data_ptr(), None, None) == -4
+
+
+def test_static_cell_sort_one_dimensional_grid():
+    """1-D grids use y alone (x ignored): cells floor((y - lo) / dy) clamped to
+    the grid, as the handle's FP64 sort assigns them; two calls in a row."""
+    import torch
+    from paper_1808_03801_gb300 import usp as U
+    from paper_1808_03801_gb300 import workloads as W
+    L = U.lib()
+    ny, n = 37, 15000
+    w = W.couette(ny=ny, ppc=20, precision="fp64")
+    w["params"]["dt"] = 1e-30
+    H = w["grid"]["hi"][1]
+    rng = np.random.default_rng(9)
+    pos = np.column_stack([rng.uniform(-5.0, 5.0, n), rng.uniform(0, H, n)])
+    pos[:5, 1] = [0.0, H, H * (1 - 1e-15), 0.5 * H, 1e-300]
+    vel = rng.normal(0, 300, (n, 3))
+    h = U.Simulation(w).set_particles(pos, vel, np.arange(n, dtype=np.uint32))
+    for k in (0, 1, 2):
+        h.run_stage(k)
+    P = h.particles()
+    cell_ref = np.empty(n, dtype=np.int64)
+    cell_ref[P["pid"]] = P["cell"]
+    start_ref = np.concatenate([[0], np.cumsum(np.bincount(P["cell"], minlength=ny))])
+    grid = U.Grid(1, 0, ny, (ctypes.c_double * 2)(0.0, 0.0), (ctypes.c_double * 2)(1.0, H))
+    dpos = torch.tensor(pos, dtype=torch.float64, device="cuda")
+    for call in range(2):
+        start = torch.full((ny + 1,), -1, dtype=torch.int32, device="cuda")
+        perm = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+        rc = L.usp_cell_sort_static(ctypes.byref(grid), n, dpos.data_ptr(), start.data_ptr(), perm.data_ptr(),
+                                    torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        assert rc == 0, rc
+        s = start.cpu().numpy().view(np.uint32).astype(np.int64)
+        p = perm.cpu().numpy().view(np.uint32).astype(np.int64)
+        assert np.array_equal(s, start_ref), call
+        cell_static = np.empty(n, dtype=np.int64)
+        cell_static[p] = np.repeat(np.arange(ny), np.diff(s))
+        assert np.array_equal(cell_static, cell_ref), call
