@@ -205,7 +205,7 @@ struct Launch {
     cudaStream_t stream;
 };
 
-constexpr int kPTile = 2048;  // particles per tile
+constexpr int kPTile = 512;   // particles per tile (small domains still spread over many SMs)
 constexpr int kCTile = 32;    // cells per tile (balances the per-cell kernels across SMs)
 constexpr int kSpillCap = 4096;  // spill entries per parity (fused pipeline)
 constexpr int kNFPrm = 16;       // u[3], theta, L[6], P_relax, nu, nu_ES, P_ne, valid, spare

@@ -14,6 +14,8 @@
 //   k_relax    Bernoulli or fixed-count selection, ES Gaussian or   (Eqs. 8b, 9, 27, 29-32,
 //              Gallis-Torczynski sampling, conservation              10-11)
 //   k_finish   advance the step counter and swap buffers
+#include <algorithm>
+
 #include "usp_device.cuh"
 
 #include <cstdio>
@@ -450,24 +452,32 @@ __device__ __forceinline__ bool selected(const SimDev& s, const PView<T>& B, uin
     return rank < ns;
 }
 
+// One warp per block, the blocks striding over single cells (not tiles of
+// cells): the relaxation is bound by FP64 issue (about two FP64 FMA per clock
+// per SM on GB300), so even a domain of a hundred cells should spread over a
+// hundred SMs.
 template <class T>
-__global__ void __launch_bounds__(256) k_relax(const SimDev* __restrict__ sims, const int2* __restrict__ tiles,
-                                               const int* __restrict__ ntiles) {
+__global__ void __launch_bounds__(32) k_relax(const SimDev* __restrict__ sims, const int2* __restrict__ tiles,
+                                              const int* __restrict__ ntiles) {
     __shared__ SimDev sim_sh;
     const int nt = *ntiles;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    for (int t = blockIdx.x; t < nt; t += gridDim.x) {
-        const int2 tile = tiles[t];
-        __syncthreads();
-        load_sim(sim_sh, sims[tile.x]);
-        __syncthreads();
+    const int lane = threadIdx.x & 31;
+    int loaded = -1;
+    for (int g = blockIdx.x; g < nt * kCTile; g += gridDim.x) {
+        const int2 tile = tiles[g / kCTile];
+        if (tile.x != loaded) {
+            __syncwarp();
+            load_sim(sim_sh, sims[tile.x]);
+            __syncwarp();
+            loaded = tile.x;
+        }
         const SimDev& s = sim_sh;
         const int K = s.K;
         const uint32_t step = s.dyn->step;
         PView<T> B = view<T>(s, s.dyn->cur ^ 1);
-        for (int cc = warp; cc < kCTile; cc += nwarps) {
-            const int cell = tile.y + cc;
-            if (cell >= K) break;
+        {
+            const int cell = tile.y + g % kCTile;
+            if (cell >= K) continue;
             const double* pr = s.prm;
             const bool valid = pr[(size_t)14 * K + cell] != 0.0;
             CellRelax R;
@@ -635,8 +645,12 @@ void launch_moments(const Launch& L, bool fp64) {
 }
 void launch_params(const Launch& L) { k_params<<<L.grid_c, 32, 0, L.stream>>>(L.sims, L.ctiles, L.nctiles); }
 void launch_relax(const Launch& L, bool fp64) {
-    if (fp64) k_relax<double><<<L.grid_c, 256, 0, L.stream>>>(L.sims, L.ctiles, L.nctiles);
-    else k_relax<float><<<L.grid_c, 256, 0, L.stream>>>(L.sims, L.ctiles, L.nctiles);
+    // one warp per cell slot of the tiles, at most 32 one-warp blocks per SM
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = std::max(1, std::min(L.grid_c * kCTile, 32 * sms));
+    if (fp64) k_relax<double><<<grid, 32, 0, L.stream>>>(L.sims, L.ctiles, L.nctiles);
+    else k_relax<float><<<grid, 32, 0, L.stream>>>(L.sims, L.ctiles, L.nctiles);
 }
 void launch_finish(const Launch& L) { k_finish<<<(L.nsims + 127) / 128, 128, 0, L.stream>>>(L.sims, L.nsims); }
 
