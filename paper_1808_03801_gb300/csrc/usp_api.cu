@@ -186,10 +186,12 @@ static void enqueue_any(usp_handle* h, const Launch& L) {
     else enqueue_step(L, h->precision == USP_FP64, h->host.has_reservoir != 0);
 }
 
+// default k_g2 configuration (7 consumer warps per CTA, two CTAs per SM):
+// the fastest of the three on every workload measured; the autotuner may
+// pick another (the staged cell size no longer depends on it)
 static int choose_R(uint32_t max_count) {
-    if (max_count <= 128) return 4;
-    if (max_count <= 256) return 8;
-    return 12;
+    (void)max_count;
+    return 8;
 }
 
 static int count_for_density(const SimDev& s, double n, double n_ref, int ppc_ref) {

@@ -212,8 +212,25 @@ __device__ __forceinline__ void es_draw1(const FCell& f, const TimeDraw& td, flo
 // and ends the warp's work, so a fault in the pipeline shows up as lost
 // particles instead of a hung GPU.
 // ---------------------------------------------------------------------------
-__device__ __noinline__ bool advect_slow(const SimDev& s, uint32_t step, uint32_t pid, float& x, float& y, float* c) {
-    return advect<float>(s, step, pid, x, y, c);
+// the general advection (wall and plate hits), out of line; the particle
+// goes in and out by value so that the common path keeps it in registers
+// (reference arguments to a call would pass through local memory)
+struct AdvOut {
+    float x, y, c0, c1, c2;
+    int alive;
+};
+
+__device__ __noinline__ AdvOut advect_slow(const SimDev& s, uint32_t step, uint32_t pid, float x, float y, float c0,
+                                           float c1, float c2) {
+    float c[3] = {c0, c1, c2};
+    AdvOut o;
+    o.alive = advect<float>(s, step, pid, x, y, c) ? 1 : 0;
+    o.x = x;
+    o.y = y;
+    o.c0 = c[0];
+    o.c1 = c[1];
+    o.c2 = c[2];
+    return o;
 }
 
 // per-cell register copy of what the advection and the scatter need
@@ -297,7 +314,13 @@ __device__ __forceinline__ bool advect_fast(const SimDev& s, const Ctx& C, uint3
         c[2] += C.b2;
         return true;
     }
-    return advect_slow(s, step, pid, x, y, c);
+    const AdvOut o = advect_slow(s, step, pid, x, y, c[0], c[1], c[2]);
+    x = o.x;
+    y = o.y;
+    c[0] = o.c0;
+    c[1] = o.c1;
+    c[2] = o.c2;
+    return o.alive != 0;
 }
 
 // append one particle to the bucket of its cell (all 32 lanes call this
