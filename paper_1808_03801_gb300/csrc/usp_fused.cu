@@ -1215,6 +1215,10 @@ __global__ void __launch_bounds__(32 * (NC + 1), 16 / (NC + 1)) k_g2(const SimDe
 __global__ void __launch_bounds__(256) k_g1(const SimDev* __restrict__ sims, const int2* __restrict__ tiles,
                                             const int* __restrict__ ntiles) {
     __shared__ uint32_t spl_all[8][32];
+    // the tile's per-cell headers, fetched in one round for all 32 cells:
+    // bucket start, particles in the bucket, arrivals, and the shift u_s
+    __shared__ uint32_t h_base[kCTile], h_nb[kCTile], h_arr[kCTile];
+    __shared__ float4 h_us[kCTile];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     __shared__ SimDev sim_sh;
     const int nt = *ntiles;
@@ -1226,18 +1230,28 @@ __global__ void __launch_bounds__(256) k_g1(const SimDev* __restrict__ sims, con
         const SimDev& s = sim_sh;
         const int K = s.K;
         const int q = s.dyn->cur ^ 1;
+        if (threadIdx.x < kCTile && tile.y + (int)threadIdx.x < K) {
+            const int cell = tile.y + (int)threadIdx.x;
+            const uint32_t base = s.lay[q][cell];
+            const uint32_t top = min(s.lay[q][cell + 1], (uint32_t)s.cap);
+            const uint32_t capc = top > base ? top - base : 0u;
+            const uint32_t arrived = s.cnt[q][cell];
+            h_base[threadIdx.x] = base;
+            h_nb[threadIdx.x] = min(arrived, capc);
+            h_arr[threadIdx.x] = arrived;
+            h_us[threadIdx.x] = reinterpret_cast<const float4*>(s.fprm)[(size_t)cell * (kNFPrm / 4)];
+        }
+        __syncthreads();
         const float* V0 = (const float*)s.vel[q][0];
         const float* V1 = (const float*)s.vel[q][1];
         const float* V2 = (const float*)s.vel[q][2];
         for (int cc = warp; cc < kCTile; cc += 8) {
             const int cell = tile.y + cc;
             if (cell >= K) break;
-            const uint32_t base = s.lay[q][cell];
-            const uint32_t top = min(s.lay[q][cell + 1], (uint32_t)s.cap);
-            const uint32_t capc = top > base ? top - base : 0u;
-            const uint32_t arrived = s.cnt[q][cell];
-            const uint32_t nb = min(arrived, capc);
-            const float4 us = reinterpret_cast<const float4*>(s.fprm)[(size_t)cell * (kNFPrm / 4)];
+            const uint32_t base = h_base[cc];
+            const uint32_t nb = h_nb[cc];
+            const uint32_t arrived = h_arr[cc];
+            const float4 us = h_us[cc];
             const float u0 = us.x, u1 = us.y, u2 = us.z;
             uint32_t nsp = 0;
             if (arrived > nb) nsp = collect_spill(s, q, cell, spl_all[warp], lane);
@@ -1254,26 +1268,41 @@ __global__ void __launch_bounds__(256) k_g1(const SimDev* __restrict__ sims, con
                 S[9] += c2 * C0; S[10] += c2 * C1; S[11] += c2 * C2;
             };
 #pragma unroll 4
-            for (uint32_t j = lane; j < nb; j += 32) add(V0[base + j], V1[base + j], V2[base + j]);
+            for (uint32_t j = lane; j < nb; j += 32) add(__ldcs(V0 + base + j), __ldcs(V1 + base + j), __ldcs(V2 + base + j));
             for (uint32_t j = nb + lane; j < n; j += 32) {   // spill-list entries of the cell
                 const uint32_t i = spl_all[warp][j - nb];
                 add(s.sp_vel[q][0][i], s.sp_vel[q][1][i], s.sp_vel[q][2][i]);
             }
+            // The cell's 64-byte record [N, 12 sums, shift u_s] as a warp
+            // reduce-scatter: at each of four halving stages a lane keeps half
+            // of its values and adds the partner's copy of that half (16
+            // shuffles instead of 60 for twelve butterfly sums); lane 2v then
+            // holds entry v of the record and writes it.  N and u_s come from
+            // lane 0 alone.  FP32 sums only: their promotion to FP64 happens in
+            // k_params_f, one cell per thread (an FP64 instruction costs the
+            // same for one lane).
+            float v[16];
+            v[0] = lane == 0 ? (float)n : 0.0f;
 #pragma unroll
-            for (int k = 0; k < 12; ++k) S[k] = warp_sumf(S[k]);
-            // FP32 sums only: their promotion to FP64 happens in k_params_f, one
-            // cell per thread (an FP64 instruction costs the same for one lane)
-            if (lane < 16) {
-                float v;
-                if (lane == 0) v = (float)n;
-                else if (lane <= 12) v = S[0];
-                else v = lane == 13 ? u0 : (lane == 14 ? u1 : u2);
-                // lanes 1..12 need S[lane - 1]: select without dynamic indexing
+            for (int k = 0; k < 12; ++k) v[1 + k] = S[k];
+            v[13] = lane == 0 ? u0 : 0.0f;
+            v[14] = lane == 0 ? u1 : 0.0f;
+            v[15] = lane == 0 ? u2 : 0.0f;
 #pragma unroll
-                for (int k = 1; k < 12; ++k)
-                    if (lane == k + 1) v = S[k];
-                s.momf[(size_t)cell * 16 + lane] = v;   // one 64-byte record per cell
+            for (int half = 8; half >= 1; half >>= 1) {
+                const bool up = (lane & (2 * half)) != 0;
+#pragma unroll
+                for (int i = 0; i < half; ++i) {
+                    const float send = up ? v[i] : v[i + half];
+                    const float recv = __shfl_xor_sync(0xffffffffu, send, 2 * half);
+                    v[i] = (up ? v[i + half] : v[i]) + recv;
+                }
             }
+            v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+            if ((lane & 1) == 0) s.momf[(size_t)cell * 16 + (lane >> 1)] = v[0];   // one 64-byte record per cell
+            // the totals of the first six sums (entries 1..6, on lanes 2..12) for the local state
+#pragma unroll
+            for (int k = 0; k < 6; ++k) S[k] = __shfl_sync(0xffffffffu, v[0], 2 * (k + 1));
             if (lane == 31) {
                 // local state of the cell for its neighbours' Kn_GLL (FP32):
                 // the instantaneous one, or the Eq. 34 average as it stood at
