@@ -47,6 +47,7 @@ class _Config(ctypes.Structure):
         ("fixed_pne", ctypes.c_double), ("reservoir_cols", ctypes.c_int),
         ("flux_axis", ctypes.c_int), ("flux_pos", ctypes.c_double), ("gll_average", ctypes.c_int),
         ("selection", ctypes.c_int), ("es_sampler", ctypes.c_int),
+        ("weighted", ctypes.c_int), ("r_p", ctypes.c_double), ("weight_average", ctypes.c_int),
     ]
 
 
@@ -94,6 +95,7 @@ def lib():
         for f in ("orc_get_particles",):
             getattr(L, f).argtypes = [vp, vp, vp, vp, vp]
         L.orc_get_counts.argtypes = [vp, vp]
+        L.orc_get_weights.argtypes = [vp, vp]
         L.orc_get_fields.argtypes = [vp, i32, vp]
         L.orc_get_params.argtypes = [vp, vp]
         L.orc_get_counters.argtypes = [vp, vp]
@@ -148,6 +150,9 @@ def make_config(w: dict) -> _Config:
     c.gll_average = int(pr.get("gll_average", 0))
     c.selection = {"bernoulli": 0, "fixed_count": 1}[pr.get("selection", "bernoulli")]
     c.es_sampler = {"cholesky": 0, "gallis_torczynski": 1}[pr.get("es_sampler", "cholesky")]
+    c.weighted = int(pr.get("weighted", 0))
+    c.r_p = float(pr.get("r_p", 10.0))
+    c.weight_average = int(pr.get("weight_average", 0))
     return c
 
 
@@ -231,7 +236,9 @@ class OracleSim:
         pid = np.zeros(n, dtype=np.uint32)
         cell = np.zeros(n, dtype=np.int32)
         lib().orc_get_particles(self._h, pos.ctypes.data, vel.ctypes.data, pid.ctypes.data, cell.ctypes.data)
-        return {"pos": pos, "vel": vel, "pid": pid, "cell": cell}
+        w = np.zeros(n)
+        lib().orc_get_weights(self._h, w.ctypes.data)
+        return {"pos": pos, "vel": vel, "pid": pid, "cell": cell, "w": w}
 
     def counts(self):
         out = np.zeros(self.K, dtype=np.int32)

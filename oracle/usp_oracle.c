@@ -38,10 +38,15 @@
 #define MAX_BOUNCE 8              /* wall interactions per particle per step */
 #define PI 3.14159265358979323846
 
-enum { P_INIT = 0, P_RELAX = 1, P_WALL = 2, P_INJECT = 3 };
+enum { P_INIT = 0, P_RELAX = 1, P_WALL = 2, P_INJECT = 3, P_ADD = 4, P_CELL = 5 };
+
+/* fields that define the weights of added particles (Eq. 26), per cell:
+ * u[3], theta, sigma/rho (xx yy zz xy xz yz), q/rho, nu */
+enum { WF_U = 0, WF_TH = 3, WF_SIG = 4, WF_Q = 10, WF_NU = 13, WF_N = 14 };
 
 typedef struct {
     double x, y, c[3];
+    double w;              /* particle weight (1 unless created by Table 2 steps 2, 4, 7) */
     uint32_t pid;
     int cell;
     int alive;
@@ -49,6 +54,7 @@ typedef struct {
 
 typedef struct {
     int n;                 /* particles in the cell */
+    double neff;           /* sum of their weights (= n when every weight is 1) */
     double u[3];           /* mean velocity */
     double theta;          /* R T = sum |C|^2 / (3 N) */
     double P[6];           /* sum C_i C_j / N: xx, yy, zz, xy, xz, yz */
@@ -90,6 +96,13 @@ struct orc_sim {
     double* inst;                /* ORC_NFIELDS x K */
     double* avg;
     int64_t counters[5];
+    /* weighted particles: fields of f^n (step 2) and f* (steps 4, 7), and
+     * their Eq. 34 averages, WF_N per cell */
+    double* wf_n;
+    double* wf_s;
+    double* wa_n;
+    double* wa_s;
+    int wa_started;
 };
 
 /* ------------------------------------------------------------------------ */
@@ -179,12 +192,20 @@ orc_sim* orc_create(const orc_config* cfg) {
     s->gs = (grad_state*)calloc((size_t)s->K, sizeof(grad_state));
     s->inst = (double*)calloc((size_t)ORC_NFIELDS * s->K, sizeof(double));
     s->avg = (double*)calloc((size_t)ORC_NFIELDS * s->K, sizeof(double));
+    if (s->cfg.r_p <= 0) s->cfg.r_p = 10.0;
+    if (s->cfg.weighted) {
+        s->wf_n = (double*)calloc((size_t)WF_N * s->K, sizeof(double));
+        s->wf_s = (double*)calloc((size_t)WF_N * s->K, sizeof(double));
+        s->wa_n = (double*)calloc((size_t)WF_N * s->K, sizeof(double));
+        s->wa_s = (double*)calloc((size_t)WF_N * s->K, sizeof(double));
+    }
     return s;
 }
 
 void orc_destroy(orc_sim* s) {
     if (!s) return;
     free(s->p); free(s->mom); free(s->par); free(s->gs); free(s->inst); free(s->avg);
+    free(s->wf_n); free(s->wf_s); free(s->wa_n); free(s->wa_s);
     free(s);
 }
 
@@ -243,6 +264,7 @@ static void fill_cell(orc_sim* s, int cell, int count, double T, const double* u
         q->pid = pid;
         q->cell = cell;
         q->alive = 1;
+        q->w = 1.0;
     }
 }
 
@@ -288,6 +310,7 @@ int orc_set_particles(orc_sim* s, int64_t n, const double* pos, const double* ve
         q->pid = pid[i];
         q->cell = cell_of(s, q->x, q->y);
         q->alive = 1;
+        q->w = 1.0;
     }
     return 0;
 }
@@ -428,7 +451,10 @@ static int flux_side(const orc_config* c, const particle* q) {
 /* advection of every particle; the net flow through the counting plane is
  * the change of side summed over the particles (a particle that leaves
  * through a reservoir face ends on that face) */
+static void weighted_step2(orc_sim* s);
+
 static void stream_phase(orc_sim* s) {
+    if (s->cfg.weighted) weighted_step2(s);   /* Table 2 step 2 precedes the advection */
     for (int64_t i = 0; i < s->np; ++i) {
         particle* q = &s->p[i];
         int before = s->cfg.flux_axis ? flux_side(&s->cfg, q) : 0;
@@ -512,25 +538,32 @@ static void moments_phase(orc_sim* s) {
         cell_moments* M = &s->mom[cell];
         int n = (int)(j - i);
         M->n = n;
+        /* weighted sums over the particles of the cell (every weight is 1
+         * unless the weighted particles of Table 2 are in use) */
+        double we = 0;
+        for (int64_t k = i; k < j; ++k) we += s->p[k].w;
+        M->neff = we;
+        if (!(we > 0)) { i = j; continue; }
         for (int d = 0; d < 3; ++d) {
             double sum = 0;
-            for (int64_t k = i; k < j; ++k) sum += s->p[k].c[d];
-            M->u[d] = sum / n;
+            for (int64_t k = i; k < j; ++k) sum += s->p[k].w * s->p[k].c[d];
+            M->u[d] = sum / we;
         }
         double e = 0, P[6] = {0}, Q[3] = {0};
         for (int64_t k = i; k < j; ++k) {
+            double wk = s->p[k].w;
             double C0 = s->p[k].c[0] - M->u[0];
             double C1 = s->p[k].c[1] - M->u[1];
             double C2 = s->p[k].c[2] - M->u[2];
             double c2 = C0 * C0 + C1 * C1 + C2 * C2;
-            e += c2;
-            P[0] += C0 * C0; P[1] += C1 * C1; P[2] += C2 * C2;
-            P[3] += C0 * C1; P[4] += C0 * C2; P[5] += C1 * C2;
-            Q[0] += c2 * C0; Q[1] += c2 * C1; Q[2] += c2 * C2;
+            e += wk * c2;
+            P[0] += wk * C0 * C0; P[1] += wk * C1 * C1; P[2] += wk * C2 * C2;
+            P[3] += wk * C0 * C1; P[4] += wk * C0 * C2; P[5] += wk * C1 * C2;
+            Q[0] += wk * c2 * C0; Q[1] += wk * c2 * C1; Q[2] += wk * c2 * C2;
         }
-        M->theta = e / (3.0 * n);
-        for (int d = 0; d < 6; ++d) M->P[d] = P[d] / n;
-        for (int d = 0; d < 3; ++d) M->Q[d] = Q[d] / (2.0 * n);
+        M->theta = e / (3.0 * we);
+        for (int d = 0; d < 6; ++d) M->P[d] = P[d] / we;
+        for (int d = 0; d < 3; ++d) M->Q[d] = Q[d] / (2.0 * we);
         i = j;
     }
 }
@@ -584,9 +617,9 @@ static void params_phase(orc_sim* s) {
         cell_moments* M = &s->mom[cell];
         cell_params* P = &s->par[cell];
         memset(P, 0, sizeof(*P));
-        P->valid = M->n >= 2 && M->theta > 0;
+        P->valid = M->n >= 2 && M->neff > 1.0 && M->theta > 0;
         if (!P->valid) continue;
-        P->n = M->n * s->w;
+        P->n = M->neff * s->w;
         P->T = M->theta / s->R;
         P->umag = sqrt(M->u[0] * M->u[0] + M->u[1] * M->u[1] + M->u[2] * M->u[2]);
         P->a_sound = sqrt(GAMMA_MONO * M->theta);
@@ -715,7 +748,316 @@ static int cmp_key_pos(const void* a, const void* b) {
     return x->pos < y->pos ? -1 : (x->pos > y->pos);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Weighted added particles (Table 2 steps 2, 4, 7; Eqs. 22-28)              */
+/* ------------------------------------------------------------------------ */
+/* Eq. 26 for one velocity C about the cell mean: the weight that makes a    */
+/* Maxwellian particle represent r_p (dt J / 2) / f_e, with the stress and   */
+/* heat flux per unit density (sigma/rho, q/rho), so that sigma/p =          */
+/* (sigma/rho)/theta and q/(p theta) = (q/rho)/theta^2.                       */
+static double eq26_weight(const double* C, double theta, const double* sig, const double* q, double nu, double pne,
+                          double dt, double Pr) {
+    double quad = sig[0] * C[0] * C[0] + sig[1] * C[1] * C[1] + sig[2] * C[2] * C[2] +
+                  2.0 * (sig[3] * C[0] * C[1] + sig[4] * C[0] * C[2] + sig[5] * C[1] * C[2]);
+    double c2 = C[0] * C[0] + C[1] * C[1] + C[2] * C[2];
+    double qc = q[0] * C[0] + q[1] * C[1] + q[2] * C[2];
+    double bracket = quad / (2.0 * theta * theta) + 0.4 * Pr * qc / (theta * theta) * (c2 / (2.0 * theta) - 2.5);
+    return -0.5 * nu * pne * dt * bracket;
+}
+
+/* N_a of Eq. 25 for a cell of N_eff particle weights: N_eff min(1, nu_ES dt)
+ * / r_p, rounded up or down at random (its expectation is the printed
+ * value); the weight of each added particle carries r_p / min(1, nu_ES dt)
+ * so that, whatever the count, the added particles represent the PDF of
+ * Eq. 22 (or 24, 27) in expectation. */
+static int added_count(const orc_sim* s, int cell, double neff, double nu, uint32_t stage, double* prefactor) {
+    double kap = fmin(1.0, s->cfg.Pr * nu * s->dt);
+    *prefactor = kap > 0 ? s->cfg.r_p / kap : 0.0;
+    if (!(neff > 0) || !(kap > 0)) return 0;
+    uint32_t w[4];
+    draw(s, (uint32_t)cell, s->step, P_CELL, stage, w);
+    return (int)floor(neff * kap / s->cfg.r_p + orc_u01(w[0]));
+}
+
+/* Add the particles of one Table 2 stage to one cell: uniform positions,
+ * Maxwellian velocities at the field's (u, theta), weights from Eq. 26 with
+ * the field's (sigma, q, nu) times `factor` (1 for steps 2 and 4, the
+ * Eq. 27 factor -2 (1 - e^-a)/a for step 7). */
+static void add_weighted(orc_sim* s, int cell, double neff, const double* F, double pne, double factor, uint32_t stage) {
+    double pref;
+    int na = added_count(s, cell, neff, F[WF_NU], stage, &pref);
+    if (na <= 0 || !(F[WF_TH] > 0)) return;
+    double xl, yl;
+    cell_lo(s, cell, &xl, &yl);
+    double sq = sqrt(F[WF_TH]);
+    reserve(s, s->np + na);
+    for (int k = 0; k < na; ++k) {
+        particle* q = &s->p[s->np++];
+        uint32_t pid = s->next_pid++;
+        uint32_t w[4], v[4];
+        draw(s, pid, s->step, P_ADD, 0, w);
+        draw(s, pid, s->step, P_ADD, 1, v);
+        q->x = s->cfg.dim == 2 ? xl + orc_u01(w[0]) * s->dx : 0.0;
+        q->y = yl + orc_u01(w[1]) * s->dy;
+        double z0, z1, z2, z3;
+        box_muller(v[0], v[1], &z0, &z1);
+        box_muller(v[2], v[3], &z2, &z3);
+        double C[3] = {sq * z0, sq * z1, sq * z2};
+        for (int d = 0; d < 3; ++d) q->c[d] = F[WF_U + d] + C[d];
+        q->w = factor * pref * eq26_weight(C, F[WF_TH], &F[WF_SIG], &F[WF_Q], F[WF_NU], pne, s->dt, s->cfg.Pr);
+        q->pid = pid;
+        q->cell = cell;
+        q->alive = 1;
+    }
+}
+
+/* Eq. 34 average of a weight field, started at zero stress and heat flux
+ * (the Maxwellian initial state) and at the first mean velocity, theta, nu */
+static void average_fields(const orc_sim* s, double* avg, const double* inst, int first) {
+    const double keep = (s->cfg.n_avg - 1.0) / s->cfg.n_avg, add = 1.0 / s->cfg.n_avg;
+    for (int cell = 0; cell < s->K; ++cell) {
+        double* a = avg + (size_t)WF_N * cell;
+        const double* f = inst + (size_t)WF_N * cell;
+        for (int k = 0; k < WF_N; ++k) {
+            if (first) a[k] = (k >= WF_SIG && k < WF_NU) ? 0.0 : f[k];
+            else a[k] = keep * a[k] + add * f[k];
+        }
+    }
+}
+
+static double nu_of_state(const orc_sim* s, double neff, double theta) {
+    double n = neff * s->w, T = theta / s->R;
+    double rho = n * s->cfg.mass, p = rho * theta;
+    double mu = s->mu_ref * pow(T / s->cfg.T_ref, s->cfg.omega);    /* Eq. 35 */
+    return p / mu;
+}
+
+static double pne_of(const orc_sim* s, int cell) {
+    const orc_config* c = &s->cfg;
+    if (c->mode == ORC_MODE_SP || c->mode == ORC_MODE_SPESBGK) return 0.0;
+    if (c->mode == ORC_MODE_FIXED_PNE) return c->fixed_pne;
+    return s->par[cell].pne;   /* Eq. 16, from the last parameter evaluation */
+}
+
+/* Table 2 step 2, at t_n: the weighted moments of f^n in every cell (the
+ * particles sit in the cells of the last sort; step-7 particles were
+ * created in theirs), then N_a particles per cell with weights W^n. */
+static void weighted_step2(orc_sim* s) {
+    const int K = s->K;
+    double* acc = (double*)calloc((size_t)K * 14, sizeof(double));
+    for (int64_t i = 0; i < s->np; ++i) {
+        const particle* q = &s->p[i];
+        double* a = acc + (size_t)14 * q->cell;
+        a[0] += q->w;
+        for (int d = 0; d < 3; ++d) a[1 + d] += q->w * q->c[d];
+    }
+    for (int cell = 0; cell < K; ++cell) {
+        double* a = acc + (size_t)14 * cell;
+        if (a[0] > 0) for (int d = 0; d < 3; ++d) a[1 + d] /= a[0];
+    }
+    for (int64_t i = 0; i < s->np; ++i) {
+        const particle* q = &s->p[i];
+        double* a = acc + (size_t)14 * q->cell;
+        double C[3] = {q->c[0] - a[1], q->c[1] - a[2], q->c[2] - a[3]};
+        double c2 = C[0] * C[0] + C[1] * C[1] + C[2] * C[2];
+        a[4] += q->w * c2;
+        a[5] += q->w * C[0] * C[0]; a[6] += q->w * C[1] * C[1]; a[7] += q->w * C[2] * C[2];
+        a[8] += q->w * C[0] * C[1]; a[9] += q->w * C[0] * C[2]; a[10] += q->w * C[1] * C[2];
+        for (int d = 0; d < 3; ++d) a[11 + d] += q->w * c2 * C[d];
+    }
+    double* neff = (double*)calloc((size_t)K, sizeof(double));
+    for (int cell = 0; cell < K; ++cell) {
+        const double* a = acc + (size_t)14 * cell;
+        double* F = s->wf_n + (size_t)WF_N * cell;
+        memset(F, 0, WF_N * sizeof(double));
+        neff[cell] = a[0];
+        if (!(a[0] > 1.0) || !(a[4] > 0)) continue;
+        double th = a[4] / (3.0 * a[0]);
+        for (int d = 0; d < 3; ++d) F[WF_U + d] = a[1 + d];
+        F[WF_TH] = th;
+        for (int d = 0; d < 3; ++d) F[WF_SIG + d] = a[5 + d] / a[0] - th;
+        for (int d = 0; d < 3; ++d) F[WF_SIG + 3 + d] = a[8 + d] / a[0];
+        for (int d = 0; d < 3; ++d) F[WF_Q + d] = a[11 + d] / (2.0 * a[0]);
+        F[WF_NU] = nu_of_state(s, a[0], th);
+    }
+    const double* use = s->wf_n;
+    if (s->cfg.weight_average) {
+        average_fields(s, s->wa_n, s->wf_n, !(s->wa_started & 1));
+        s->wa_started |= 1;
+        use = s->wa_n;
+    }
+    for (int cell = 0; cell < K; ++cell) {
+        double pne = pne_of(s, cell);
+        if (pne == 0.0 || !(neff[cell] > 1.0)) continue;
+        add_weighted(s, cell, neff[cell], use + (size_t)WF_N * cell, pne, 1.0, 1);
+    }
+    free(acc);
+    free(neff);
+}
+
+/* fields of f* for steps 4 and 7 from this step's moments and parameters
+ * (sigma* and q* of Eq. 33, per unit density) */
+static const double* star_fields(orc_sim* s) {
+    for (int cell = 0; cell < s->K; ++cell) {
+        const cell_moments* M = &s->mom[cell];
+        const cell_params* P = &s->par[cell];
+        double* F = s->wf_s + (size_t)WF_N * cell;
+        memset(F, 0, WF_N * sizeof(double));
+        if (!P->valid) continue;
+        for (int d = 0; d < 3; ++d) F[WF_U + d] = M->u[d];
+        F[WF_TH] = M->theta;
+        for (int d = 0; d < 6; ++d) F[WF_SIG + d] = P->sig_star[d];
+        for (int d = 0; d < 3; ++d) F[WF_Q + d] = P->q_star[d];
+        F[WF_NU] = P->nu;
+    }
+    if (!s->cfg.weight_average) return s->wf_s;
+    average_fields(s, s->wa_s, s->wf_s, !(s->wa_started & 2));
+    s->wa_started |= 2;
+    return s->wa_s;
+}
+
+/* Table 2 steps 4-7 in place of the plain relaxation: step 4 adds weighted
+ * particles for f*; steps 5-6 select (Bernoulli, as the plain path), give
+ * int(sum of the selected weights) of them, in selection-key order, weight 1
+ * and a velocity from f_G(t) (Eq. 28, the count rounded at random so that
+ * mass is kept in expectation), delete the others and restore the momentum
+ * and thermal energy per unit weight of the selected set; step 7 adds
+ * weighted particles for the third term of Eq. 27. */
+static void relax_weighted(orc_sim* s) {
+    const orc_config* c = &s->cfg;
+    const double* F = star_fields(s);
+    for (int cell = 0; cell < s->K; ++cell) {
+        const cell_params* P = &s->par[cell];
+        double pne = pne_of(s, cell);
+        if (!P->valid || pne == 0.0) continue;
+        add_weighted(s, cell, s->mom[cell].neff, F + (size_t)WF_N * cell, pne, 1.0, 2);
+    }
+    /* the step-4 particles join their cells */
+    qsort(s->p, (size_t)s->np, sizeof(particle), cmp_cell_pid);
+    int64_t i = 0, cap = 0;
+    double* cold = NULL;
+    key_pos* order = NULL;
+    int* sel = NULL;
+    while (i < s->np) {
+        int cell = s->p[i].cell;
+        int64_t j = i;
+        while (j < s->np && s->p[j].cell == cell) ++j;
+        cell_params* P = &s->par[cell];
+        cell_moments* M = &s->mom[cell];
+        int64_t n = j - i;
+        if (n > cap) {
+            cap = n;
+            cold = (double*)realloc(cold, (size_t)cap * 3 * sizeof(double));
+            sel = (int*)realloc(sel, (size_t)cap * sizeof(int));
+            order = (key_pos*)realloc(order, (size_t)cap * sizeof(key_pos));
+        }
+        P->n_relaxed = 0;
+        if (!P->valid) { i = j; continue; }
+        /* step 5: selection, and the selected set's weight, momentum, energy */
+        int64_t ns = 0;
+        double sw = 0, su[3] = {0, 0, 0};
+        for (int64_t k = i; k < j; ++k) {
+            uint32_t w[4];
+            draw(s, s->p[k].pid, s->step, P_RELAX, 0, w);
+            double key = orc_u01(w[0]);
+            sel[k - i] = key < P->p_relax;
+            if (!sel[k - i]) continue;
+            order[ns].key = key;
+            order[ns].pos = k - i;
+            ++ns;
+            sw += s->p[k].w;
+            for (int d = 0; d < 3; ++d) su[d] += s->p[k].w * s->p[k].c[d];
+        }
+        if (ns == 0) { i = j; continue; }
+        /* Eq. 28: int(sum W) of the selected keep weight 1, the rest go */
+        uint32_t w4[4];
+        draw(s, (uint32_t)cell, s->step, P_CELL, 0, w4);
+        int64_t m = sw > 0 ? (int64_t)floor(sw + orc_u01(w4[0])) : 0;
+        if (m > ns) m = ns;
+        qsort(order, (size_t)ns, sizeof(key_pos), cmp_key_pos);
+        double uo[3] = {0, 0, 0}, eo = 0;
+        if (sw > 0) {
+            for (int d = 0; d < 3; ++d) uo[d] = su[d] / sw;
+            for (int64_t r = 0; r < ns; ++r) {
+                const particle* q = &s->p[i + order[r].pos];
+                for (int d = 0; d < 3; ++d) eo += q->w * (q->c[d] - uo[d]) * (q->c[d] - uo[d]);
+            }
+            eo /= sw;
+        }
+        for (int64_t r = m; r < ns; ++r) s->p[i + order[r].pos].alive = 0;
+        /* step 6: the reassigned particles from f_G(t) (Eqs. 29-32) */
+        double un[3] = {0, 0, 0};
+        for (int64_t r = 0; r < m; ++r) {
+            particle* q = &s->p[i + order[r].pos];
+            uint32_t w[4], v[4];
+            draw(s, q->pid, s->step, P_RELAX, 0, w);
+            double t = sample_time(orc_u01(w[1]), P->nu_es, s->dt);
+            double sfac = c->mode == ORC_MODE_SPESBGK ? 1.0 : P->pne + (1.0 - P->pne) * exp(-P->nu * t);
+            if (c->mode == ORC_MODE_FIXED_PNE) sfac = c->fixed_pne + (1.0 - c->fixed_pne) * exp(-P->nu * t);
+            draw(s, q->pid, s->step, P_RELAX, 1, v);
+            double z[6];
+            box_muller(w[2], w[3], &z[0], &z[1]);
+            box_muller(v[0], v[1], &z[2], &z[3]);
+            box_muller(v[2], v[3], &z[4], &z[5]);
+            const double* L = P->L;
+            double a = sqrt(sfac), bb = sqrt((1.0 - sfac) * M->theta);
+            double C0 = a * (L[0] * z[0]) + bb * z[3];
+            double C1 = a * (L[1] * z[0] + L[2] * z[1]) + bb * z[4];
+            double C2 = a * (L[3] * z[0] + L[4] * z[1] + L[5] * z[2]) + bb * z[5];
+            q->c[0] = M->u[0] + C0;
+            q->c[1] = M->u[1] + C1;
+            q->c[2] = M->u[2] + C2;
+            q->w = 1.0;
+            for (int d = 0; d < 3; ++d) un[d] += q->c[d];
+        }
+        /* conservation: the reassigned set carries the selected set's mean
+         * velocity and thermal energy per unit weight */
+        if (m >= 2 && sw > 0) {
+            for (int d = 0; d < 3; ++d) un[d] /= m;
+            double en = 0;
+            for (int64_t r = 0; r < m; ++r) {
+                const particle* q = &s->p[i + order[r].pos];
+                for (int d = 0; d < 3; ++d) en += (q->c[d] - un[d]) * (q->c[d] - un[d]);
+            }
+            en /= m;
+            double alpha = (en > 0 && eo > 0) ? sqrt(eo / en) : 1.0;
+            for (int64_t r = 0; r < m; ++r) {
+                particle* q = &s->p[i + order[r].pos];
+                for (int d = 0; d < 3; ++d) q->c[d] = uo[d] + alpha * (q->c[d] - un[d]);
+            }
+        } else if (m == 1 && sw > 0) {
+            particle* q = &s->p[i + order[0].pos];
+            for (int d = 0; d < 3; ++d) q->c[d] = uo[d] + (q->c[d] - un[d]) * sqrt(eo > 0 ? eo / (3.0 * M->theta) : 1.0);
+        }
+        P->n_relaxed = (int)m;
+        (void)cold;
+        i = j;
+    }
+    free(cold);
+    free(sel);
+    free(order);
+    /* deleted particles leave */
+    int64_t k = 0;
+    for (int64_t r = 0; r < s->np; ++r)
+        if (s->p[r].alive) s->p[k++] = s->p[r];
+    s->np = k;
+    /* step 7: the third term of Eq. 27, -(1 - e^-a)/nu_ES J*: weights
+     * W' = -W* 2 (1 - e^-a) / a, a = nu_ES dt */
+    for (int cell = 0; cell < s->K; ++cell) {
+        const cell_params* P = &s->par[cell];
+        double pne = pne_of(s, cell);
+        if (!P->valid || pne == 0.0) continue;
+        double a = P->nu_es * s->dt;
+        double fac = -2.0 * (-expm1(-a)) / a;
+        add_weighted(s, cell, s->mom[cell].neff, F + (size_t)WF_N * cell, pne, fac, 3);
+    }
+}
+
 static void relax_phase(orc_sim* s) {
+    if (s->cfg.weighted) {
+        relax_weighted(s);
+        return;
+    }
     int64_t i = 0;
     double* cold = NULL;
     double* ukey = NULL;
@@ -853,7 +1195,7 @@ static void sample_phase(orc_sim* s) {
         cell_params* P = &s->par[cell];
         double f[ORC_NFIELDS];
         memset(f, 0, sizeof(f));
-        f[0] = M->n * s->w;
+        f[0] = M->neff * s->w;
         f[15] = M->n;
         if (M->n >= 1) for (int d = 0; d < 3; ++d) f[1 + d] = M->u[d];
         if (P->valid) {
@@ -914,6 +1256,12 @@ int orc_get_particles(const orc_sim* s, double* pos, double* vel, uint32_t* pid,
         if (pid) pid[i] = q->pid;
         if (cell) cell[i] = cell_of(s, q->x, q->y);
     }
+    return 0;
+}
+
+int orc_get_weights(const orc_sim* s, double* w) {
+    if (!s) return -1;
+    for (int64_t i = 0; i < s->np; ++i) w[i] = s->p[i].w;
     return 0;
 }
 

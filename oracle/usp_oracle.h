@@ -84,6 +84,14 @@ typedef struct {
      * or ORC_SAMPLER_GALLIS_TORCZYNSKI (thermal velocities of Eq. 10
      * transformed by S of Eq. 11) */
     int selection, es_sampler;
+    /* weighted: 1 adds the weighted particles of Table 2 steps 2, 4 and 7
+     * (Eqs. 22-28, the third term of Eq. 27); r_p the scale of Eq. 25 (0:
+     * 10, the paper's value); weight_average: the fields that define the
+     * weights (u, theta, sigma, q, nu of Eq. 26) are the Eq. 34 averages,
+     * stress and heat flux starting from zero */
+    int weighted;
+    double r_p;
+    int weight_average;
 } orc_config;
 
 typedef struct {
@@ -118,6 +126,8 @@ double orc_mu_ref(const orc_sim* s);
 uint32_t orc_step_index(const orc_sim* s);
 /* particles in storage order ((cell, pid) after a sort) */
 int orc_get_particles(const orc_sim* s, double* pos, double* vel, uint32_t* pid, int32_t* cell);
+/* particle weights in the order of orc_get_particles */
+int orc_get_weights(const orc_sim* s, double* w);
 /* per-cell: counts, fields (ORC_NFIELDS x K, [field][cell]) */
 int orc_get_counts(const orc_sim* s, int32_t* counts);
 int orc_get_fields(const orc_sim* s, int averaged, double* out);
