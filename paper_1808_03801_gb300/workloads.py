@@ -133,9 +133,10 @@ def cavity(n=200, ppc=100, Kn=1e-3, dt_over_tauc=None, u_lid=50.0, precision="fp
 
 
 def slit(nx=400, ny=200, ppc=200, Kn=1e-2, dt_over_tauc=1.0, pressure_ratio=10.0, precision="fp32",
-         steps=2000, seed=1, reservoir_cols=2, delta=None):
-    """2-D flow through a slit (Sec. 4.5), upper half domain: x in [-10a, 10a],
-    y in [0, 10a]; specular symmetry plane at y = 0; diffuse wall at y = 10a;
+         steps=2000, seed=1, reservoir_cols=2, delta=None, chamber=10.0):
+    """2-D flow through a slit (Sec. 4.5), upper half domain: x in [-c a, c a],
+    y in [0, c a] with c = `chamber` (10 by default, the paper's height of
+    20a for the full domain); specular symmetry plane at y = 0; diffuse wall at y = c a;
     a zero-thickness diffuse plate at x = 0 for y >= a/2; reservoir buffer
     columns at both x ends (upstream n_1, downstream n_1 / pressure_ratio at
     the same temperature; pressure_ratio = inf gives the paper's vacuum).
@@ -145,13 +146,13 @@ def slit(nx=400, ny=200, ppc=200, Kn=1e-2, dt_over_tauc=1.0, pressure_ratio=10.0
     The whole domain starts at the upstream state.  A counting plane at
     x = 0 gives the net particle flow through the slit (Eq. 41)."""
     a = 1.0e-5
-    lo, hi = (-10.0 * a, 0.0), (10.0 * a, 10.0 * a)
+    lo, hi = (-chamber * a, 0.0), (chamber * a, chamber * a)
     n_down = 0.0 if math.isinf(pressure_ratio) else N0 / pressure_ratio
     faces = [_face("reservoir", T0, (0, 0, 0), N0), _face("reservoir", T0, (0, 0, 0), n_down),
              _face("specular"), _face("diffuse")]
     w = _base(2, nx, ny, lo, hi, faces, Kn=Kn, L_ref=a, dt_over_tauc=dt_over_tauc, ppc=ppc, omega=0.5,
               precision=precision, steps=steps, seed=seed)
-    w["segments"] = [{"pos": 0.0, "lo": 0.5 * a, "hi": 10.0 * a, "kind": "diffuse", "T": T0,
+    w["segments"] = [{"pos": 0.0, "lo": 0.5 * a, "hi": chamber * a, "kind": "diffuse", "T": T0,
                       "u": (0.0, 0.0, 0.0)}]
     w["params"]["reservoir_cols"] = reservoir_cols
     w["params"]["flux_axis"] = 1
@@ -170,8 +171,10 @@ SLIT_CASES = {1: (580, 280, 0.2), 2: (580, 280, 1.0), 3: (580, 280, 2.0), 4: (28
               5: (160, 80, 4.0), 6: (160, 80, 5.0)}
 
 
-def slit_case(case=4, ppc=100, precision="fp32", steps=4000, seed=1, buffer_flights=3.0):
-    """A slit case of Table 7: delta = 20, vacuum downstream.
+def slit_case(case=4, ppc=100, precision="fp32", steps=4000, seed=1, buffer_flights=3.0, chamber=10.0):
+    """A slit case of Table 7: delta = 20, vacuum downstream.  `chamber` scales
+    the domain (half-length and height, in slit widths) at the case's cell
+    size (the printed cell counts are for chamber = 10).
 
     The reservoir buffer must be deeper than a particle flies in one step, or
     the particles that would enter from beyond it are missing and the
@@ -183,8 +186,10 @@ def slit_case(case=4, ppc=100, precision="fp32", steps=4000, seed=1, buffer_flig
     delta = 20.0
     dx_over_a = 20.0 / nx
     cols = max(2, math.ceil(buffer_flights * 0.8 * r / (delta * dx_over_a)))
-    return slit(nx=nx, ny=ny, ppc=ppc, dt_over_tauc=r, pressure_ratio=math.inf, precision=precision,
-                steps=steps, seed=seed, delta=delta, reservoir_cols=cols)
+    scale = chamber / 10.0
+    return slit(nx=int(round(nx * scale)), ny=int(round(ny * scale)), ppc=ppc, dt_over_tauc=r,
+                pressure_ratio=math.inf, precision=precision, steps=steps, seed=seed, delta=delta,
+                reservoir_cols=cols, chamber=chamber)
 
 
 def homogeneous_box(ppc=1000, Kn=0.05, dt_over_tauc=0.5, mode="usp", precision="fp64", Pr=PR_MONO,
