@@ -180,3 +180,45 @@ def test_couette_viscosity_independent_of_dt():
     assert abs(m - 1.0) < 4 * se + 0.04, (m, se)
     assert abs(m - 1.23) > 4 * se + 0.05, (m, se)
     assert max(counts) < 1.3 * n0 and min(counts) > n0, (n0, min(counts), max(counts))
+
+
+@pytest.mark.slow
+def test_thermal_couette_conductivity_independent_of_dt():
+    """Steady thermal Couette (plates at T0 -/+ 50 K, Kn = 0.01, 50 cells,
+    300 per cell, P_ne = 1, x = nu dt near 4): with the weighted particles
+    the sampled heat flux over kappa dT/dy (kappa = 15/4 k/m mu) is 1 -- the
+    moment balance of the heat flux, with Pr in Eq. 33 and in J, gives kappa
+    at every x -- where the split scheme gives (2/3) x / (1 - e^{-Pr x}) /
+    (1 + x Pr / 2) = 1.23."""
+    ny, ppc = 50, 300
+    w = W.couette(ny=ny, ppc=ppc, Kn=0.01, u_wall=0.0, dt_over_tauc=5.0, omega=0.81, seed=8)
+    w["faces"][2]["T"] = W.T0 + 50.0
+    w["faces"][3]["T"] = W.T0 - 50.0
+    w["params"].update(mode="fixed", fixed_pne=1.0, weighted=1, weight_average=1, n_avg=100)
+    o = oracle.OracleSim(w).init_particles()
+    n0 = o.n
+    H = w["grid"]["hi"][1]
+    y = (np.arange(ny) + 0.5) * H / ny
+    c = slice(int(0.2 * ny), int(0.8 * ny))
+    counts = []
+    for _ in range(15):
+        o.step(100)
+        counts.append(o.n)
+    ratios, xs = [], []
+    for _ in range(10):
+        acc = np.zeros((16, ny))
+        for _ in range(200):
+            o.step(1)
+            acc += o.fields()
+        counts.append(o.n)
+        xs.append(o.params()[c, 11].mean() * o.dt)
+        F = acc / 200
+        kappa = 15.0 / 4.0 * KB_M * o.mu_ref * (F[4][c].mean() / W.T0) ** 0.81
+        ratios.append(-F[12][c].mean() / (kappa * np.polyfit(y[c], F[4][c], 1)[0]))
+    m, se = _mean_se(ratios)
+    x = float(np.mean(xs))
+    split = (2.0 / 3.0) * x / (1.0 - math.exp(-PR * x)) / (1.0 + x * PR / 2.0)
+    assert 3.0 < x < 5.5, x
+    assert abs(m - 1.0) < 4 * se + 0.02, (m, se)
+    assert abs(m - split) > 4 * se + 0.05, (m, se, split)
+    assert max(counts) < 1.3 * n0 and min(counts) > n0, (n0, min(counts), max(counts))
