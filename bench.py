@@ -2,8 +2,8 @@
 """Benchmark of the USP-ESBGK particle update on GB300.
 
 Default workload: the Sod shock tube of Sec. 4.3 (1000 cells, 360 / 45
-particles per cell, Kn = 1e-4, dt = 10 tau_c, FP32 particles / FP64 per-cell
-moments), as a batch of B independent tubes (seeds 1..B) advanced together
+particles per cell, Kn = 1e-4, dt = 10 tau_c, FP32 particles, moment sums and
+per-cell parameters, FP64 field averages), as a batch of B independent tubes (seeds 1..B) advanced together
 by the graph-captured batched launches.  One bench step is one time step of
 every tube.  The particle state (B * 2.0e5 particles, two buffers) is larger
 than the 129 MB L2, so no flush is needed between steps.
@@ -33,7 +33,7 @@ FUSED_SRC = os.path.join(ROOT, "paper_1808_03801_gb300", "csrc", "usp_fused.cu")
 # dram__bytes_write.sum of the 32-tube Sod case divided by its particles),
 # valid only for the k_g2 source with this SHA-1; any other source reports
 # traffic as null until it is captured again
-KG2_TRAFFIC = {"sha1": "2c48bccaba59bdfd686da2453f4e684ce39a3e00", "bytes_per_particle": 39.22}
+KG2_TRAFFIC = {"sha1": "ff02524184d327f58c9e9088168eca304172b248", "bytes_per_particle": 39.14}
 
 
 def parse():
@@ -63,7 +63,7 @@ def parse():
 def workload_cfg(batch, pipeline):
     return {"workload": "sod_shock_tube_batch", "cells": 1000, "ppc_left": 360, "ppc_right": 45,
             "particles_per_tube": 202500, "global_batch": batch, "Kn": 1e-4, "dt_over_tauc": 10.0,
-            "storage": "fp32", "moments": "fp32 centred sums, fp64 per-cell parameters", "pipeline": pipeline,
+            "storage": "fp32", "moments": "fp32 centred sums and per-cell parameters, fp64 Eq. 34 averages", "pipeline": pipeline,
             "l2": "state larger than L2 (no flush)", "parallelism": "replicas"}
 
 

@@ -59,7 +59,7 @@ extern "C" {
 #define USP_MODE_SPESBGK 3   /* the SP-ESBGK step of Sec. 2 (Eq. 8b): the Gaussian target held at the
                                 post-convection state (no time instant, no Eq. 33 division) */
 
-/* relaxation selection and sampler (the SP-ESBGK ablations of Sec. 2; plain pipeline only) */
+/* relaxation selection and sampler (the SP-ESBGK ablations of Sec. 2; both pipelines) */
 #define USP_SELECT_BERNOULLI 0        /* each particle relaxes with probability 1 - exp(-nu_ES dt) */
 #define USP_SELECT_FIXED_COUNT 1      /* Eq. 9: the nearest integer to N_c (1 - exp(-nu_ES dt)) particles
                                          of the cell with the smallest selection words */
@@ -68,7 +68,8 @@ extern "C" {
 
 /* particle storage precision */
 #define USP_FP64 0       /* positions and velocities stored and streamed in FP64 */
-#define USP_FP32_MIXED 1 /* FP32 storage and per-particle math, FP64 per-cell sums and parameters */
+#define USP_FP32_MIXED 1 /* FP32 storage and per-particle math; plain pipeline: FP64 per-cell sums and
+                            parameters; fused: FP32 centred sums and parameters, FP64 field averages */
 
 /* step pipeline */
 #define USP_PIPE_PLAIN 0 /* one kernel per stage */
@@ -168,12 +169,30 @@ typedef struct {
  *                  state is empty has Kn_GLL = 0.  0 (default): from the
  *                  instantaneous moments of the step.
  *   selection, es_sampler: USP_SELECT_* and USP_SAMPLER_* (0, 0 = the
- *                  defaults); the others need the plain pipeline
- *                  (INVALID_ARG otherwise).  With the
- *                  Gallis-Torczynski sampler, usp_get_params slots 4-9 hold
+ *                  defaults).  With the Gallis-Torczynski sampler,
+ *                  usp_get_params slots 4-9 (plain pipeline) hold
  *                  B = ((1 - Pr)/(2 Pr)) sigma* / (rho theta) (xx, yy, zz, xy,
  *                  xz, yz; S = I - s B at the time instant of Eq. 32)
- *                  instead of the Cholesky factor. */
+ *                  instead of the Cholesky factor.  The fused pipeline takes
+ *                  the same N_s particles of Eq. 9 (the smallest selection
+ *                  words; ties go to the lower position in the cell's
+ *                  bucket, which the arrival order sets) and scales their
+ *                  time instants by the (N_s + 1)-th smallest word.
+ *   weighted     : 1 runs the full USP step of Table 2 with weighted added
+ *                  particles (steps 2, 4 and 7; Eqs. 22-28 and the third
+ *                  term of Eq. 27): per cell N_a = N_eff min(1, nu_ES dt) /
+ *                  r_p particles (rounded at random), Maxwellian, with the
+ *                  weights of Eq. 26 times r_p / min(1, nu_ES dt); Eq. 28
+ *                  keeps int(sum of the selected weights), rounded at random,
+ *                  of the selected particles (smallest selection words) at
+ *                  weight 1 and deletes the others.  Needs the plain FP64
+ *                  pipeline, one domain (no slabs, no batch), no reservoir
+ *                  face, the default selection and sampler (INVALID_ARG
+ *                  otherwise).  Every moment is W-weighted.
+ *   r_p          : the scale of Eq. 25 (> 0 when weighted; the paper's 10).
+ *   weight_average: 1 feeds the weights with Eq. 34 averages (n_avg) of the
+ *                  fields they are built from, the stress and heat flux
+ *                  started at zero (steady flows); 0: instantaneous. */
 typedef struct {
     double Kn, L_ref, n_ref;
     double dt, dt_over_tauc;
@@ -189,6 +208,9 @@ typedef struct {
     double flux_pos;
     int gll_average;
     int selection, es_sampler;
+    int weighted;
+    double r_p;
+    int weight_average;
 } usp_params;
 
 /* A box of initial gas at number density n, temperature T, velocity u. */
@@ -269,6 +291,13 @@ int usp_sample_macro(usp_handle* h, int which, double* out, size_t out_len, int 
  * the live count; CAPACITY if cap is too small. */
 int usp_get_particles(usp_handle* h, double* pos, double* vel, uint32_t* pid, int32_t* cell,
                       int64_t cap, int64_t* n_out);
+
+/* Particle weights W (Table 2; 1 for a particle of the initial state) of a
+ * handle created with params.weighted, in the storage order of
+ * usp_get_particles, into the HOST array w[cap].  *n_out receives the live
+ * count.  STATE for a handle without weights, INVALID_ARG if cap is too
+ * small. */
+int usp_get_weights(usp_handle* h, double* w, int64_t cap, int64_t* n_out);
 
 /* Debug / test: run one stage of the plain pipeline (same stage numbers as
  * the step order above: 0 advect, 1 reservoir refill, 2 sort, 3 moments,

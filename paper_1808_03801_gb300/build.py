@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libusp.so")
-SOURCES = ["usp_kernels.cu", "usp_fused.cu", "usp_api.cu", "usp_static.cu"]
+SOURCES = ["usp_kernels.cu", "usp_fused.cu", "usp_api.cu", "usp_static.cu", "usp_weighted.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 # the FP32 pipeline is compared statistically: approximate single-precision

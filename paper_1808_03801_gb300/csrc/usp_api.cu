@@ -182,7 +182,8 @@ static void enqueue_fused_step(const Launch& L, int R, bool reservoir) {
 }
 
 static void enqueue_any(usp_handle* h, const Launch& L) {
-    if (h->pipeline == USP_PIPE_FUSED) enqueue_fused_step(L, h->fused_R, h->host.has_reservoir != 0);
+    if (h->host.weighted) enqueue_weighted_step(L);
+    else if (h->pipeline == USP_PIPE_FUSED) enqueue_fused_step(L, h->fused_R, h->host.has_reservoir != 0);
     else enqueue_step(L, h->precision == USP_FP64, h->host.has_reservoir != 0);
 }
 
@@ -233,8 +234,17 @@ extern "C" int usp_create(const usp_gas* gas, const usp_grid* grid, const usp_bc
     if (prm->mode < 0 || prm->mode > 3) return USP_ERR_INVALID_ARG;
     if (prm->selection < 0 || prm->selection > 1 || prm->es_sampler < 0 || prm->es_sampler > 1)
         return USP_ERR_INVALID_ARG;
-    if ((prm->selection || prm->es_sampler) && prm->pipeline != USP_PIPE_PLAIN) return USP_ERR_INVALID_ARG;
     if (prm->precision != USP_FP64 && prm->precision != USP_FP32_MIXED) return USP_ERR_INVALID_ARG;
+    if (prm->weighted < 0 || prm->weighted > 1 || prm->weight_average < 0 || prm->weight_average > 1)
+        return USP_ERR_INVALID_ARG;
+    if (prm->weighted) {
+        // the weighted particles run on the plain FP64 pipeline, one domain,
+        // without reservoirs, with the default selection and sampler
+        if (prm->pipeline != USP_PIPE_PLAIN || prm->precision != USP_FP64 || !(prm->r_p > 0)) return USP_ERR_INVALID_ARG;
+        if (prm->selection || prm->es_sampler || prm->slab_count > 1) return USP_ERR_INVALID_ARG;
+        for (int f = 0; f < 4; ++f)
+            if (faces[f].kind == USP_BC_RESERVOIR) return USP_ERR_INVALID_ARG;
+    }
     if (prm->pipeline != USP_PIPE_PLAIN && prm->pipeline != USP_PIPE_FUSED) return USP_ERR_INVALID_ARG;
     if (prm->pipeline == USP_PIPE_FUSED && prm->precision != USP_FP32_MIXED) return USP_ERR_INVALID_ARG;
     if (prm->body_accel[1] != 0 || (grid->dim == 2 && prm->body_accel[0] != 0)) return USP_ERR_INVALID_ARG;
@@ -335,6 +345,9 @@ extern "C" int usp_create(const usp_gas* gas, const usp_grid* grid, const usp_bc
     s.gll_average = prm->gll_average != 0;
     s.selection = prm->selection;
     s.es_sampler = prm->es_sampler;
+    s.weighted = prm->weighted;
+    s.weight_average = prm->weight_average;
+    s.r_p = prm->weighted ? prm->r_p : 0.0;
     for (int d = 0; d < 3; ++d) s.body[d] = prm->body_accel[d];
     for (int f = 0; f < 4; ++f) {
         s.face[f].kind = faces[f].kind;
@@ -392,6 +405,15 @@ extern "C" int usp_create(const usp_gas* gas, const usp_grid* grid, const usp_bc
     CALLOC(inj_pidoff, uint32_t, K);
     CALLOC(fprm, float, (size_t)kNFPrm * K);
     if (prm->gll_average && prm->pipeline == USP_PIPE_PLAIN) { CALLOC(gavg, double, 3 * (size_t)K); }
+    if (prm->weighted) {
+        CALLOC(wneff, double, K);
+        CALLOC(wst, double, 9 * (size_t)K);
+        CALLOC(wfs, double, (size_t)kNWF * K);
+        CALLOC(wan, double, (size_t)kNWF * K);
+        CALLOC(was, double, (size_t)kNWF * K);
+        CALLOC(wna, uint32_t, K);
+        CALLOC(woff, uint32_t, K + 1);
+    }
     if (prm->pipeline == USP_PIPE_FUSED) {
         CALLOC(momf, float, 16 * (size_t)K);
         CALLOC(floc, float, 4 * (size_t)K);
@@ -467,6 +489,10 @@ extern "C" int usp_create(const usp_gas* gas, const usp_grid* grid, const usp_bc
 static int alloc_particles(usp_handle* h, int64_t n) {
     SimDev& s = h->host;
     double f = h->capacity_factor > 0 ? h->capacity_factor : (s.has_reservoir ? 2.0 : 1.25);
+    // weighted particles: the three stages of a step add up to 3 N / r_p
+    // before the deletions of Eq. 28, and the population settles up to
+    // ~20 % above its start
+    if (s.weighted) f = std::max(f, 1.5 * (1.0 + 3.0 / s.r_p));
     int64_t cap = (int64_t)std::ceil(n * f) + 2 * (int64_t)s.inj_total + 1024;
     if (h->pipeline == USP_PIPE_FUSED) {
         // slack buckets: about 1.25 x the largest neighbouring count + 16 per cell
@@ -500,6 +526,14 @@ static int alloc_particles(usp_handle* h, int64_t n) {
         }
     }
     s.cell = (uint32_t*)grab(4 * cap);
+    if (s.weighted) {
+        s.wgt[0] = (double*)grab(8 * cap);
+        s.wgt[1] = (double*)grab(8 * cap);
+        if (!s.wgt[0] || !s.wgt[1]) {
+            free_particles(h);
+            return fail(h, USP_ERR_OOM, "particle weight allocation failed");
+        }
+    }
     if (!s.cell) {
         free_particles(h);
         return fail(h, USP_ERR_OOM, "particle storage allocation failed");
@@ -542,6 +576,22 @@ static int reset_dynamic(usp_handle* h, uint32_t n, uint32_t next_pid) {
     CK(cudaMemsetAsync(h->host.inst, 0, sizeof(double) * kNFields * K, h->stream));
     CK(cudaMemsetAsync(h->host.avg, 0, sizeof(double) * kNFields * K, h->stream));
     CK(cudaMemsetAsync(h->host.prm, 0, sizeof(double) * kNPrm * K, h->stream));
+    return USP_OK;
+}
+
+// weighted particles: every loaded particle has weight 1, the parameters
+// (P_ne of the first step 2) and the weight-field averages start at zero
+static int weighted_setup(usp_handle* h) {
+    SimDev& s = h->host;
+    if (!s.weighted) return USP_OK;
+    const size_t K = (size_t)s.K;
+    CK(cudaMemsetAsync(s.prm, 0, sizeof(double) * kNPrm * K, h->stream));
+    CK(cudaMemsetAsync(s.wan, 0, sizeof(double) * kNWF * K, h->stream));
+    CK(cudaMemsetAsync(s.was, 0, sizeof(double) * kNWF * K, h->stream));
+    Launch L = make_launch(h);
+    launch_weighted_init(L);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(h->stream));
     return USP_OK;
 }
 
@@ -620,6 +670,7 @@ extern "C" int usp_init_particles(usp_handle* h, const usp_region* regions, int 
         CK(cudaGetLastError());
         CK(cudaStreamSynchronize(h->stream));
     }
+    if ((rc = weighted_setup(h)) != 0) return rc;
     h->initialised = true;
     h->mid_step = false;
     h->sorted = true;
@@ -688,6 +739,7 @@ extern "C" int usp_set_particles(usp_handle* h, int64_t n, const double* pos, co
     if ((rc = reset_dynamic(h, (uint32_t)n, next_pid)) != 0) return rc;
     CK(cudaStreamSynchronize(h->stream));
     if (h->pipeline == USP_PIPE_FUSED && (rc = fused_from_unsorted(h)) != 0) return rc;
+    if ((rc = weighted_setup(h)) != 0) return rc;
     h->initialised = true;
     h->mid_step = false;
     h->sorted = h->pipeline == USP_PIPE_FUSED;
@@ -762,6 +814,7 @@ static int stage_launch(const Launch& L, int pipeline, bool fp64, int R, bool re
 extern "C" int usp_run_stage(usp_handle* h, int stage) {
     if (!h) return USP_ERR_INVALID_ARG;
     if (!h->initialised) return fail(h, USP_ERR_STATE, "particles not initialised");
+    if (h->host.weighted) return fail(h, USP_ERR_STATE, "weighted particles step whole steps only");
     if (h->batch_refs) return fail(h, USP_ERR_STATE, "handle is admitted to a batch");
     if (h->host.slab_count > 1) return fail(h, USP_ERR_STATE, "a slab steps only in a batch with its neighbours");
     Launch L = make_launch(h);
@@ -952,6 +1005,18 @@ extern "C" int usp_get_params(usp_handle* h, double* out, size_t out_len) {
     return USP_OK;
 }
 
+extern "C" int usp_get_weights(usp_handle* h, double* w, int64_t cap, int64_t* n_out) {
+    if (!h || !w || !n_out) return USP_ERR_INVALID_ARG;
+    if (!h->host.weighted) return fail(h, USP_ERR_STATE, "the handle has no particle weights");
+    SimDyn d;
+    int rc = read_dyn(h, &d);
+    if (rc && rc != USP_ERR_CAPACITY) return rc;
+    if ((int64_t)d.n > cap) return fail(h, USP_ERR_INVALID_ARG, "output too small");
+    *n_out = d.n;
+    if (d.n) CK(cudaMemcpy(w, h->host.wgt[d.cur], sizeof(double) * d.n, cudaMemcpyDeviceToHost));
+    return USP_OK;
+}
+
 extern "C" int usp_get_info(usp_handle* h, usp_info* info) {
     if (!h || !info) return USP_ERR_INVALID_ARG;
     SimDyn d{};
@@ -1067,6 +1132,7 @@ extern "C" int usp_batch_info(usp_batch* b, int* n_sims, size_t* bytes) {
 extern "C" int usp_batch_admit(usp_batch* b, usp_handle* h) {
     if (!b || !h) return USP_ERR_INVALID_ARG;
     if (!h->initialised || h->mid_step) return bfail(b, USP_ERR_STATE, "handle not ready");
+    if (h->host.weighted) return bfail(b, USP_ERR_INVALID_ARG, "weighted particles step alone");
     for (auto* m : b->members)
         if (m == h) return bfail(b, USP_ERR_STATE, "already admitted");
     if ((int)b->members.size() >= b->max_sims) return bfail(b, USP_ERR_CAPACITY, "no free slot");

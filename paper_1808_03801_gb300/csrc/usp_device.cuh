@@ -281,13 +281,16 @@ __device__ __forceinline__ void local_state(const SimDev& s, int cell, Local& L,
     const int K = s.K;
     const double* M = s.mom;
     const int N = (int)M[cell];
+    // with weighted particles the sums are W-weighted and N_eff = sum W
+    // stands for N in the means and the density
+    const double we = s.weighted ? s.wneff[cell] : (double)N;
     L.N = N;
     L.valid = 0;
-    L.n = N * s.w;
+    L.n = we * s.w;
     L.u[0] = L.u[1] = L.u[2] = 0.0;
     L.theta = 0.0;
-    if (N < 1) return;
-    const double inv = 1.0 / N;
+    if (N < 1 || !(we > 0.0)) return;
+    const double inv = 1.0 / we;
     const double d0 = M[K + cell] * inv, d1 = M[2 * K + cell] * inv, d2 = M[3 * K + cell] * inv;
     L.u[0] = s.ushift[cell] + d0;
     L.u[1] = s.ushift[K + cell] + d1;
@@ -310,7 +313,7 @@ __device__ __forceinline__ void local_state(const SimDev& s, int cell, Local& L,
         Q3[1] = 0.5 * (t1 - d1 * tr - 2.0 * md1 + 2.0 * d1 * dd);
         Q3[2] = 0.5 * (t2 - d2 * tr - 2.0 * md2 + 2.0 * d2 * dd);
     }
-    L.valid = N >= 2 && L.theta > 0.0;
+    L.valid = N >= 2 && (!s.weighted || we > 1.0) && L.theta > 0.0;
     if (!L.valid) return;
     L.T = L.theta / s.R;
     L.umag = sqrt(L.u[0] * L.u[0] + L.u[1] * L.u[1] + L.u[2] * L.u[2]);

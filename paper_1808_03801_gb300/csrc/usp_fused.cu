@@ -14,18 +14,17 @@
 //             about the cell's mean velocity of the previous step, and the
 //             cell's n, T, |u| for its neighbours' Kn_GLL.
 //   k_params  per cell: Kn_GLL and P_ne (Eqs. 16-18), sigma* and q* (Eq. 33),
-//             the Cholesky factor of the ES covariance (Eq. 6c) in FP64, the
-//             fields and the average of Eq. 34.
+//             the Cholesky factor of the ES covariance (Eq. 6c), the fields
+//             and the average of Eq. 34.
 //   k_layout  per simulation: histogram -> bucket sizes -> exclusive scan,
 //             the layout that the next step writes with; then the end of
 //             the step (swap buffers, advance the step).
-// Per particle all arithmetic is FP32.  FP64 is used per cell in k_params_f
-// (one cell per thread): the promotion of the moment sums, the stress
-// tensor, Eq. 33 and the Cholesky factor.  FP64 issue rate is scarce on
-// GB300 and an FP64 instruction costs about as much for one lane as for a
-// whole warp, so the warp-per-cell kernels keep their per-cell arithmetic
-// in FP32: moments are sums about the previous step's cell mean and the
-// conservation factors use sums about the cell mean, so neither cancels.
+// All arithmetic of a step is FP32 except the number density and the Eq. 34
+// running averages (FP64, in k_params_f).  FP64 issue rate is scarce on
+// GB300 (about two FP64 FMA per clock per SM).  The moments are sums about
+// the previous step's cell mean and the conservation factors use sums about
+// the cell mean, so no subtraction cancels: the per-cell state, Eq. 33 and
+// the Cholesky factor lose nothing in FP32 that the FP32 sums still carry.
 // Each particle is read once and written once by k_g2 and its velocity is
 // read once more by k_g1.
 #include <algorithm>
@@ -169,6 +168,29 @@ __device__ __forceinline__ void es_draw1(const FCell& f, const TimeDraw& td, flo
     C[0] = l00 * z0;
     C[1] = l10 * z0 + l11 * z1;
     C[2] = l20 * z0 + l21 * z1 + l22 * z2;
+}
+
+// The Gallis-Torczynski draw (Eqs. 10-11) of the SP-ESBGK ablations: a
+// thermal velocity sqrt(theta) z, with z three independent normals drawn as
+// in es_draw1, transformed by S = I - s B, B = ((1 - Pr)/(2 Pr)) sigma* /
+// (rho theta) (symmetric; f.M holds its lower triangle) and s of Eq. 32 at
+// the time instant.
+__device__ __forceinline__ void es_draw_gt(const FCell& f, const TimeDraw& td, float u, const uint4& w, float* C) {
+    const float U1 = fminf(u * td.inv_pr, 1.0f);
+    const float t = td.a < 1.0f ? __logf(1.0f + U1 * td.em1) * td.inv_nues
+                                : td.dt + __logf(U1 + (1.0f - U1) * td.ema) * td.inv_nues;
+    const float sf = f.pne + (1.0f - f.pne) * __expf(-f.nu * t);          // Eq. 32
+    float z0, z1;
+    box_muller<float>(w.y, w.z, z0, z1);
+    const uint32_t lo = (w.x & 511u) | ((w.y & 511u) << 9) | ((w.z & 31u) << 18);
+    const float r2 = sqrtf(-1.3862943611198906f * __log2f(u01<float>(w.w)));
+    const float z2 = r2 * __cosf(6.283185307179586f * (((float)lo + 0.5f) * 1.1920928955078125e-7f) - 3.14159265358979f);
+    const float st = sqrtf(f.th);
+    const float c0 = st * z0, c1 = st * z1, c2 = st * z2;
+    const float b00 = f.M[0], b10 = f.M[1], b11 = f.M[2], b20 = f.M[3], b21 = f.M[4], b22 = f.M[5];
+    C[0] = c0 - sf * (b00 * c0 + b10 * c1 + b20 * c2);
+    C[1] = c1 - sf * (b10 * c0 + b11 * c1 + b21 * c2);
+    C[2] = c2 - sf * (b20 * c0 + b21 * c1 + b22 * c2);
 }
 
 // ---------------------------------------------------------------------------
@@ -723,6 +745,185 @@ __device__ __forceinline__ void g2_relax(const float* prm, const SimDev& s, cons
     __syncwarp();
 }
 
+// Eq. 9 fixed count for one cell: the ns = nearest-int(n P_relax) particles
+// with the smallest selection words w.x (ties: lower staged position).  T is
+// the ns-th smallest word and `quota` the number of particles with word T
+// that are taken; the (ns+1)-th smallest word T2 scales the time instants
+// (given T2, the ns smallest words are independent and uniform below it).
+struct G2Fixed {
+    uint32_t T, quota, ties, ns;
+    float inv_thr;
+};
+
+// the words of the staged particles [0, cnt) one chunk at a time: the
+// radix select of the ns-th smallest (four passes of 8-bit digits counted
+// in the warp's window array), then the ties and T2.  Cells above the
+// ring allocation reload each chunk in every pass.
+template <int DIM>
+__device__ __noinline__ G2Fixed g2_fixed(const SimDev& s, const G2Desc& D, const G2Stage& S, uint32_t n,
+                                          const uint32_t* spl, uint32_t* hist, int lane) {
+    const int p = (D.flags & kDescParity) ? 1 : 0;
+    const uint32_t m = D.m, nch = (n + m - 1) / m;
+    const uint2 key = make_uint2(s.key0, s.key1);
+    G2Fixed F;
+    F.ns = (uint32_t)floorf((float)n * D.prm[10] + 0.5f);
+    F.ns = min(F.ns, n);
+    F.ties = 0;
+    F.T = 0xFFFFFFFFu;
+    F.quota = 0;
+    F.inv_thr = 1.0f;
+    if (F.ns == 0) return F;
+    uint32_t prefix = 0, mask = 0, rem = F.ns;
+    for (int shift = 24; shift >= 0; shift -= 8) {
+        for (int b = lane; b < 256; b += 32) hist[b] = 0u;
+        __syncwarp();
+        for (uint32_t ch = 0; ch < nch; ++ch) {
+            const uint32_t cnt = min(m, n - ch * m);
+            if (nch > 1) g2_load<DIM>(s, S, p, D.base, D.nb, spl, ch * m, cnt, false, lane);
+            for (uint32_t j = lane; j < cnt; j += 32) {
+                const uint32_t k = philox(make_uint4(S.id[j], D.step, kRelax, 0), key).x;
+                if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], 1u);
+            }
+            __syncwarp();
+        }
+        // lane l holds digits [8l, 8l + 8): the digit where the running count reaches rem
+        uint32_t h[8], tot = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            h[i] = hist[8 * lane + i];
+            tot += h[i];
+        }
+        uint32_t inc = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        const uint32_t exc = inc - tot;
+        const unsigned own = __ballot_sync(0xffffffffu, exc < rem && rem <= inc);
+        const int L = __ffs(own) - 1;
+        uint32_t d = 0, below = exc;
+        if (lane == L) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                if (below + h[i] >= rem) {
+                    d = 8u * lane + i;
+                    break;
+                }
+                below += h[i];
+            }
+        }
+        d = __shfl_sync(0xffffffffu, d, L);
+        below = __shfl_sync(0xffffffffu, below, L);
+        rem -= below;
+        prefix |= d << shift;
+        mask |= 0xFFu << shift;
+        __syncwarp();
+    }
+    F.T = prefix;
+    F.quota = rem;
+    // words equal to T, and the smallest word above it
+    uint32_t eq = 0, above = 0xFFFFFFFFu;
+    bool any_above = false;
+    for (uint32_t ch = 0; ch < nch; ++ch) {
+        const uint32_t cnt = min(m, n - ch * m);
+        if (nch > 1) g2_load<DIM>(s, S, p, D.base, D.nb, spl, ch * m, cnt, false, lane);
+        for (uint32_t j = lane; j < cnt; j += 32) {
+            const uint32_t k = philox(make_uint4(S.id[j], D.step, kRelax, 0), key).x;
+            eq += k == F.T;
+            if (k > F.T) {
+                any_above = true;
+                above = min(above, k);
+            }
+        }
+    }
+    eq = __reduce_add_sync(0xffffffffu, eq);
+    above = __reduce_min_sync(0xffffffffu, above);
+    any_above = __any_sync(0xffffffffu, any_above);
+    uint32_t T2 = 0;
+    bool has2 = true;
+    if (eq > F.quota) T2 = F.T;
+    else if (any_above) T2 = above;
+    else has2 = false;
+    F.inv_thr = has2 ? 1.0f / u01<float>(T2) : 1.0f;
+    return F;
+}
+
+// Relaxation draws of the SP-ESBGK ablations (same contract as g2_relax):
+// the Bernoulli or fixed-count selection (Eq. 9), the ES Cholesky or
+// Gallis-Torczynski sampler (Eqs. 10-11).  The loop is warp-uniform so
+// that the ties of the fixed count are ranked by position with ballots.
+template <bool SUMS>
+__device__ __forceinline__ void g2_relax_abl(const float* prm, const SimDev& s, const G2Stage& S, uint32_t cnt,
+                                             uint32_t step, bool relax, int lane, G2Sums& R, G2Fixed& X) {
+    FCell f;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) f.u[d] = prm[d];
+    f.th = prm[3];
+    const bool gt = s.es_sampler != 0, fixed = s.selection != 0;
+    if (gt) {   // B of Eq. 11 (lower triangle)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) f.M[k] = prm[4 + k];
+    } else {
+        const float L0 = prm[4], L1 = prm[5], L2 = prm[6], L3 = prm[7], L4 = prm[8], L5 = prm[9];
+        f.M[0] = L0 * L0 - f.th;
+        f.M[1] = L1 * L0;
+        f.M[2] = L1 * L1 + L2 * L2 - f.th;
+        f.M[3] = L3 * L0;
+        f.M[4] = L3 * L1 + L4 * L2;
+        f.M[5] = L3 * L3 + L4 * L4 + L5 * L5 - f.th;
+    }
+    f.pr = prm[10];
+    f.nu = prm[11];
+    f.nues = prm[12];
+    f.pne = prm[13];
+    TimeDraw td;
+    td.dt = s.f_dt;
+    td.a = f.nues * td.dt;
+    td.em1 = expm1f(td.a);
+    td.ema = __expf(-td.a);
+    td.inv_nues = 1.0f / f.nues;
+    td.inv_pr = fixed ? X.inv_thr : (f.pr > 0.0f ? 1.0f / f.pr : 0.0f);
+    const uint2 key = make_uint2(s.key0, s.key1);
+    const unsigned lt = lanemask_lt();
+#pragma unroll 1
+    for (uint32_t b = 0; b < cnt; b += 32) {
+        const uint32_t j = b + lane;
+        const bool has = j < cnt;
+        bool sel = false;
+        uint4 w = make_uint4(0u, 0u, 0u, 0u);
+        if (relax) {
+            w = philox(make_uint4(has ? S.id[j] : 0u, step, kRelax, 0), key);
+            if (fixed) {
+                const bool tie = has && w.x == X.T;
+                const unsigned tb = __ballot_sync(0xffffffffu, tie);
+                const uint32_t rank = X.ties + (uint32_t)__popc(tb & lt);
+                X.ties += (uint32_t)__popc(tb);
+                sel = has && X.ns > 0 && (w.x < X.T || (tie && rank < X.quota));
+            } else {
+                sel = has && u01<float>(w.x) < f.pr;
+            }
+            if (sel) {
+                float C[3];
+                const float u = u01<float>(w.x);
+                if (gt) es_draw_gt(f, td, u, w, C);
+                else es_draw1(f, td, u, w, C);
+                if (SUMS) {
+                    const float o0 = S.v0[j] - f.u[0], o1 = S.v1[j] - f.u[1], o2 = S.v2[j] - f.u[2];
+                    R.a0 += o0; R.a1 += o1; R.a2 += o2;
+                    R.ae += o0 * o0 + o1 * o1 + o2 * o2;
+                    R.b0 += C[0]; R.b1 += C[1]; R.b2 += C[2];
+                    R.be += C[0] * C[0] + C[1] * C[1] + C[2] * C[2];
+                    R.nr += 1.0f;
+                }
+                S.v0[j] = C[0]; S.v1[j] = C[1]; S.v2[j] = C[2];
+            }
+        }
+        if (has) S.sel[j] = sel ? 1 : 0;
+    }
+    __syncwarp();
+}
+
 // conservation factors of the cell from the warp's partial sums
 __device__ __forceinline__ G2Cons g2_factors(const float* prm, G2Sums R, bool relax, G2Acc& acc) {
     G2Cons K;
@@ -900,18 +1101,24 @@ __device__ __noinline__ void g2_cell_chunked(const SimDev* __restrict__ sims, co
                                              uint32_t* win, int lane, G2Acc& acc) {
     const int p = (D.flags & kDescParity) ? 1 : 0;
     const uint32_t m = D.m, nch = (n + m - 1) / m;
+    const bool abl = s.selection | s.es_sampler;
+    G2Fixed X = {0u, 0u, 0u, 0u, 1.0f};
+    if (relax && s.selection) X = g2_fixed<DIM>(s, D, S, n, spl, win, lane);
     G2Sums R = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (uint32_t ch = 0; ch < nch; ++ch) {
         const uint32_t cnt = min(m, n - ch * m);
         g2_load<DIM>(s, S, p, D.base, D.nb, spl, ch * m, cnt, false, lane);
-        g2_relax<true>(D.prm, s, S, cnt, D.step, relax, lane, R);
+        if (abl) g2_relax_abl<true>(D.prm, s, S, cnt, D.step, relax, lane, R, X);
+        else g2_relax<true>(D.prm, s, S, cnt, D.step, relax, lane, R);
     }
     const G2Cons K = g2_factors(D.prm, R, relax, acc);
     uint32_t removed = 0;
+    X.ties = 0;
     for (uint32_t ch = 0; ch < nch; ++ch) {
         const uint32_t cnt = min(m, n - ch * m);
         g2_load<DIM>(s, S, p, D.base, D.nb, spl, ch * m, cnt, false, lane);
-        g2_relax<false>(D.prm, s, S, cnt, D.step, relax, lane, R);
+        if (abl) g2_relax_abl<false>(D.prm, s, S, cnt, D.step, relax, lane, R, X);
+        else g2_relax<false>(D.prm, s, S, cnt, D.step, relax, lane, R);
         if (MODE == kRelaxOnly) g2_store_relaxed<DIM>(s, S, K, p, D.base, D.nb, spl, ch * m, cnt, lane);
         else g2_move<DIM, MODE>(sims, s, S, K, D.cell, p, D.base, D.nb, spl, ch * m, cnt, D.step, win, lane, removed);
     }
@@ -935,7 +1142,13 @@ __device__ __forceinline__ void g2_cell(const SimDev* __restrict__ sims, const S
     }
     g2_load<DIM>(s, S, p, D.base, D.nb, spl, 0u, n, (D.flags & kDescBulk) != 0, lane);
     G2Sums R = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    g2_relax<true>(D.prm, s, S, n, D.step, relax, lane, R);
+    if (s.selection | s.es_sampler) {   // the SP-ESBGK ablations
+        G2Fixed X = {0u, 0u, 0u, 0u, 1.0f};
+        if (relax && s.selection) X = g2_fixed<DIM>(s, D, S, n, spl, win, lane);
+        g2_relax_abl<true>(D.prm, s, S, n, D.step, relax, lane, R, X);
+    } else {
+        g2_relax<true>(D.prm, s, S, n, D.step, relax, lane, R);
+    }
     const G2Cons K = g2_factors(D.prm, R, relax, acc);
     if (MODE == kRelaxOnly) {
         g2_store_relaxed<DIM>(s, S, K, p, D.base, D.nb, spl, 0u, n, lane);
@@ -1342,35 +1555,35 @@ struct LocalF {
     float n, T, umag;
 };
 
-// promotion of the cell's FP32 shifted sums: mean velocity, pressure tensor
-// per unit density (P / rho) and theta = R T; inv = 1 / N
-__device__ __forceinline__ void local_f(const SimDev& s, int cell, LocalF& L, double* u, double* P, double* theta,
-                                        double& inv) {
-    const float* M = s.momf + (size_t)cell * 16;   // N, 12 sums, shift[3]
+// the cell's state from its FP32 shifted sums: mean velocity, pressure
+// tensor per unit density (P / rho) and theta = R T; inv = 1 / N.  The sums
+// are about the previous mean, so the subtractions below do not cancel and
+// FP32 keeps the accuracy the FP32 sums carry.
+__device__ __forceinline__ void local_f(const SimDev& s, const float* M, LocalF& L, float* u, float* P, float* theta,
+                                        float& inv) {
     const int N = (int)M[0];
     L.N = N;
     L.valid = 0;
-    L.n = (float)(N * s.w);
+    L.n = (float)N * s.f_w;
     L.T = 0;
     L.umag = 0;
-    inv = 0.0;
+    inv = 0.0f;
     if (N < 1) return;
-    inv = 1.0 / N;
-    const double d0 = M[1] * inv, d1 = M[2] * inv, d2 = M[3] * inv;
-    const double uu[3] = {M[13] + d0, M[14] + d1, M[15] + d2};
-    const double p0 = M[4] * inv - d0 * d0, p1 = M[5] * inv - d1 * d1,
-                 p2 = M[6] * inv - d2 * d2;
-    const double th = (p0 + p1 + p2) * (1.0 / 3.0);
-    u[0] = uu[0]; u[1] = uu[1]; u[2] = uu[2];
-    P[0] = p0; P[1] = p1; P[2] = p2;
+    inv = 1.0f / (float)N;
+    const float d0 = M[1] * inv, d1 = M[2] * inv, d2 = M[3] * inv;
+    u[0] = M[13] + d0; u[1] = M[14] + d1; u[2] = M[15] + d2;
+    P[0] = M[4] * inv - d0 * d0;
+    P[1] = M[5] * inv - d1 * d1;
+    P[2] = M[6] * inv - d2 * d2;
     P[3] = M[7] * inv - d0 * d1;
     P[4] = M[8] * inv - d0 * d2;
     P[5] = M[9] * inv - d1 * d2;
+    const float th = (P[0] + P[1] + P[2]) * (1.0f / 3.0f);
     *theta = th;
-    L.valid = N >= 2 && th > 0.0;
+    L.valid = N >= 2 && th > 0.0f;
     if (!L.valid) return;
-    L.T = (float)(th * s.inv_R);
-    L.umag = sqrtf((float)(uu[0] * uu[0] + uu[1] * uu[1] + uu[2] * uu[2]));
+    L.T = th * s.f_inv_R;
+    L.umag = sqrtf(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
 }
 
 // neighbour state for the Kn_GLL stencil, written in FP32 by k_g1
@@ -1446,21 +1659,22 @@ __global__ void __launch_bounds__(128) k_params_f(const SimDev* __restrict__ sim
                 }
             }
             LocalF L;
-            double u[3] = {0, 0, 0}, P[6], th = 0, inv;
-            local_f(s, cell, L, u, P, &th, inv);
-            double f[kNFields];
-            for (int k = 0; k < kNFields; ++k) f[k] = 0.0;
-            f[0] = L.N * s.w;
-            f[15] = L.N;
+            const float* M = s.momf + (size_t)cell * 16;   // N, 12 sums, shift[3]
+            float u[3] = {0, 0, 0}, P[6], th = 0, inv;
+            local_f(s, M, L, u, P, &th, inv);
+            float f[kNFields];
+            for (int k = 0; k < kNFields; ++k) f[k] = 0.0f;
+            f[0] = L.n;
+            f[15] = (float)L.N;
             if (L.N >= 1) {
                 f[1] = u[0]; f[2] = u[1]; f[3] = u[2];
             }
             float pr[kNFPrm];
             for (int k = 0; k < kNFPrm; ++k) pr[k] = 0.0f;
-            pr[0] = (float)u[0]; pr[1] = (float)u[1]; pr[2] = (float)u[2];
-            pr[3] = (float)th;
+            pr[0] = u[0]; pr[1] = u[1]; pr[2] = u[2];
+            pr[3] = th;
             if (L.valid) {
-                const float thf = (float)th;
+                const float thf = th;
                 const float rho = L.n * (float)s.mass;
                 const float pf = rho * thf;
                 const float mu = (float)s.mu_ref * __powf(L.T / (float)s.T_ref, (float)s.omega);   // Eq. 35
@@ -1512,44 +1726,49 @@ __global__ void __launch_bounds__(128) k_params_f(const SimDev* __restrict__ sim
                     const float kn = gvalid ? glam * sqrtf(fmaxf(g2[0], fmaxf(g2[1], g2[2]))) : 0.0f;
                     pne = __expf(-kn / (float)kKnC);                                              // Eqs. 16-18
                 }
-                // Eq. 33; FP64 divisions are costly here, so each factor is
-                // inverted once
-                const double ifs = 1.0 / (1.0 + 0.5 * s.dt * (double)nu * pne);
-                const double ifq = 1.0 / (1.0 + 0.5 * s.dt * (double)nu * s.Pr * pne);
-                const double sig[6] = {(P[0] - th) * ifs, (P[1] - th) * ifs, (P[2] - th) * ifs, P[3] * ifs, P[4] * ifs,
-                                       P[5] * ifs};
-                const double b = s.es_b;                                                        // Eq. 6c
-                const double A00 = th + b * sig[0], A11 = th + b * sig[1], A22 = th + b * sig[2];
-                const double A10 = b * sig[3], A20 = b * sig[4], A21 = b * sig[5];
-                // Cholesky factor with reciprocal square roots (no FP64 divisions)
-                double l00 = 0, l10 = 0, l11 = 0, l20 = 0, l21 = 0, l22 = 0;
-                bool ok = A00 > 0.0;
-                if (ok) {
-                    const double r0 = rsqrt(A00);
+                // Eq. 33
+                const float ifs = 1.0f / (1.0f + 0.5f * s.f_dt * nu * pne);
+                const float ifq = 1.0f / (1.0f + 0.5f * s.f_dt * nu * (float)s.Pr * pne);
+                const float sig[6] = {(P[0] - th) * ifs, (P[1] - th) * ifs, (P[2] - th) * ifs, P[3] * ifs, P[4] * ifs,
+                                      P[5] * ifs};
+                const float b = (float)s.es_b;                                                  // Eq. 6c
+                const float A00 = th + b * sig[0], A11 = th + b * sig[1], A22 = th + b * sig[2];
+                const float A10 = b * sig[3], A20 = b * sig[4], A21 = b * sig[5];
+                float l00 = 0, l10 = 0, l11 = 0, l20 = 0, l21 = 0, l22 = 0;
+                bool ok = A00 > 0.0f;
+                if (s.es_sampler) {
+                    // Gallis-Torczynski (Eq. 11): B = ((1 - Pr)/(2 Pr)) sigma* / (rho theta)
+                    // in the factor's slots, lower triangle row-major
+                    const float beta = (1.0f - (float)s.Pr) / (2.0f * (float)s.Pr * th);
+                    l00 = beta * sig[0]; l10 = beta * sig[3]; l11 = beta * sig[1];
+                    l20 = beta * sig[4]; l21 = beta * sig[5]; l22 = beta * sig[2];
+                    ok = true;
+                } else if (ok) {
+                    const float r0 = rsqrtf(A00);
                     l00 = A00 * r0;
                     l10 = A10 * r0;
                     l20 = A20 * r0;
-                    const double d1 = A11 - l10 * l10;
-                    ok = d1 > 0.0;
+                    const float d1 = A11 - l10 * l10;
+                    ok = d1 > 0.0f;
                     if (ok) {
-                        const double r1 = rsqrt(d1);
+                        const float r1 = rsqrtf(d1);
                         l11 = d1 * r1;
                         l21 = (A21 - l20 * l10) * r1;
-                        const double d2 = A22 - l20 * l20 - l21 * l21;
-                        ok = d2 > 0.0;
-                        if (ok) l22 = d2 * rsqrt(d2);
+                        const float d2 = A22 - l20 * l20 - l21 * l21;
+                        ok = d2 > 0.0f;
+                        if (ok) l22 = d2 * rsqrtf(d2);
                     }
                 }
                 if (!ok) {
-                    const double r = sqrt(th);
+                    const float r = sqrtf(th);
                     l00 = l11 = l22 = r;
-                    l10 = l20 = l21 = 0.0;
+                    l10 = l20 = l21 = 0.0f;
                     atomicAdd(&s.dyn->counters[kCntChol], 1ull);
                 }
                 const float nues = (float)s.Pr * nu;
-                pr[4] = (float)l00; pr[5] = (float)l10; pr[6] = (float)l11;
-                pr[7] = (float)l20; pr[8] = (float)l21; pr[9] = (float)l22;
-                pr[10] = -expm1f(-nues * (float)s.dt);                                        // Eqs. 8b, 9
+                pr[4] = l00; pr[5] = l10; pr[6] = l11;
+                pr[7] = l20; pr[8] = l21; pr[9] = l22;
+                pr[10] = -expm1f(-nues * s.f_dt);                                             // Eqs. 8b, 9
                 // the decay rate of Eq. 32; the SP-ESBGK step holds its target
                 // for the whole step (Eq. 8b): with P_ne = 0 a rate of 0 gives s = 1
                 pr[11] = s.mode == kModeSPESBGK ? 0.0f : nu;
@@ -1557,17 +1776,16 @@ __global__ void __launch_bounds__(128) k_params_f(const SimDev* __restrict__ sim
                 pr[13] = pne;
                 pr[14] = 1.0f;
                 // heat flux from the third central moment of the shifted sums
-                const float* M = s.momf + (size_t)cell * 16;
-                const double d0 = M[1] * inv, d1 = M[2] * inv, d2 = M[3] * inv;
-                const double m00 = M[4] * inv, m11 = M[5] * inv, m22 = M[6] * inv;
-                const double m01 = M[7] * inv, m02 = M[8] * inv, m12 = M[9] * inv;
-                const double t0 = M[10] * inv, t1 = M[11] * inv, t2 = M[12] * inv;
-                const double tr = m00 + m11 + m22, dd = d0 * d0 + d1 * d1 + d2 * d2;
-                const double Q0 = 0.5 * (t0 - d0 * tr - 2.0 * (m00 * d0 + m01 * d1 + m02 * d2) + 2.0 * d0 * dd);
-                const double Q1 = 0.5 * (t1 - d1 * tr - 2.0 * (m01 * d0 + m11 * d1 + m12 * d2) + 2.0 * d1 * dd);
-                const double Q2 = 0.5 * (t2 - d2 * tr - 2.0 * (m02 * d0 + m12 * d1 + m22 * d2) + 2.0 * d2 * dd);
-                const double rhod = L.N * s.w * s.mass, pd = rhod * th;
-                f[4] = th * s.inv_R;
+                const float d0 = M[1] * inv, d1 = M[2] * inv, d2 = M[3] * inv;
+                const float m00 = M[4] * inv, m11 = M[5] * inv, m22 = M[6] * inv;
+                const float m01 = M[7] * inv, m02 = M[8] * inv, m12 = M[9] * inv;
+                const float t0 = M[10] * inv, t1 = M[11] * inv, t2 = M[12] * inv;
+                const float tr = m00 + m11 + m22, dd = d0 * d0 + d1 * d1 + d2 * d2;
+                const float Q0 = 0.5f * (t0 - d0 * tr - 2.0f * (m00 * d0 + m01 * d1 + m02 * d2) + 2.0f * d0 * dd);
+                const float Q1 = 0.5f * (t1 - d1 * tr - 2.0f * (m01 * d0 + m11 * d1 + m12 * d2) + 2.0f * d1 * dd);
+                const float Q2 = 0.5f * (t2 - d2 * tr - 2.0f * (m02 * d0 + m12 * d1 + m22 * d2) + 2.0f * d2 * dd);
+                const float rhod = rho, pd = pf;
+                f[4] = L.T;
                 f[5] = pd + rhod * sig[0];
                 f[6] = pd + rhod * sig[1];
                 f[7] = pd + rhod * sig[2];
@@ -1584,10 +1802,14 @@ __global__ void __launch_bounds__(128) k_params_f(const SimDev* __restrict__ sim
 #pragma unroll
                 for (int k = 0; k < kNFPrm / 4; ++k) dst[k] = make_float4(pr[4 * k], pr[4 * k + 1], pr[4 * k + 2], pr[4 * k + 3]);
             }
+            // the number density in FP64 (N w exactly as the FP64 paths form
+            // it: a closed box keeps its domain total to the last bit)
+            const double n_d = (double)L.N * s.w;
 #pragma unroll
             for (int k = 0; k < kNFields; ++k) {
-                s.inst[(size_t)k * K + cell] = f[k];
-                s.avg[(size_t)k * K + cell] = first ? f[k] : s.avg_keep * av[k] + f[k] * s.avg_new;   // Eq. 34
+                const double fk = k == 0 ? n_d : (double)f[k];
+                s.inst[(size_t)k * K + cell] = fk;
+                s.avg[(size_t)k * K + cell] = first ? fk : s.avg_keep * av[k] + fk * s.avg_new;   // Eq. 34, FP64
             }
         }
     }

@@ -17,7 +17,7 @@ constexpr double kKnC = 0.1;                    // Kn_c of Eq. 16
 constexpr double kGammaMono = 5.0 / 3.0;
 
 // Philox purposes (third counter word); the first two words are (pid, step).
-enum : uint32_t { kInit = 0, kRelax = 1, kWall = 2, kInject = 3 };
+enum : uint32_t { kInit = 0, kRelax = 1, kWall = 2, kInject = 3, kAdd = 4, kCellDraw = 5 };
 enum { kBcDiffuse = 0, kBcSpecular = 1, kBcPeriodic = 2, kBcReservoir = 3 };
 enum { kModeUSP = 0, kModeSP = 1, kModeFixed = 2, kModeSPESBGK = 3 };
 
@@ -50,6 +50,8 @@ struct SimDyn {
     uint32_t sp_n[2];   // fused pipeline: entries in the spill lists
     uint32_t qnext;     // fused pipeline: next cell handed out by k_g2 (zero between launches)
     uint32_t lay_dst;   // fused pipeline: buffer whose bucket layout the layout kernels build
+    uint32_t w_started; // weighted particles: bit 0 / 1, the step-2 / step-4,7 weight-field averages exist
+    uint32_t w_added;   // weighted particles: particles added by the current stage
     unsigned long long counters[8];
 };
 
@@ -113,8 +115,24 @@ struct alignas(16) SimDev {
     float* fprm;          // [K][kNFPrm] relaxation parameters in FP32 (one 64-byte record per cell)
     float* momf;          // [K][16]: N, 12 sums of C = c - u_s, the shift u_s[3]  (fused moments)
     float* floc;          // [K][4]: n, T, |u|, valid of each cell for the Kn_GLL stencil
+    // weighted added particles (Table 2 steps 2, 4, 7; plain FP64 pipeline)
+    int weighted, weight_average;
+    double r_p;           // scale of Eq. 25
+    double* wgt[2];       // particle weights per buffer
+    double* wneff;        // K: sum of the weights in each cell (N_eff)
+    double* wst;          // 9 x K: sigma* (6) and q* (3) per unit density (Eq. 33)
+    double* wfs;          // kNWF x K: the weight fields of steps 4 and 7 as used
+    double* wan;          // kNWF x K: Eq. 34 average of the step-2 weight fields
+    double* was;          // kNWF x K: Eq. 34 average of the step-4/7 weight fields
+    uint32_t* wna;        // K: particles added to each cell by the current stage
+    uint32_t* woff;       // K + 1: their exclusive offsets
     SimDyn* dyn;
 };
+
+// fields behind the weights of Eq. 26: u[3], theta, sigma[6] and q[3] per
+// unit density, nu, and the stage's pref (r_p / min(1, nu_ES dt)) and P_ne
+constexpr int kNWF = 16;
+enum { kWFU = 0, kWFTh = 3, kWFSig = 4, kWFQ = 10, kWFNu = 13, kWFPref = 14, kWFPne = 15 };
 
 // copy one simulation descriptor into shared memory (whole block)
 __device__ __forceinline__ void load_sim(SimDev& dst, const SimDev& src) {
@@ -212,10 +230,13 @@ constexpr int kNFPrm = 16;       // u[3], theta, L[6], P_relax, nu, nu_ES, P_ne,
 constexpr int kLayTile = 1024;   // cells per block of the layout kernels (fused pipeline)
 
 void launch_stream(const Launch& L, bool fp64);
+void enqueue_weighted_step(const Launch& L);
 void launch_scan(const Launch& L, bool with_inj = true);
 void launch_scatter(const Launch& L, bool fp64);
 void launch_inject(const Launch& L, bool fp64);
 void launch_moments(const Launch& L, bool fp64);
+void launch_moments_src(const Launch& L, bool fp64, bool src_cur);
+void launch_weighted_init(const Launch& L);
 void launch_params(const Launch& L);
 void launch_relax(const Launch& L, bool fp64);
 void launch_finish(const Launch& L);

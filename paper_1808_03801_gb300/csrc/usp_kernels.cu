@@ -234,9 +234,12 @@ __global__ void __launch_bounds__(256) k_inject(const SimDev* __restrict__ sims,
 // ---------------------------------------------------------------------------
 // K5: per-cell sums of velocities shifted by the previous cell mean (Eq. 1)
 // ---------------------------------------------------------------------------
+// src_cur: the sums of the current buffer (the weighted step's moments of
+// f^n) instead of the sorted one; with weighted particles every sum is
+// W-weighted and the cell's weight sum goes to wneff
 template <class T>
 __global__ void __launch_bounds__(256) k_moments(const SimDev* __restrict__ sims, const int2* __restrict__ tiles,
-                                                 const int* __restrict__ ntiles) {
+                                                 const int* __restrict__ ntiles, int src_cur) {
     __shared__ SimDev sim_sh;
     const int nt = *ntiles;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -247,7 +250,9 @@ __global__ void __launch_bounds__(256) k_moments(const SimDev* __restrict__ sims
         __syncthreads();
         const SimDev& s = sim_sh;
         const int K = s.K;
-        PView<T> B = view<T>(s, s.dyn->cur ^ 1);
+        const int buf = src_cur ? s.dyn->cur : s.dyn->cur ^ 1;
+        PView<T> B = view<T>(s, buf);
+        const double* Wt = s.weighted ? s.wgt[buf] : nullptr;
         if (tile.y == 0 && threadIdx.x == 0) s.fill[K] = 0;
         for (int cc = warp; cc < kCTile; cc += nwarps) {
             const int cell = tile.y + cc;
@@ -255,12 +260,21 @@ __global__ void __launch_bounds__(256) k_moments(const SimDev* __restrict__ sims
             const uint32_t cap = (uint32_t)s.cap;
             const uint32_t b = min(s.start[cell], cap), e = min(s.start[cell + 1], cap);
             const double sh0 = s.ushift[cell], sh1 = s.ushift[K + cell], sh2 = s.ushift[2 * K + cell];
-            double a[12];
+            double a[12], we = 0.0;
 #pragma unroll
             for (int m = 0; m < 12; ++m) a[m] = 0.0;
             for (uint32_t i = b + lane; i < e; i += 32) {
                 const double C0 = (double)B.c0[i] - sh0, C1 = (double)B.c1[i] - sh1, C2 = (double)B.c2[i] - sh2;
                 const double c2 = C0 * C0 + C1 * C1 + C2 * C2;
+                if (Wt) {
+                    const double w = Wt[i];
+                    we += w;
+                    a[0] += w * C0; a[1] += w * C1; a[2] += w * C2;
+                    a[3] += w * C0 * C0; a[4] += w * C1 * C1; a[5] += w * C2 * C2;
+                    a[6] += w * C0 * C1; a[7] += w * C0 * C2; a[8] += w * C1 * C2;
+                    a[9] += w * c2 * C0; a[10] += w * c2 * C1; a[11] += w * c2 * C2;
+                    continue;
+                }
                 a[0] += C0; a[1] += C1; a[2] += C2;
                 a[3] += C0 * C0; a[4] += C1 * C1; a[5] += C2 * C2;
                 a[6] += C0 * C1; a[7] += C0 * C2; a[8] += C1 * C2;
@@ -268,8 +282,10 @@ __global__ void __launch_bounds__(256) k_moments(const SimDev* __restrict__ sims
             }
 #pragma unroll
             for (int m = 0; m < 12; ++m) a[m] = warp_sum(a[m]);
+            if (Wt) we = warp_sum(we);
             if (lane == 0) {
                 s.mom[cell] = (double)(e - b);
+                if (Wt) s.wneff[cell] = we;
 #pragma unroll
                 for (int m = 0; m < 12; ++m) s.mom[(size_t)(m + 1) * K + cell] = a[m];
                 s.fill[cell] = 0;
@@ -404,6 +420,11 @@ __global__ void __launch_bounds__(128) k_params(const SimDev* __restrict__ sims,
                     // Eq. 11: B = ((1 - Pr)/(2 Pr)) sigma*/(rho theta); S = I - s B
                     const double beta = (1.0 - s.Pr) / (2.0 * s.Pr) / L.theta;
                     for (int k = 0; k < 6; ++k) pr[4 + k] = beta * sig[k];
+                }
+                if (s.weighted) {
+                    // sigma* and q* per unit density for the weights of steps 4 and 7
+                    for (int k = 0; k < 6; ++k) s.wst[(size_t)k * K + cell] = sig[k];
+                    for (int k = 0; k < 3; ++k) s.wst[(size_t)(6 + k) * K + cell] = Q[k] / fq;
                 }
                 pr[10] = -expm1(-s.Pr * L.nu * s.dt);                       // Eqs. 8b, 9
                 pr[11] = L.nu;
@@ -639,9 +660,11 @@ void launch_inject(const Launch& L, bool fp64) {
     if (fp64) k_inject<double><<<L.grid_c, 256, 0, L.stream>>>(L.sims, L.ctiles, L.nctiles);
     else k_inject<float><<<L.grid_c, 256, 0, L.stream>>>(L.sims, L.ctiles, L.nctiles);
 }
-void launch_moments(const Launch& L, bool fp64) {
-    if (fp64) k_moments<double><<<L.grid_c, 256, 0, L.stream>>>(L.sims, L.ctiles, L.nctiles);
-    else k_moments<float><<<L.grid_c, 256, 0, L.stream>>>(L.sims, L.ctiles, L.nctiles);
+void launch_moments(const Launch& L, bool fp64) { launch_moments_src(L, fp64, false); }
+void launch_moments_src(const Launch& L, bool fp64, bool src_cur) {
+    const int sc = src_cur ? 1 : 0;
+    if (fp64) k_moments<double><<<L.grid_c, 256, 0, L.stream>>>(L.sims, L.ctiles, L.nctiles, sc);
+    else k_moments<float><<<L.grid_c, 256, 0, L.stream>>>(L.sims, L.ctiles, L.nctiles, sc);
 }
 void launch_params(const Launch& L) { k_params<<<L.grid_c, 32, 0, L.stream>>>(L.sims, L.ctiles, L.nctiles); }
 void launch_relax(const Launch& L, bool fp64) {

@@ -61,7 +61,8 @@ class Params(ctypes.Structure):
                 ("precision", c_int), ("pipeline", c_int), ("capacity_factor", c_double),
                 ("slab_count", c_int), ("slab_index", c_int), ("slab_group", c_int),
                 ("flux_axis", c_int), ("flux_pos", c_double), ("gll_average", c_int),
-                ("selection", c_int), ("es_sampler", c_int)]
+                ("selection", c_int), ("es_sampler", c_int), ("weighted", c_int), ("r_p", c_double),
+                ("weight_average", c_int)]
 
 
 class Region(ctypes.Structure):
@@ -108,6 +109,7 @@ def lib(build_if_missing: bool = True):
         "usp_step": (c_int, [c_void_p, c_int]),
         "usp_sample_macro": (c_int, [c_void_p, c_int, c_void_p, c_size_t, c_int]),
         "usp_get_particles": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int64, P(c_int64)]),
+        "usp_get_weights": (c_int, [c_void_p, c_void_p, c_int64, P(c_int64)]),
         "usp_run_stage": (c_int, [c_void_p, c_int]),
         "usp_get_params": (c_int, [c_void_p, c_void_p, c_size_t]),
         "usp_debug_philox": (c_int, [c_int64, c_void_p, c_uint32, c_uint32, c_void_p]),
@@ -222,7 +224,8 @@ def make_structs(w: dict, pipeline: str | None = None):
                     int(pr.get("slab_index", 0)), int(pr.get("slab_group", 0)),
                     int(pr.get("flux_axis", 0)), float(pr.get("flux_pos", 0.0)),
                     int(pr.get("gll_average", 0)), SELECTION[pr.get("selection", "bernoulli")],
-                    SAMPLER[pr.get("es_sampler", "cholesky")])
+                    SAMPLER[pr.get("es_sampler", "cholesky")], int(pr.get("weighted", 0)),
+                    float(pr.get("r_p", 10.0)), int(pr.get("weight_average", 0)))
     return gas, grid, faces, segs, len(w.get("segments", [])), params
 
 
@@ -338,7 +341,14 @@ class Simulation:
                                      cap, ctypes.byref(n))
         self._check(rc, "usp_get_particles")
         m = n.value
-        return {"pos": pos[:m], "vel": vel[:m], "pid": pid[:m], "cell": cell[:m]}
+        out = {"pos": pos[:m], "vel": vel[:m], "pid": pid[:m], "cell": cell[:m]}
+        if self.w["params"].get("weighted"):
+            wt = np.zeros(cap)
+            nw = c_int64()
+            self._check(lib().usp_get_weights(self._h, wt.ctypes.data, cap, ctypes.byref(nw)), "usp_get_weights")
+            assert nw.value == m
+            out["w"] = wt[:m]
+        return out
 
     def set_tuning(self, fused_R=0, grid_per_sm=0):
         self._check(lib().usp_set_tuning(self._h, int(fused_R), int(grid_per_sm)), "usp_set_tuning")

@@ -204,6 +204,20 @@ def homogeneous_box(ppc=1000, Kn=0.05, dt_over_tauc=0.5, mode="usp", precision="
     return w
 
 
+def homogeneous_column(ny=2000, ppc=500, Kn=0.05, dt_over_tauc=0.5, mode="usp", precision="fp64", Pr=PR_MONO,
+                       fixed_pne=0.0):
+    """ny periodic cells of the homogeneous box's size stacked along y: a
+    uniform gas, so every cell relaxes alone, with cells small enough for
+    the per-cell work of the fused pipeline (positions y in [0, ny 1e-6])."""
+    H = 1.0e-6
+    faces = [_face("periodic")] * 4
+    w = _base(1, 1, ny, (0.0, 0.0), (1.0, ny * H), faces, Kn=Kn, L_ref=H, dt_over_tauc=dt_over_tauc,
+              ppc=ppc, precision=precision, mode=mode, steps=10)
+    w["gas"]["Pr"] = Pr
+    w["params"]["fixed_pne"] = fixed_pne
+    return w
+
+
 def bimaxwellian(n, T=(1.3 * T0, 0.85 * T0, 0.85 * T0), u=(0.0, 0.0, 0.0), y_range=(0.0, 1.0e-6),
                  x_range=(0.0, 1.0), seed=7, heat_skew=0.0):
     """Seeded particle state: positions uniform in the box, velocity component i

@@ -90,12 +90,18 @@ def test_struct_layouts_match_header(tmp_path):
             assert got[(cname, f[0])] == getattr(py, f[0]).offset, (cname, f[0])
 
 
-@pytest.mark.parametrize("key,value", [("selection", "fixed_count"), ("es_sampler", "gallis_torczynski")])
-def test_ablations_need_the_plain_pipeline(key, value):
-    """Fixed-count selection and the Gallis-Torczynski sampler run on the
-    plain pipeline; the fused one rejects them (INVALID_ARG) instead of
-    running something else."""
+@pytest.mark.parametrize("pipeline", ["plain", "fused"])
+@pytest.mark.parametrize("key", ["selection", "es_sampler"])
+def test_ablation_codes_out_of_range_rejected(pipeline, key):
+    """Both pipelines run fixed-count selection and the Gallis-Torczynski
+    sampler; a code outside USP_SELECT_* / USP_SAMPLER_* is INVALID_ARG."""
     w = W.sod(ny=10, ppc_left=10)
-    w["params"][key] = value
-    w["params"]["pipeline"] = "fused"
-    assert _create_rc(w) == -1
+    w["params"]["pipeline"] = pipeline
+    if pipeline == "fused":
+        w = W.with_precision(w, "fp32")
+    gas, grid, faces, segs, nseg, params = U.make_structs(w, pipeline)
+    setattr(params, key, 2)
+    h = ctypes.c_void_p()
+    rc = U.lib().usp_create(ctypes.byref(gas), ctypes.byref(grid), faces, segs, nseg, ctypes.byref(params), None,
+                            None, ctypes.byref(h))
+    assert rc == -1 and not h.value

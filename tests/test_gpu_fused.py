@@ -147,6 +147,105 @@ def test_fused_homogeneous_relaxation_closed_form(usp, mode):
     assert abs(sig1 - r * sig0) < 5 * se, (sig1, r * sig0, se)
 
 
+def _column(usp, nc, ppc, mode, seed, T=(1.3 * W.T0, 0.85 * W.T0, 0.85 * W.T0), **abl):
+    """A uniform gas in nc periodic cells of ppc particles (fused, FP32)
+    after one step: the flight, then the relaxation with that step's
+    parameters (reading the particles applies the pending relaxation).
+    Returns the workload, the handle, the initial velocities (as stored,
+    FP32) and the particles after the step, both in pid order, the fields
+    the relaxation's parameters came from and the step counter of its
+    random numbers."""
+    w = _fused(W.homogeneous_column(ny=nc, ppc=ppc, dt_over_tauc=5.0, mode=mode))
+    w["params"].update(abl)
+    n = nc * ppc
+    pos, vel, pid = W.bimaxwellian(n, T=T, y_range=(0.0, w["grid"]["hi"][1]), seed=seed)
+    g = usp.Simulation(w).set_particles(pos, vel, pid)
+    g.step(1)
+    F1, step_key = g.sample(), g.info()["step"]
+    P1 = g.particles()
+    o0, o1 = np.argsort(pid), np.argsort(P1["pid"])
+    v0 = vel[o0].astype(np.float32).astype(np.float64)
+    P1 = {k: v[o1] for k, v in P1.items()}
+    assert np.array_equal(P1["pid"], pid[o0])
+    return w, g, v0, P1, F1, step_key
+
+
+def _relax_probability(w, g, F):
+    """P_relax = 1 - exp(-nu_ES dt) per cell (Eqs. 6a, 9, 35) from the
+    sampled n and T of each cell."""
+    gas = w["gas"]
+    T = F[4]
+    rho = F[0] * gas["mass"]
+    mu = g.info()["mu_ref"] * (T / gas["T_ref"]) ** gas["omega"]
+    nu = rho * KB_M_AR * T / mu
+    return -np.expm1(-gas["Pr"] * nu * g.info()["dt"])
+
+
+def test_fused_fixed_count_takes_the_smallest_selection_words(usp):
+    """Eq. 9 on the fused path: in every cell exactly the nearest integer to
+    N_c P_relax particles relax, namely those with the smallest selection
+    words (Philox word 0 of the relaxation counter, drawn here with the
+    oracle's independent generator).  Cells where N_c P_relax lies within
+    0.01 of a half-integer (FP32 and FP64 may round it apart) or where the
+    word at the threshold is tied are left out (a few at most)."""
+    nc, ppc = 400, 500
+    w, g, v0, P1, F1, step_key = _column(usp, nc, ppc, "spesbgk", 31, selection="fixed_count")
+    changed = np.any(P1["vel"] != v0, axis=1)
+    key = np.array([w["seed"] & 0xFFFFFFFF, w["seed"] >> 32], dtype=np.uint32)
+    words = np.array([oracle.philox(np.array([p, step_key, 1, 0], dtype=np.uint32), key)[0] for p in P1["pid"]],
+                     dtype=np.int64)
+    prob = _relax_probability(w, g, F1)
+    checked = 0
+    for c in range(nc):
+        idx = np.nonzero(P1["cell"] == c)[0]
+        x = len(idx) * prob[c]
+        ns = int(math.floor(x + 0.5))
+        if abs(x - math.floor(x) - 0.5) < 0.01:
+            continue
+        order = idx[np.argsort(words[idx], kind="stable")]
+        if ns < len(idx) and words[order[ns - 1]] == words[order[ns]]:
+            continue
+        want = np.zeros(len(P1["pid"]), dtype=bool)
+        want[order[:ns]] = True
+        assert np.array_equal(changed[idx], want[idx]), (c, len(idx), ns, int(changed[idx].sum()))
+        checked += 1
+    assert checked > 0.95 * nc, checked
+    assert g.info()["counters"][5] == 0
+
+
+def test_fused_gallis_torczynski_closed_form(usp):
+    """Eqs. 10-11 on the fused path, SP-ESBGK step: relaxed particles carry
+    S theta S^T (S = I - ((1 - Pr)/(2 Pr)) sigma / theta) rescaled to the old
+    energy, so one relaxation leaves E[sigma'] = e^-a sigma + (1 - e^-a)
+    theta (3 S S^T / tr(S S^T) - I), a = nu_ES dt -- many standard errors
+    from the Gaussian target's e^-a sigma + (1 - e^-a)(1 - 1/Pr) sigma at
+    this anisotropy (T = 2, 0.5, 0.5 T0)."""
+    nc, ppc = 2000, 500
+    w, g, v0, P1, F1, _ = _column(usp, nc, ppc, "spesbgk", 33, T=(2.0 * W.T0, 0.5 * W.T0, 0.5 * W.T0),
+                                  es_sampler="gallis_torczynski")
+    n = nc * ppc
+
+    def stress(v):
+        C = v.astype(np.float64) - v.astype(np.float64).mean(axis=0)
+        cov = C.T @ C / len(v)
+        th = np.trace(cov) / 3.0
+        return cov - th * np.eye(3), th
+
+    sig0, theta = stress(v0)
+    sig1, _ = stress(P1["vel"])
+    a = -np.log1p(-_relax_probability(w, g, F1).mean())
+    Pr = w["gas"]["Pr"]
+    S = np.eye(3) - (1 - Pr) / (2 * Pr) * sig0 / theta
+    SS = S @ S.T
+    want = math.exp(-a) * sig0 + (1 - math.exp(-a)) * theta * (3.0 * SS / np.trace(SS) - np.eye(3))
+    gauss = math.exp(-a) * sig0 + (1 - math.exp(-a)) * (1 - 1 / Pr) * sig0
+    se = theta * math.sqrt(2.0 / n)
+    for i in range(3):
+        assert abs(sig1[i, i] - want[i, i]) < 5 * se, (i, sig1[i, i], want[i, i], se)
+    assert abs(want[0, 0] - gauss[0, 0]) > 20 * se
+    assert g.info()["counters"][5] == 0
+
+
 def test_fused_relaxation_full_covariance(usp):
     """Every component of the stress relaxes by the same factor (Eqs. 8b,
     29-33): a Gaussian state with a full, rotated covariance exercises the
