@@ -444,6 +444,28 @@ def config_leg(U, W, torch, name, w, pipeline, steps, warmup, stream, flush, hbm
     return out
 
 
+def weighted_leg(U, W, torch, stream, flush, steps=20, warmup=20):
+    """C1 Couette with the weighted added particles of Table 2 (plain FP64
+    pipeline, P_ne from Kn_GLL, Eq. 34-averaged weight fields): the full USP
+    step.  Its stages run as one captured sequence (no per-stage timing)."""
+    w = W.couette()
+    w["params"].update(weighted=1, weight_average=1, capacity_factor=4.0)
+    sim = U.Simulation(w, stream=stream).init_particles()
+    n0 = sim.info()["n_particles"]
+    sim.step(warmup)
+    sim.synchronize()
+    n = sim.info()["n_particles"]
+    el = time_sim_steps(torch, sim, steps, flush)
+    n1 = sim.info()["n_particles"]
+    assert sim.info()["counters"][5] == 0, "weighted Couette: particles lost"
+    sim.close()
+    step_s = el / steps
+    return {"workload": "C1_couette_fp64_weighted", "particles": n, "particles_initial": n0,
+            "particles_end": n1, "cells": w["grid"]["ny"], "precision": "fp64", "pipeline": "plain+weighted",
+            "steps": steps, "ms_per_step": 1e3 * step_s, "value": 0.5 * (n + n1) / step_s, "unit": METRIC,
+            "l2": "flushed before every timed step", "roofline": None}
+
+
 def config_legs(U, W, torch, args, stream, hbm, pipeline):
     """Every benchmark shape of the paper's Sec. 4 at one GPU, each alone."""
     from paper_1808_03801_gb300 import autotune
@@ -467,6 +489,8 @@ def config_legs(U, W, torch, args, stream, hbm, pipeline):
                                 comparator=not args.no_comparator, tuning=tuning)
         if tuning:
             legs[name]["tuning"] = {k: v for k, v in tuning.items() if k != "tried"}
+    if not args.only_config or "C1_couette_fp64_weighted" in args.only_config:
+        legs["C1_couette_fp64_weighted"] = weighted_leg(U, W, torch, stream, flush)
     del flush
     torch.cuda.empty_cache()
     return legs
@@ -572,6 +596,8 @@ def run_gpu(args):
             result["configs"] = config_legs(U, W, torch, args, stream, hbm, pipeline)
         if args.serve_requests > 0:
             result["serving"] = serving_leg(W, args, value)
+        if not args.no_configs and world == 1:
+            result["precision"] = precision_leg(U, W)
         if not args.no_cpu_baseline and world == 1:
             rate1, n, done1, el1 = oracle_rate(args.cpu_seconds)
             rate, cores, n, done, elc = oracle_rate_all_cores(args.cpu_seconds)
@@ -585,6 +611,54 @@ def run_gpu(args):
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+FIELD_NAMES = ["n", "u0", "u1", "u2", "T", "pxx", "pyy", "pzz", "pxy", "pxz", "pyz", "q0", "q1", "q2", "Pne"]
+
+
+def precision_leg(U, W, seeds=8):
+    """Error of each time-averaged field of the fused FP32 path against the
+    FP64 GPU path (which matches the FP64 oracle particle by particle), on
+    Sod tubes of 200 cells x 200 particles and 60 steps after 40: for each
+    field the relative difference of the domain averages and the largest
+    |difference| / standard error over the cells (standard errors from
+    independent seeds on each side)."""
+    import numpy as np
+
+    def runs(precision, pipeline, seed0):
+        out = []
+        for s in range(seeds):
+            w = W.with_precision(W.sod(ny=200, ppc_left=200, seed=seed0 + s), precision)
+            w["params"]["pipeline"] = pipeline
+            g = U.Simulation(w).init_particles()
+            g.step(40)
+            acc = None
+            for _ in range(60):
+                g.step(1)
+                f = g.sample()[:len(FIELD_NAMES)]
+                acc = f if acc is None else acc + f
+            assert g.info()["counters"][5] == 0, f"precision {precision}: particles lost"
+            g.close()
+            out.append(acc / 60)
+        return np.array(out)
+    t0 = time.time()
+    a = runs("fp32", "fused", 1)
+    b = runs("fp64", "plain", 1001)
+    rows = {}
+    for k, name in enumerate(FIELD_NAMES):
+        fa, fb = a[:, k], b[:, k]
+        ma, mb = fa.mean(0), fb.mean(0)
+        se = np.sqrt(fa.var(0, ddof=1) / seeds + fb.var(0, ddof=1) / seeds)
+        z = np.where(se > 0, (ma - mb) / np.where(se > 0, se, 1.0), 0.0)
+        da, db = fa.mean(1), fb.mean(1)
+        sed = math.sqrt(da.var(ddof=1) / seeds + db.var(ddof=1) / seeds)
+        den = abs(db.mean())
+        rows[name] = {"rel_err_domain_mean": float(abs(da.mean() - db.mean()) / den) if den > 0 else 0.0,
+                      "z_domain_mean": float((da.mean() - db.mean()) / sed) if sed > 0 else 0.0,
+                      "max_abs_z_cell": float(np.abs(z).max()), "mean_z2_cell": float((z ** 2).mean())}
+    return {"reference": "plain FP64 GPU path (per-particle parity with the FP64 oracle)",
+            "case": f"Sod, 200 cells, 200/25 particles per cell, {seeds} seeds per side, fields averaged over "
+                    "steps 41-100", "seconds": round(time.time() - t0, 1), "fields": rows}
 
 
 def run_profile_case(args):

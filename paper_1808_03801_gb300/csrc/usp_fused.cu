@@ -213,11 +213,9 @@ __device__ __forceinline__ void es_draw_gt(const FCell& f, const TimeDraw& td, f
 //            cell's 64-cell destination window; each particle's rank among
 //            the arrivals of its slot;
 //   pass B   one atomic reservation per occupied slot in the destination
-//            buckets (one round trip for the whole cell) and each slot's
-//            offset in a slot-ordered list of the cell's particles;
-//   pass C   the list: perm[offset of the slot + rank] = particle;
-//   pass D   the list written out by consecutive lanes, so each store fills
-//            whole lines of one destination bucket.
+//            buckets (one round trip for the whole cell);
+//   writes   each particle at its slot's reserved start plus its rank, so
+//            the lanes of one slot write consecutive words of one bucket.
 // Then it releases the descriptor ("empty" mbarrier) and the producer may
 // reuse its ring space.  While a consumer works on a cell, the copies of the
 // cells behind it are in flight, so HBM latency is paid once per run of
@@ -510,10 +508,10 @@ struct alignas(16) G2Desc {
     uint32_t end;        // ring counter after this allocation (producer bookkeeping)
 };
 
-// bytes of ring per staged particle: (x,) y, v0, v1, v2, id; slot; rank; list entry
+// bytes of ring per staged particle: (x,) y, v0, v1, v2, id; slot; rank
 template <int DIM>
 __host__ __device__ constexpr uint32_t g2_bytes_per_particle() {
-    return (DIM == 2 ? 24u : 20u) + 1u + 2u + 2u;
+    return (DIM == 2 ? 24u : 20u) + 1u + 2u;
 }
 
 struct G2Stage {
@@ -525,7 +523,6 @@ struct G2Stage {
     uint32_t* id;
     unsigned char* sel;
     uint16_t* rank;
-    uint16_t* perm;
 };
 
 template <int DIM>
@@ -544,7 +541,6 @@ __device__ __forceinline__ G2Stage g2_stage(unsigned char* ring, uint32_t off, u
     S.id = (uint32_t*)(f + 4 * m);
     S.sel = (unsigned char*)(f + 5 * m);
     S.rank = (uint16_t*)(S.sel + m);
-    S.perm = S.rank + m;
     return S;
 }
 
