@@ -459,15 +459,19 @@ __global__ void __launch_bounds__(128) k_params(const SimDev* __restrict__ sims,
 // ---------------------------------------------------------------------------
 // is the particle at slot i of the cell [b, e) relaxed?  Bernoulli: its
 // selection word against the probability; fixed count (Eq. 9): its rank
-// among the cell's selection words below ns
+// among the cell's selection words below ns.  `words` holds the cell's
+// selection words (staged once per cell) when the cell fits, else null and
+// the words are drawn again.
+constexpr uint32_t kRelaxWords = 1024;
+
 template <class T>
 __device__ __forceinline__ bool selected(const SimDev& s, const PView<T>& B, uint32_t b, uint32_t e, uint32_t i,
-                                         uint32_t wx, T pth, uint32_t ns, uint32_t step) {
+                                         uint32_t wx, T pth, uint32_t ns, uint32_t step, const uint32_t* words) {
     if (!s.selection) return u01<T>(wx) < pth;
     if (ns == 0) return false;
     uint32_t rank = 0;
     for (uint32_t j = b; j < e && rank < ns; ++j) {
-        const uint32_t xj = draw(s, B.pid[j], step, kRelax, 0).x;
+        const uint32_t xj = words ? words[j - b] : draw(s, B.pid[j], step, kRelax, 0).x;
         rank += (xj < wx || (xj == wx && j < i)) ? 1u : 0u;
     }
     return rank < ns;
@@ -481,6 +485,7 @@ template <class T>
 __global__ void __launch_bounds__(32) k_relax(const SimDev* __restrict__ sims, const int2* __restrict__ tiles,
                                               const int* __restrict__ ntiles) {
     __shared__ SimDev sim_sh;
+    __shared__ uint32_t sel_words[kRelaxWords];
     const int nt = *ntiles;
     const int lane = threadIdx.x & 31;
     int loaded = -1;
@@ -520,10 +525,17 @@ __global__ void __launch_bounds__(32) k_relax(const SimDev* __restrict__ sims, c
             // Eq. 9 fixed count: the ns particles with the smallest selection
             // words (ties: lower position first)
             const uint32_t ns = s.selection ? (uint32_t)floor((double)(e - b) * R.p_relax + 0.5) : 0u;
+            const uint32_t* words = nullptr;
+            if (s.selection && e - b <= kRelaxWords) {
+                __syncwarp();
+                for (uint32_t i = b + lane; i < e; i += 32) sel_words[i - b] = draw(s, B.pid[i], step, kRelax, 0).x;
+                __syncwarp();
+                words = sel_words;
+            }
             for (uint32_t i = b + lane; i < e; i += 32) {
                 const uint32_t pid = B.pid[i];
                 const uint4 w = draw(s, pid, step, kRelax, 0);
-                if (!selected<T>(s, B, b, e, i, w.x, pth, ns, step)) continue;
+                if (!selected<T>(s, B, b, e, i, w.x, pth, ns, step, words)) continue;
                 T C[3];
                 es_draw<T>(s, R, pid, step, w, C);
                 const double o0 = (double)B.c0[i] - R.u[0], o1 = (double)B.c1[i] - R.u[1],
@@ -555,7 +567,7 @@ __global__ void __launch_bounds__(32) k_relax(const SimDev* __restrict__ sims, c
                     for (uint32_t i = b + lane; i < e; i += 32) {
                         const uint32_t pid = B.pid[i];
                         const uint4 w = draw(s, pid, step, kRelax, 0);
-                        if (!selected<T>(s, B, b, e, i, w.x, pth, ns, step)) continue;
+                        if (!selected<T>(s, B, b, e, i, w.x, pth, ns, step, words)) continue;
                         T C[3];
                         es_draw<T>(s, R, pid, step, w, C);
                         B.c0[i] = (T)(uo[0] + alpha * ((double)C[0] - mn[0]));

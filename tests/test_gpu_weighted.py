@@ -93,3 +93,47 @@ def test_weighted_handle_rejects_unsupported_options(usp):
         w["params"].update(change)
         with pytest.raises(usp.UspError):
             usp.Simulation(w)
+
+
+@pytest.mark.parametrize("kind", ["shear", "heat"])
+def test_weighted_transport_independent_of_dt_on_the_gpu(usp, kind):
+    """The GPU weighted path reproduces what the oracle's pins establish:
+    steady Couette (shear) or thermal Couette (heat) at Kn = 0.01, 50 cells,
+    1000 particles per cell, P_ne = 1, dt = 5 tau_c (x = nu dt near 4),
+    Eq. 34-averaged weight fields (n_a = 100): mu_eff / mu (or kappa_eff /
+    kappa) is 1 within noise, where the scheme without the added particles
+    gives 1.23 (the closed forms of the transport section)."""
+    ny, ppc = 50, 1000
+    if kind == "shear":
+        w = W.couette(ny=ny, ppc=ppc, Kn=0.01, u_wall=20.0, dt_over_tauc=5.0, omega=0.81, precision="fp64", seed=4)
+    else:
+        w = W.couette(ny=ny, ppc=ppc, Kn=0.01, u_wall=0.0, dt_over_tauc=5.0, omega=0.81, precision="fp64", seed=8)
+        w["faces"][2]["T"] = W.T0 + 50.0
+        w["faces"][3]["T"] = W.T0 - 50.0
+    w["params"].update(mode="fixed", fixed_pne=1.0, weighted=1, weight_average=1, n_avg=100, capacity_factor=4.0)
+    g = usp.Simulation(w).init_particles()
+    n0 = g.info()["n_particles"]
+    H = w["grid"]["hi"][1]
+    y = (np.arange(ny) + 0.5) * H / ny
+    c = slice(int(0.2 * ny), int(0.8 * ny))
+    g.step(1500)
+    ratios, counts = [], []
+    for _ in range(16):
+        acc = np.zeros((16, ny))
+        for _ in range(200):
+            g.step(1)
+            acc += g.sample()
+        counts.append(g.info()["n_particles"])
+        F = acc / 200
+        mu = g.info()["mu_ref"] * (F[4][c].mean() / W.T0) ** 0.81
+        if kind == "shear":
+            ratios.append(-F[8][c].mean() / (mu * np.polyfit(y[c], F[1][c], 1)[0]))
+        else:
+            kappa = 15.0 / 4.0 * KB_M_AR * mu
+            ratios.append(-F[12][c].mean() / (kappa * np.polyfit(y[c], F[4][c], 1)[0]))
+    r = np.array(ratios)
+    m, se = r.mean(), r.std(ddof=1) / math.sqrt(len(r))
+    assert abs(m - 1.0) < 4 * se + 0.03, (m, se)
+    assert abs(m - 1.23) > 4 * se + 0.1, (m, se)
+    assert max(counts) < 1.3 * n0 and min(counts) > n0, (n0, min(counts), max(counts))
+    assert g.info()["counters"][5] == 0
