@@ -99,11 +99,11 @@ def test_weighted_handle_rejects_unsupported_options(usp):
 def test_weighted_transport_independent_of_dt_on_the_gpu(usp, kind):
     """The GPU weighted path reproduces what the oracle's pins establish:
     steady Couette (shear) or thermal Couette (heat) at Kn = 0.01, 50 cells,
-    1000 particles per cell, P_ne = 1, dt = 5 tau_c (x = nu dt near 4),
+    2000 particles per cell, P_ne = 1, dt = 5 tau_c (x = nu dt near 4),
     Eq. 34-averaged weight fields (n_a = 100): mu_eff / mu (or kappa_eff /
     kappa) is 1 within noise, where the scheme without the added particles
     gives 1.23 (the closed forms of the transport section)."""
-    ny, ppc = 50, 1000
+    ny, ppc = 50, 2000
     if kind == "shear":
         w = W.couette(ny=ny, ppc=ppc, Kn=0.01, u_wall=20.0, dt_over_tauc=5.0, omega=0.81, precision="fp64", seed=4)
     else:
@@ -118,7 +118,7 @@ def test_weighted_transport_independent_of_dt_on_the_gpu(usp, kind):
     c = slice(int(0.2 * ny), int(0.8 * ny))
     g.step(1500)
     ratios, counts = [], []
-    for _ in range(16):
+    for _ in range(24):
         acc = np.zeros((16, ny))
         for _ in range(200):
             g.step(1)
@@ -134,6 +134,6 @@ def test_weighted_transport_independent_of_dt_on_the_gpu(usp, kind):
     r = np.array(ratios)
     m, se = r.mean(), r.std(ddof=1) / math.sqrt(len(r))
     assert abs(m - 1.0) < 4 * se + 0.03, (m, se)
-    assert abs(m - 1.23) > 4 * se + 0.1, (m, se)
+    assert abs(m - 1.23) > 4 * se + 0.05, (m, se)
     assert max(counts) < 1.3 * n0 and min(counts) > n0, (n0, min(counts), max(counts))
     assert g.info()["counters"][5] == 0
