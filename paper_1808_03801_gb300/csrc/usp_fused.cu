@@ -1421,6 +1421,8 @@ __global__ void __launch_bounds__(32 * (NC + 1), 16 / (NC + 1)) k_g2(const SimDe
 // FP32 sums of the centred velocities do not cancel; k_params_f promotes
 // them to FP64 with the shift taken into account.
 // ---------------------------------------------------------------------------
+constexpr int kG1Pre = 64;    // slots of a cell loaded ahead (a multiple of 32)
+
 __global__ void __launch_bounds__(256) k_g1(const SimDev* __restrict__ sims, const int2* __restrict__ tiles,
                                             const int* __restrict__ ntiles) {
     __shared__ uint32_t spl_all[8][32];
@@ -1454,11 +1456,36 @@ __global__ void __launch_bounds__(256) k_g1(const SimDev* __restrict__ sims, con
         const float* V0 = (const float*)s.vel[q][0];
         const float* V1 = (const float*)s.vel[q][1];
         const float* V2 = (const float*)s.vel[q][2];
+        // the first kG1Pre slots of the warp's next cell are loaded while the
+        // current one is summed and reduced, so each cell's first round trip
+        // overlaps the previous cell's work
+        float px[kG1Pre / 32], py[kG1Pre / 32], pz[kG1Pre / 32];
+        auto prefetch = [&](int c) {
+            const bool live = c < kCTile && tile.y + c < K;
+            const uint32_t b0 = live ? h_base[c] : 0u, n0 = live ? h_nb[c] : 0u;
+#pragma unroll
+            for (int r = 0; r < kG1Pre / 32; ++r) {
+                const uint32_t j = (uint32_t)(32 * r + lane);
+                const bool ok = j < n0;
+                px[r] = ok ? __ldcs(V0 + b0 + j) : 0.0f;
+                py[r] = ok ? __ldcs(V1 + b0 + j) : 0.0f;
+                pz[r] = ok ? __ldcs(V2 + b0 + j) : 0.0f;
+            }
+        };
+        prefetch(warp);
         for (int cc = warp; cc < kCTile; cc += 8) {
             const int cell = tile.y + cc;
             if (cell >= K) break;
             const uint32_t base = h_base[cc];
             const uint32_t nb = h_nb[cc];
+            float cx[kG1Pre / 32], cy[kG1Pre / 32], cz[kG1Pre / 32];
+#pragma unroll
+            for (int r = 0; r < kG1Pre / 32; ++r) {
+                cx[r] = px[r];
+                cy[r] = py[r];
+                cz[r] = pz[r];
+            }
+            prefetch(cc + 8);
             const uint32_t arrived = h_arr[cc];
             const float4 us = h_us[cc];
             const float u0 = us.x, u1 = us.y, u2 = us.z;
@@ -1476,8 +1503,12 @@ __global__ void __launch_bounds__(256) k_g1(const SimDev* __restrict__ sims, con
                 S[6] += C0 * C1; S[7] += C0 * C2; S[8] += C1 * C2;
                 S[9] += c2 * C0; S[10] += c2 * C1; S[11] += c2 * C2;
             };
+#pragma unroll
+            for (int r = 0; r < kG1Pre / 32; ++r)
+                if ((uint32_t)(32 * r + lane) < nb) add(cx[r], cy[r], cz[r]);
 #pragma unroll 4
-            for (uint32_t j = lane; j < nb; j += 32) add(__ldcs(V0 + base + j), __ldcs(V1 + base + j), __ldcs(V2 + base + j));
+            for (uint32_t j = kG1Pre + lane; j < nb; j += 32)
+                add(__ldcs(V0 + base + j), __ldcs(V1 + base + j), __ldcs(V2 + base + j));
             for (uint32_t j = nb + lane; j < n; j += 32) {   // spill-list entries of the cell
                 const uint32_t i = spl_all[warp][j - nb];
                 add(s.sp_vel[q][0][i], s.sp_vel[q][1][i], s.sp_vel[q][2][i]);
