@@ -1036,19 +1036,11 @@ __device__ __forceinline__ void g2_move(const SimDev* __restrict__ sims, const S
             S.y[j] = y; S.v0[j] = c[0]; S.v1[j] = c[1]; S.v2[j] = c[2];
             S.sel[j] = ws;
         }
-        const unsigned grp = __match_any_sync(0xffffffffu, slot);
-        if (slot >= 0) {
-            const int leader = __ffs(grp) - 1;
-            uint32_t r0 = 0;
-            if (lane == leader) {
-                r0 = wcnt[slot];
-                wcnt[slot] = r0 + (uint32_t)__popc(grp);
-            }
-            r0 = __shfl_sync(grp, r0, leader);
-            S.rank[j] = (uint16_t)(r0 + (uint32_t)__popc(grp & lanemask_lt()));
-        }
-        __syncwarp();
+        // the particle's rank among the arrivals of its slot: one shared
+        // atomic (lanes of one slot are served one after another)
+        if (slot >= 0) S.rank[j] = (uint16_t)atomicAdd(&wcnt[slot], 1u);
     }
+    __syncwarp();
     // pass B: one reservation per occupied slot, all in flight together
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
