@@ -33,7 +33,7 @@ FUSED_SRC = os.path.join(ROOT, "paper_1808_03801_gb300", "csrc", "usp_fused.cu")
 # dram__bytes_write.sum of the 32-tube Sod case divided by its particles),
 # valid only for the k_g2 source with this SHA-1; any other source reports
 # traffic as null until it is captured again
-KG2_TRAFFIC = {"sha1": "58a8e6555c0362750768776f64d919ab4cb08f9a", "bytes_per_particle": 39.01}
+KG2_TRAFFIC = {"sha1": "8534965cb3990759cfe601e5c38d987dbb238e7a", "bytes_per_particle": 39.02}
 
 
 def parse():
