@@ -269,8 +269,11 @@ int usp_init_particles(usp_handle* h, const usp_region* regions, int nregions, u
  * 1-D), vel[n][3], pid[n]; next_pid is the first id given to injected
  * particles.  The arrays are copied to the device as they are (pinned memory
  * makes this a direct DMA) and transposed into the storage planes there; the
- * particle storage of an earlier load of a similar size is reused.  Returns
- * after the copy.  A slab keeps particles outside its rows in its edge cells
+ * particle storage of an earlier load of a similar size is reused, and so is
+ * the device staging area of the copy (it grows to the largest load and
+ * stays with the handle).  Returns after the copy and the set-up kernels
+ * have run (one synchronisation of the handle's stream), so the arrays may
+ * be reused at once.  A slab keeps particles outside its rows in its edge cells
  * until they move.  Resets the step counter and the averages. */
 int usp_set_particles(usp_handle* h, int64_t n, const double* pos, const double* vel,
                       const uint32_t* pid, uint32_t next_pid, uint64_t seed);

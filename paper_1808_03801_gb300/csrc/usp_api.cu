@@ -67,6 +67,8 @@ struct usp_handle {
     int fused_R = 8;                  // k_g2 consumer warps per CTA: 3, 7, 15 for R = 4, 8, 12
     int grid_per_sm = 8;              // persistent blocks per SM of the tiled kernels
     cudaStream_t batch_stream = nullptr;   // stream of the batch the handle is admitted to
+    void* stage = nullptr;            // device staging of usp_set_particles (grows, kept)
+    size_t stage_bytes = 0;
 };
 
 struct usp_batch {
@@ -690,17 +692,11 @@ static int fused_from_unsorted(usp_handle* h) {
     CK(cudaMemsetAsync(s.fill, 0, sizeof(uint32_t) * (K + 1), h->stream));
     // no parameters yet: zero shift for the first moments, no relaxation
     CK(cudaMemsetAsync(s.fprm, 0, sizeof(float) * kNFPrm * (size_t)K, h->stream));
-    int one = 1;
+    int one = 1;   // pageable: copied out before the call returns
     CK(cudaMemcpyAsync(&h->d_dyn->cur, &one, sizeof(int), cudaMemcpyHostToDevice, h->stream));
-    std::vector<uint32_t> start(K + 2);
-    CK(cudaMemcpyAsync(start.data(), s.start, sizeof(uint32_t) * (K + 2), cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-    uint32_t mx = 0;
-    for (int c = 0; c < K; ++c) mx = std::max(mx, start[c + 1] - start[c]);
-    h->fused_R = choose_R(mx + mx / 4);
+    h->fused_R = choose_R(0);
     launch_fused_setup(L);
     CK(cudaGetLastError());
-    CK(cudaStreamSynchronize(h->stream));
     return USP_OK;
 }
 
@@ -721,9 +717,19 @@ extern "C" int usp_set_particles(usp_handle* h, int64_t n, const double* pos, co
     const bool fp64 = h->precision == USP_FP64;
     cudaError_t e = cudaSuccess;
     if (n > 0) {
-        void* stage = dalloc(h, sizeof(double) * 5 * (size_t)n);
-        if (!stage) return fail(h, USP_ERR_OOM, "staging buffer for the particle upload");
-        double* dpos = (double*)stage;
+        // the staging area grows and stays with the handle (no allocation,
+        // free or synchronisation per upload once it is large enough)
+        const size_t need = sizeof(double) * 5 * (size_t)n;
+        if (need > h->stage_bytes) {
+            if (h->stage) {
+                CK(cudaStreamSynchronize(h->stream));
+                dfree(h, h->stage);
+            }
+            h->stage = dalloc(h, need);
+            h->stage_bytes = h->stage ? need : 0;
+            if (!h->stage) return fail(h, USP_ERR_OOM, "staging buffer for the particle upload");
+        }
+        double* dpos = (double*)h->stage;
         double* dvel = dpos + 2 * n;
         e = cudaMemcpyAsync(dpos, pos, sizeof(double) * 2 * n, cudaMemcpyHostToDevice, h->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(dvel, vel, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream);
@@ -732,13 +738,12 @@ extern "C" int usp_set_particles(usp_handle* h, int64_t n, const double* pos, co
             launch_unpack(s, fp64, dpos, dvel, n, h->stream);
             e = cudaGetLastError();
         }
-        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-        dfree(h, stage);
     }
     if (e != cudaSuccess) return fail(h, USP_ERR_CUDA, cudaGetErrorString(e));
     if ((rc = reset_dynamic(h, (uint32_t)n, next_pid)) != 0) return rc;
-    CK(cudaStreamSynchronize(h->stream));
     if (h->pipeline == USP_PIPE_FUSED && (rc = fused_from_unsorted(h)) != 0) return rc;
+    // one synchronisation: the caller's arrays are free to reuse on return
+    CK(cudaStreamSynchronize(h->stream));
     if ((rc = weighted_setup(h)) != 0) return rc;
     h->initialised = true;
     h->mid_step = false;
@@ -1061,6 +1066,7 @@ extern "C" int usp_destroy(usp_handle* h) {
     free_particles(h);
     for (void* p : h->cell_allocs) dfree(h, p);
     h->cell_allocs.clear();
+    if (h->stage) dfree(h, h->stage);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
     return USP_OK;
