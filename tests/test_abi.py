@@ -105,3 +105,22 @@ def test_ablation_codes_out_of_range_rejected(pipeline, key):
     rc = U.lib().usp_create(ctypes.byref(gas), ctypes.byref(grid), faces, segs, nseg, ctypes.byref(params), None,
                             None, ctypes.byref(h))
     assert rc == -1 and not h.value
+
+
+@pytest.mark.parametrize("change", [
+    dict(pipeline="fused", precision="fp32"),   # weighted particles: plain FP64 only
+    dict(r_p=0.0),                              # Eq. 25 needs r_p > 0
+    dict(selection="fixed_count"),              # the default selection and sampler only
+    dict(slab_count=2),                         # one domain
+])
+def test_weighted_options_validated_before_any_device_work(change):
+    w = W.couette(ny=10, ppc=10, precision="fp64")
+    w["params"].update(weighted=1)
+    w["params"].update(change)
+    assert _create_rc(w) == -1
+
+
+def test_weighted_particles_reject_reservoir_faces():
+    w = W.slit(nx=20, ny=10, ppc=5, precision="fp64")
+    w["params"].update(weighted=1, pipeline="plain")
+    assert _create_rc(w) == -1
