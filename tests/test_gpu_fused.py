@@ -109,6 +109,41 @@ def test_fused_relaxation_conserves_each_cell(usp):
         assert abs(ea - eb) < 1e-5 * eb, (c, (ea - eb) / eb)
 
 
+def test_fused_relaxation_conserves_each_cell_at_full_size(usp):
+    """The same per-cell conservation at the size of the slit workload:
+    1.6e7 particles in 32 000 periodic cells of 500 (a uniform gas, so the
+    velocities before the relaxation are the loaded ones).  Every cell keeps
+    its count, its mean velocity within 1e-5 of its thermal speed and its
+    thermal energy within 1e-5 relative."""
+    nc, ppc = 32_000, 500
+    n = nc * ppc
+    w = _fused(W.homogeneous_column(ny=nc, ppc=ppc, dt_over_tauc=2.0))
+    pos, vel, pid = W.bimaxwellian(n, seed=14, u=(60.0, -30.0, 10.0), y_range=(0.0, w["grid"]["hi"][1]))
+    g = usp.Simulation(w).set_particles(pos, vel, pid)
+    g.step(1)
+    P = g.particles()
+    assert len(P["pid"]) == n and g.info()["counters"][5] == 0
+    assert g.info()["counters"][4] > 0.5 * n
+    before = np.empty((n, 3))
+    before[pid] = vel.astype(np.float32).astype(np.float64)
+    before = before[P["pid"]]
+    after = P["vel"]
+    cell = P["cell"].astype(np.int64)
+    cnt = np.bincount(cell, minlength=nc).astype(np.float64)
+    assert cnt.min() > 0
+
+    def mean_energy(v):
+        m = np.stack([np.bincount(cell, v[:, d], minlength=nc) for d in range(3)], 1) / cnt[:, None]
+        C = v - m[cell]
+        return m, np.bincount(cell, (C ** 2).sum(1), minlength=nc)
+
+    mb, eb = mean_energy(before)
+    ma, ea = mean_energy(after)
+    th = eb / (3 * cnt)
+    assert np.all(np.abs(ma - mb) < 1e-5 * np.sqrt(th)[:, None]), np.abs(ma - mb).max()
+    assert np.all(np.abs(ea - eb) < 1e-5 * eb), (np.abs(ea - eb) / eb).max()
+
+
 @pytest.mark.parametrize("mode", ["usp", "sp", "spesbgk"])
 def test_fused_homogeneous_relaxation_closed_form(usp, mode):
     """The expectation of one relaxation step (derived from Eqs. 8b, 29-33)
