@@ -463,6 +463,9 @@ __global__ void __launch_bounds__(128) k_params(const SimDev* __restrict__ sims,
 // selection words (staged once per cell) when the cell fits, else null and
 // the words are drawn again.
 constexpr uint32_t kRelaxWords = 1024;
+// new peculiar velocities of a cell's relaxed particles kept from the sums
+// pass for the apply pass (larger cells draw them again)
+constexpr uint32_t kRelaxKeep = 512;
 
 template <class T>
 __device__ __forceinline__ bool selected(const SimDev& s, const PView<T>& B, uint32_t b, uint32_t e, uint32_t i,
@@ -486,6 +489,8 @@ __global__ void __launch_bounds__(32) k_relax(const SimDev* __restrict__ sims, c
                                               const int* __restrict__ ntiles) {
     __shared__ SimDev sim_sh;
     __shared__ uint32_t sel_words[kRelaxWords];
+    __shared__ double keep_c[3][kRelaxKeep];
+    __shared__ unsigned char keep_sel[kRelaxKeep];
     const int nt = *ntiles;
     const int lane = threadIdx.x & 31;
     int loaded = -1;
@@ -532,12 +537,18 @@ __global__ void __launch_bounds__(32) k_relax(const SimDev* __restrict__ sims, c
                 __syncwarp();
                 words = sel_words;
             }
+            const bool keep = e - b <= kRelaxKeep;
+            __syncwarp();
             for (uint32_t i = b + lane; i < e; i += 32) {
                 const uint32_t pid = B.pid[i];
                 const uint4 w = draw(s, pid, step, kRelax, 0);
-                if (!selected<T>(s, B, b, e, i, w.x, pth, ns, step, words)) continue;
+                const bool sel = selected<T>(s, B, b, e, i, w.x, pth, ns, step, words);
+                if (keep) keep_sel[i - b] = sel ? 1 : 0;
+                if (!sel) continue;
                 T C[3];
                 es_draw<T>(s, R, pid, step, w, C);
+                if (keep)
+                    for (int d = 0; d < 3; ++d) keep_c[d][i - b] = (double)C[d];
                 const double o0 = (double)B.c0[i] - R.u[0], o1 = (double)B.c1[i] - R.u[1],
                              o2 = (double)B.c2[i] - R.u[2];
                 nr += 1.0;
@@ -563,13 +574,20 @@ __global__ void __launch_bounds__(32) k_relax(const SimDev* __restrict__ sims, c
                     const double alpha = sqrt(Eo / En);
                     const double uo[3] = {R.u[0] + so[0] * inv, R.u[1] + so[1] * inv, R.u[2] + so[2] * inv};
                     const double mn[3] = {sn[0] * inv, sn[1] * inv, sn[2] * inv};
-                    // pass 2: redraw and apply c = ubar_old + alpha (c' - ubar_new)
+                    // pass 2: apply c = ubar_old + alpha (c' - ubar_new), with c'
+                    // kept from pass 1 or drawn again
+                    __syncwarp();
                     for (uint32_t i = b + lane; i < e; i += 32) {
-                        const uint32_t pid = B.pid[i];
-                        const uint4 w = draw(s, pid, step, kRelax, 0);
-                        if (!selected<T>(s, B, b, e, i, w.x, pth, ns, step, words)) continue;
                         T C[3];
-                        es_draw<T>(s, R, pid, step, w, C);
+                        if (keep) {
+                            if (!keep_sel[i - b]) continue;
+                            for (int d = 0; d < 3; ++d) C[d] = (T)keep_c[d][i - b];
+                        } else {
+                            const uint32_t pid = B.pid[i];
+                            const uint4 w = draw(s, pid, step, kRelax, 0);
+                            if (!selected<T>(s, B, b, e, i, w.x, pth, ns, step, words)) continue;
+                            es_draw<T>(s, R, pid, step, w, C);
+                        }
                         B.c0[i] = (T)(uo[0] + alpha * ((double)C[0] - mn[0]));
                         B.c1[i] = (T)(uo[1] + alpha * ((double)C[1] - mn[1]));
                         B.c2[i] = (T)(uo[2] + alpha * ((double)C[2] - mn[2]));
