@@ -407,6 +407,7 @@ extern "C" int usp_create(const usp_gas* gas, const usp_grid* grid, const usp_bc
     CALLOC(inj_pidoff, uint32_t, K);
     CALLOC(fprm, float, (size_t)kNFPrm * K);
     if (prm->gll_average && prm->pipeline == USP_PIPE_PLAIN) { CALLOC(gavg, double, 3 * (size_t)K); }
+    if (prm->pipeline == USP_PIPE_PLAIN) { CALLOC(gloc, double, 6 * (size_t)K); }
     if (prm->weighted) {
         CALLOC(wneff, double, K);
         CALLOC(wst, double, 9 * (size_t)K);

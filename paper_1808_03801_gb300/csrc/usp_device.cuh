@@ -374,6 +374,28 @@ __device__ __forceinline__ void grad_from_local(const Local& L, GradState& G) {
     G.lambda = L.lambda;
 }
 
+// the stencil state of a cell as k_moments stored it (plain pipeline), or
+// computed from its sums when no store exists
+__device__ __forceinline__ void store_grad_state(const SimDev& s, int cell, const GradState& G) {
+    const size_t K = (size_t)s.K;
+    s.gloc[cell] = G.valid ? 1.0 : 0.0;
+    s.gloc[K + cell] = G.n;
+    s.gloc[2 * K + cell] = G.T;
+    s.gloc[3 * K + cell] = G.umag;
+    s.gloc[4 * K + cell] = G.a_sound;
+    s.gloc[5 * K + cell] = G.lambda;
+}
+
+__device__ __forceinline__ void load_grad_state(const SimDev& s, int cell, GradState& G) {
+    const size_t K = (size_t)s.K;
+    G.valid = s.gloc[cell] != 0.0;
+    G.n = s.gloc[K + cell];
+    G.T = s.gloc[2 * K + cell];
+    G.umag = s.gloc[3 * K + cell];
+    G.a_sound = s.gloc[4 * K + cell];
+    G.lambda = s.gloc[5 * K + cell];
+}
+
 __device__ __forceinline__ int neighbor(const SimDev& s, int cell, int axis, int dir) {
     const int ix = cell % s.nx, iy = cell / s.nx;
     if (axis == 0) {

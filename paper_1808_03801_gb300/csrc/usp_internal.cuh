@@ -101,6 +101,7 @@ struct alignas(16) SimDev {
     double* avg;          // kNFields x K
     double* ushift;       // 3 x K, previous mean velocity (shift of the sums)
     double* gavg;         // 3 x K, averaged n, T, |u| at the start of the step (plain pipeline, gll_average)
+    double* gloc;         // 6 x K, each cell's stencil state (valid, n, T, |u|, a, lambda) of this step (plain)
     uint32_t* inj_count;  // K (buffer cells only)
     uint32_t* inj_pidoff; // K
     uint32_t inj_total;

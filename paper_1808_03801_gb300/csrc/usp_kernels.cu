@@ -237,26 +237,33 @@ __global__ void __launch_bounds__(256) k_inject(const SimDev* __restrict__ sims,
 // src_cur: the sums of the current buffer (the weighted step's moments of
 // f^n) instead of the sorted one; with weighted particles every sum is
 // W-weighted and the cell's weight sum goes to wneff
+// One warp per block, the blocks striding over single cells: the FP64 sums
+// are latency-bound, so even a domain of a hundred cells should spread
+// over a hundred SMs.
 template <class T>
-__global__ void __launch_bounds__(256) k_moments(const SimDev* __restrict__ sims, const int2* __restrict__ tiles,
-                                                 const int* __restrict__ ntiles, int src_cur) {
+__global__ void __launch_bounds__(32) k_moments(const SimDev* __restrict__ sims, const int2* __restrict__ tiles,
+                                                const int* __restrict__ ntiles, int src_cur) {
     __shared__ SimDev sim_sh;
     const int nt = *ntiles;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    for (int t = blockIdx.x; t < nt; t += gridDim.x) {
-        const int2 tile = tiles[t];
-        __syncthreads();
-        load_sim(sim_sh, sims[tile.x]);
-        __syncthreads();
+    const int lane = threadIdx.x & 31;
+    int loaded = -1;
+    for (int g = blockIdx.x; g < nt * kCTile; g += gridDim.x) {
+        const int2 tile = tiles[g / kCTile];
+        if (tile.x != loaded) {
+            __syncwarp();
+            load_sim(sim_sh, sims[tile.x]);
+            __syncwarp();
+            loaded = tile.x;
+        }
         const SimDev& s = sim_sh;
         const int K = s.K;
         const int buf = src_cur ? s.dyn->cur : s.dyn->cur ^ 1;
         PView<T> B = view<T>(s, buf);
         const double* Wt = s.weighted ? s.wgt[buf] : nullptr;
-        if (tile.y == 0 && threadIdx.x == 0) s.fill[K] = 0;
-        for (int cc = warp; cc < kCTile; cc += nwarps) {
-            const int cell = tile.y + cc;
-            if (cell >= K) break;
+        const int cell = tile.y + g % kCTile;
+        if (cell == 0 && lane == 0) s.fill[K] = 0;
+        if (cell >= K) continue;
+        {
             const uint32_t cap = (uint32_t)s.cap;
             const uint32_t b = min(s.start[cell], cap), e = min(s.start[cell + 1], cap);
             const double sh0 = s.ushift[cell], sh1 = s.ushift[K + cell], sh2 = s.ushift[2 * K + cell];
@@ -288,6 +295,15 @@ __global__ void __launch_bounds__(256) k_moments(const SimDev* __restrict__ sims
                 if (Wt) s.wneff[cell] = we;
 #pragma unroll
                 for (int m = 0; m < 12; ++m) s.mom[(size_t)(m + 1) * K + cell] = a[m];
+                if (s.gloc) {
+                    // the cell's stencil state once (from the sums just
+                    // stored), for its neighbours' Kn_GLL
+                    Local L;
+                    local_state(s, cell, L, nullptr, nullptr);
+                    GradState G;
+                    grad_from_local(L, G);
+                    store_grad_state(s, cell, G);
+                }
                 s.fill[cell] = 0;
                 if (gll_averaged(s)) snap_avg(s, cell);
             }
@@ -352,6 +368,7 @@ __global__ void __launch_bounds__(128) k_params(const SimDev* __restrict__ sims,
                             GradState Gm, Gp;
                             if (m >= 0) {
                                 if (avg) grad_from_avg(s, m, Gm);
+                                else if (s.gloc) load_grad_state(s, m, Gm);
                                 else {
                                     Local Lm;
                                     local_state(s, m, Lm, nullptr, nullptr);
@@ -361,6 +378,7 @@ __global__ void __launch_bounds__(128) k_params(const SimDev* __restrict__ sims,
                             }
                             if (p >= 0) {
                                 if (avg) grad_from_avg(s, p, Gp);
+                                else if (s.gloc) load_grad_state(s, p, Gp);
                                 else {
                                     Local Lp;
                                     local_state(s, p, Lp, nullptr, nullptr);
@@ -693,8 +711,11 @@ void launch_inject(const Launch& L, bool fp64) {
 void launch_moments(const Launch& L, bool fp64) { launch_moments_src(L, fp64, false); }
 void launch_moments_src(const Launch& L, bool fp64, bool src_cur) {
     const int sc = src_cur ? 1 : 0;
-    if (fp64) k_moments<double><<<L.grid_c, 256, 0, L.stream>>>(L.sims, L.ctiles, L.nctiles, sc);
-    else k_moments<float><<<L.grid_c, 256, 0, L.stream>>>(L.sims, L.ctiles, L.nctiles, sc);
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = std::max(1, std::min(L.grid_c * kCTile, 32 * sms));
+    if (fp64) k_moments<double><<<grid, 32, 0, L.stream>>>(L.sims, L.ctiles, L.nctiles, sc);
+    else k_moments<float><<<grid, 32, 0, L.stream>>>(L.sims, L.ctiles, L.nctiles, sc);
 }
 void launch_params(const Launch& L) { k_params<<<L.grid_c, 32, 0, L.stream>>>(L.sims, L.ctiles, L.nctiles); }
 void launch_relax(const Launch& L, bool fp64) {
