@@ -36,6 +36,35 @@ int persistent_grid(int ntiles, int per_sm) {
 
 }  // namespace
 
+// a second stream and two events for the forked part of a fused step
+struct Fork {
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    bool make() {
+        if (side) return true;
+        if (cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            release();
+            return false;
+        }
+        return true;
+    }
+    void release() {
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
+        if (side) cudaStreamDestroy(side);
+        side = nullptr;
+        ev_fork = ev_join = nullptr;
+    }
+    void attach(Launch& L) const {
+        L.side = side;
+        L.ev_fork = ev_fork;
+        L.ev_join = ev_join;
+    }
+};
+
 struct usp_handle {
     SimDev host{};            // host copy of the simulation description
     SimDev* d_sim = nullptr;  // device copy
@@ -69,6 +98,7 @@ struct usp_handle {
     cudaStream_t batch_stream = nullptr;   // stream of the batch the handle is admitted to
     void* stage = nullptr;            // device staging of usp_set_particles (grows, kept)
     size_t stage_bytes = 0;
+    Fork fork;                        // fused steps: layout beside the moments and parameters
 };
 
 struct usp_batch {
@@ -89,6 +119,7 @@ struct usp_batch {
     bool dirty = true;
     int precision = -1, pipeline = -1;
     std::string err;
+    Fork fork;
 };
 
 // ---------------------------------------------------------------------------
@@ -174,10 +205,25 @@ static void enqueue_step(const Launch& L, bool fp64, bool reservoir) {
     launch_finish(L);
 }
 
-// one full step of the fused FP32 pipeline
+// one full step of the fused FP32 pipeline.  The next step's bucket layout
+// depends only on this step's arrivals, so it runs on a second stream beside
+// the moments and parameters; the end of the step waits for both.
 static void enqueue_fused_step(const Launch& L, int R, bool reservoir) {
     launch_fused_relax_stream(L, R, false);
     if (reservoir) launch_fused_inject(L);
+    if (L.side) {
+        cudaEventRecord(L.ev_fork, L.stream);
+        cudaStreamWaitEvent(L.side, L.ev_fork, 0);
+        Launch Ls = L;
+        Ls.stream = L.side;
+        launch_fused_layout_parts(Ls);
+        cudaEventRecord(L.ev_join, L.side);
+        launch_fused_moments(L, R);
+        launch_fused_params(L);
+        cudaStreamWaitEvent(L.stream, L.ev_join, 0);
+        launch_fused_step_end(L);
+        return;
+    }
     launch_fused_moments(L, R);
     launch_fused_params(L);
     launch_fused_layout(L);   // ends the step too
@@ -757,6 +803,7 @@ extern "C" int usp_set_particles(usp_handle* h, int64_t n, const double* pos, co
 // ---------------------------------------------------------------------------
 static int capture(usp_handle* h, int nsteps, cudaGraphExec_t* exec) {
     Launch L = make_launch(h);
+    if (h->pipeline == USP_PIPE_FUSED && !h->host.weighted && h->fork.make()) h->fork.attach(L);
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     for (int i = 0; i < nsteps; ++i) enqueue_any(h, L);
@@ -1068,6 +1115,7 @@ extern "C" int usp_destroy(usp_handle* h) {
     for (void* p : h->cell_allocs) dfree(h, p);
     h->cell_allocs.clear();
     if (h->stage) dfree(h, h->stage);
+    h->fork.release();
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
     return USP_OK;
@@ -1282,6 +1330,7 @@ static int batch_capture(usp_batch* b, int nsteps, cudaGraphExec_t* exec) {
         res |= h->host.has_reservoir != 0;
         R = std::max(R, h->fused_R);
     }
+    if (b->pipeline == USP_PIPE_FUSED && b->fork.make()) b->fork.attach(L);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return bfail(b, USP_ERR_CUDA, cudaGetErrorString(e));
@@ -1330,6 +1379,7 @@ extern "C" int usp_batch_destroy(usp_batch* b) {
     cudaFree(b->d_ptiles);
     cudaFree(b->d_ctiles);
     cudaFree(b->d_ntiles);
+    b->fork.release();
     if (b->own_stream) cudaStreamDestroy(b->stream);
     delete b;
     return USP_OK;

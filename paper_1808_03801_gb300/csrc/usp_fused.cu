@@ -2137,17 +2137,25 @@ __global__ void __launch_bounds__(kLayTile) k_lay_scan(const SimDev* __restrict_
             dyn->n = (uint32_t)min(tot_exact, 0xFFFFFFFFull);
             dyn->sp_n[cur] = 0;
             dyn->lay_dst = (uint32_t)cur;
-            // end of the step
-            if (s.has_reservoir) {
-                dyn->next_pid += s.inj_total;
-                dyn->counters[kCntInjected] += s.inj_total;
-            }
-            dyn->cur = cur ^ 1;
-            dyn->step += 1;
-            dyn->nsamples += 1;
-            dyn->relax_pending = 1;
         }
         __syncthreads();
+    }
+}
+
+// end of the step (after the layout and the parameters): buffers swap, the
+// step counter and the sample count advance, the relaxation becomes pending
+__global__ void k_step_end(const SimDev* __restrict__ sims, int nsims) {
+    for (int si = blockIdx.x * blockDim.x + threadIdx.x; si < nsims; si += gridDim.x * blockDim.x) {
+        const SimDev& s = sims[si];
+        SimDyn* dyn = s.dyn;
+        if (s.has_reservoir) {
+            dyn->next_pid += s.inj_total;
+            dyn->counters[kCntInjected] += s.inj_total;
+        }
+        dyn->cur ^= 1;
+        dyn->step += 1;
+        dyn->nsamples += 1;
+        dyn->relax_pending = 1;
     }
 }
 
@@ -2292,11 +2300,20 @@ void launch_fused_moments(const Launch& L, int R) {
 
 void launch_fused_params(const Launch& L) { k_params_f<<<L.grid_c, 32, 0, L.stream>>>(L.sims, L.ctiles, L.nctiles); }
 
-void launch_fused_layout(const Launch& L) {
+// the bucket layout of the next step's destination buffer (reads only the
+// arrivals of this step, so it may run beside k_g1 and k_params_f)
+void launch_fused_layout_parts(const Launch& L) {
     const dim3 grid((unsigned)std::min(L.lay_tiles, 1024), (unsigned)L.nsims);
     k_lay_sum<<<grid, kLayTile, 0, L.stream>>>(L.sims);
     k_lay_scan<<<L.nsims, kLayTile, 0, L.stream>>>(L.sims, L.nsims);
     k_lay_put<<<grid, kLayTile, 0, L.stream>>>(L.sims);
+}
+
+void launch_fused_step_end(const Launch& L) { k_step_end<<<(L.nsims + 127) / 128, 128, 0, L.stream>>>(L.sims, L.nsims); }
+
+void launch_fused_layout(const Launch& L) {
+    launch_fused_layout_parts(L);
+    launch_fused_step_end(L);
 }
 
 

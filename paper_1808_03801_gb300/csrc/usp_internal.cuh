@@ -222,6 +222,10 @@ struct Launch {
     int grid_p, grid_c;   // persistent grid sizes
     int lay_tiles = 1;    // layout tiles (kLayTile cells) of the largest simulation
     cudaStream_t stream;
+    // fused step: a second stream and two events let the layout kernels run
+    // beside k_g1 and k_params_f (null: one stream)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 constexpr int kPTile = 512;   // particles per tile (small domains still spread over many SMs)
@@ -251,6 +255,8 @@ void launch_fused_inject(const Launch& L);
 void launch_fused_moments(const Launch& L, int R);
 void launch_fused_params(const Launch& L);
 void launch_fused_layout(const Launch& L);
+void launch_fused_layout_parts(const Launch& L);
+void launch_fused_step_end(const Launch& L);
 void fused_prepare_attributes();
 cudaError_t debug_philox(int64_t n, const uint32_t* d_ctr, uint32_t k0, uint32_t k1, uint32_t* d_out, cudaStream_t st);
 
