@@ -141,9 +141,9 @@ def lib(build_if_missing: bool = True):
 _STAGES = {
     "plain": [(0, "k_stream"), (2, "k_scan+k_scatter"), (3, "k_moments"), (4, "k_params"), (5, "k_relax"),
               (6, "k_finish")],
-    "fused": [(10, "k_g2"), (12, "k_g1"), (13, "k_params_f"), (14, "k_lay_sum+scan+put")],
+    "fused": [(10, "k_g2"), (12, "k_g1"), (13, "k_params_f"), (14, "k_lay_sum+scan+put+k_step_end")],
 }
-_LAUNCHES = {"plain": 7, "fused": 6}
+_LAUNCHES = {"plain": 7, "fused": 7}
 
 
 def fused_available() -> bool:

@@ -385,7 +385,7 @@ def test_fused_stages_compose_a_step(usp):
     a.step(1)
     for k, _ in usp.stage_list("fused"):
         b.run_stage(k)
-    assert usp.launches_per_step("fused") == 6   # k_g2, k_g1, k_params_f and three layout kernels
+    assert usp.launches_per_step("fused") == 7   # k_g2, k_g1, k_params_f, three layout kernels, the end of the step
     ia, ib = a.info(), b.info()
     assert ia["step"] == ib["step"] == 1
     from tests._util import by_pid
