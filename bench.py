@@ -33,7 +33,7 @@ FUSED_SRC = os.path.join(ROOT, "paper_1808_03801_gb300", "csrc", "usp_fused.cu")
 # dram__bytes_write.sum of the 32-tube Sod case divided by its particles),
 # valid only for the k_g2 source with this SHA-1; any other source reports
 # traffic as null until it is captured again
-KG2_TRAFFIC = {"sha1": "8534965cb3990759cfe601e5c38d987dbb238e7a", "bytes_per_particle": 39.02}
+KG2_TRAFFIC = {"sha1": "457b722e98bf31a08f53d7535213d4a2cfddae41", "bytes_per_particle": 39.01}
 
 
 def parse():
@@ -273,17 +273,21 @@ def stage_times(torch, B, stages, steps=3):
     return {k: v / steps for k, v in acc.items()}
 
 
-def e2e_rate(U, W, torch, batch, pipeline, steps, stream):
+def e2e_rate(U, W, torch, batch, pipeline, steps, warmup, stream):
     """Through the public API with host buffers: each tube's initial state is
     uploaded from pinned host memory (usp_set_particles), the batch advances
-    `steps` steps, and every tube's fields come back to the host."""
+    `steps` steps, and every tube's fields come back to the host.  Each tube
+    has a stream of its own, so the set-up kernels of one upload run beside
+    the next one.  One untimed pass of `warmup` steps over the same handles
+    and host buffers comes first (the first device access to the freshly
+    pinned pages and the batch's graph capture); the next pass is timed."""
     import numpy as np
     sims = []
     hosts = []
     for i in range(batch):
         w = W.sod(precision="fp32", seed=1 + i)
         w["params"]["pipeline"] = pipeline
-        s = U.Simulation(w, stream=stream).init_particles()
+        s = U.Simulation(w, stream=torch.cuda.Stream()).init_particles()
         P = s.particles()
         pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory().numpy() for k, v in P.items()
                if k in ("pos", "vel", "pid")}
@@ -291,14 +295,19 @@ def e2e_rate(U, W, torch, batch, pipeline, steps, stream):
         sims.append(s)
     torch.cuda.synchronize()
     B = U.Batch(hbm_budget=200 << 30, max_sims=batch, stream=stream)
+
+    def solve(nsteps):
+        for s, h in zip(sims, hosts):
+            s.set_particles(h["pos"], h["vel"], h["pid"])
+            B.admit(s)
+        B.step(nsteps)
+        for s in sims:
+            B.retire(s)
+        return [s.sample() for s in sims]
+
+    solve(max(1, warmup))
     t0 = time.perf_counter()
-    for s, h in zip(sims, hosts):
-        s.set_particles(h["pos"], h["vel"], h["pid"])
-        B.admit(s)
-    B.step(steps)
-    for s in sims:
-        B.retire(s)
-    fields = [s.sample() for s in sims]
+    fields = solve(steps)
     el = time.perf_counter() - t0
     n = sum(len(h["pid"]) for h in hosts)
     h2d = sum(h["pos"].nbytes + h["vel"].nbytes + h["pid"].nbytes for h in hosts)
@@ -569,10 +578,11 @@ def run_gpu(args):
     torch.cuda.synchronize()
 
     if rank == 0:
-        e2e, h2d, d2h = e2e_rate(U, W, torch, args.batch, pipeline, args.steps, stream)
+        e2e, h2d, d2h = e2e_rate(U, W, torch, args.batch, pipeline, args.steps, args.warmup, stream)
         result["e2e"] = {"value": e2e * world, "unit": METRIC, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                         "note": "initial state uploaded once per solve from pinned host memory and fields "
-                                 "read back at the end; bytes amortised over the steps"}
+                         "note": "initial state uploaded once per solve from pinned host memory (one stream per "
+                                 "tube) and fields read back at the end; bytes amortised over the steps; "
+                                 "one untimed solve of the same tubes first"}
         if not args.no_comparator:
             # plain per-simulation FP64 path on the same tubes (fewer, timed alone)
             nb = min(4, args.batch)

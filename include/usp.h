@@ -242,6 +242,7 @@ typedef struct {
                              a full bucket (fused pipeline), 7 net particles
                              through the counting plane (signed; params.flux_axis) */
     size_t device_bytes;  /* device memory held by the handle */
+    uint32_t next_pid;    /* id the next injected particle receives */
 } usp_info;
 
 /* Create a simulation.  faces[4] in order x-lo, x-hi, y-lo, y-hi; segs may be
@@ -267,14 +268,23 @@ int usp_init_particles(usp_handle* h, const usp_region* regions, int nregions, u
 
 /* Load an arbitrary state from HOST arrays: pos[n][2] (x, y; x ignored in
  * 1-D), vel[n][3], pid[n]; next_pid is the first id given to injected
- * particles.  The arrays are copied to the device as they are (pinned memory
- * makes this a direct DMA) and transposed into the storage planes there; the
- * particle storage of an earlier load of a similar size is reused, and so is
- * the device staging area of the copy (it grows to the largest load and
- * stays with the handle).  Returns after the copy and the set-up kernels
- * have run (one synchronisation of the handle's stream), so the arrays may
- * be reused at once.  A slab keeps particles outside its rows in its edge cells
- * until they move.  Resets the step counter and the averages. */
+ * particles (USP_NEXT_PID_AUTO: one past the largest id of pid, found on the
+ * device).  Page-locked (pinned) arrays are read in place by one device pass
+ * through their mapped addresses; pageable ones are copied as they are into
+ * the handle's second particle buffer, which the sort fills only afterwards
+ * (no staging area of its own).  Either way they are transposed into the
+ * storage planes on the device; the particle storage of an earlier load of
+ * a similar size is reused.  The reset of the per-cell state and the sort
+ * into cells run on the handle's stream.  Returns once the arrays have been
+ * read (they may be reused at once); the set-up kernels behind that point
+ * are asynchronous like usp_step, and a later failure of theirs is reported
+ * by the next synchronising call.  A slab keeps particles outside its rows
+ * in its edge cells until they move.  Resets the step counter and the
+ * averages. */
+/* next_pid value of usp_set_particles: one past the largest loaded id,
+ * found on the device while the ids are loaded (0 for an empty load) */
+#define USP_NEXT_PID_AUTO 0xFFFFFFFFu
+
 int usp_set_particles(usp_handle* h, int64_t n, const double* pos, const double* vel,
                       const uint32_t* pid, uint32_t next_pid, uint64_t seed);
 

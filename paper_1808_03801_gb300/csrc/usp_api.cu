@@ -96,8 +96,9 @@ struct usp_handle {
     int fused_R = 8;                  // k_g2 consumer warps per CTA: 3, 7, 15 for R = 4, 8, 12
     int grid_per_sm = 8;              // persistent blocks per SM of the tiled kernels
     cudaStream_t batch_stream = nullptr;   // stream of the batch the handle is admitted to
-    void* stage = nullptr;            // device staging of usp_set_particles (grows, kept)
-    size_t stage_bytes = 0;
+    void* b1_block = nullptr;         // buffer 1 and the cell plane (one allocation)
+    size_t b1_bytes = 0;
+    cudaEvent_t upload_ev = nullptr;  // usp_set_particles: the caller's arrays have been read
     Fork fork;                        // fused steps: layout beside the moments and parameters
 };
 
@@ -168,6 +169,8 @@ static void free_particles(usp_handle* h) {
     for (void* p : h->part_allocs) dfree(h, p);
     h->part_allocs.clear();
     h->part_bytes = 0;
+    h->b1_block = nullptr;
+    h->b1_bytes = 0;
 }
 
 static int upload_sim(usp_handle* h) {
@@ -564,17 +567,33 @@ static int alloc_particles(usp_handle* h, int64_t n) {
         }
         return p;
     };
+    // buffer 0 plane by plane; buffer 1 and the cell plane as one block
+    // (usp_set_particles stages the caller's FP64 arrays there before the
+    // sort fills it); every plane starts on a 16-byte boundary (cap is a
+    // multiple of 4)
+    const size_t plane = es * (size_t)cap, slots = 4 * (size_t)cap;
+    const size_t b1_bytes = (s.dim == 2 ? 5 : 4) * plane + 2 * slots;
+    char* blk = (char*)grab(b1_bytes);
+    h->b1_block = blk;
+    h->b1_bytes = blk ? b1_bytes : 0;
     for (int b = 0; b < 2; ++b) {
-        s.pos[b][0] = s.dim == 2 ? grab(es * cap) : nullptr;
-        s.pos[b][1] = grab(es * cap);
-        for (int d = 0; d < 3; ++d) s.vel[b][d] = grab(es * cap);
-        s.pid[b] = (uint32_t*)grab(4 * cap);
+        auto take = [&](size_t bytes) -> void* {
+            if (b == 0) return grab(bytes);
+            if (!blk) return nullptr;
+            void* r = blk;
+            blk += bytes;
+            return r;
+        };
+        s.pos[b][0] = s.dim == 2 ? take(plane) : nullptr;
+        s.pos[b][1] = take(plane);
+        for (int d = 0; d < 3; ++d) s.vel[b][d] = take(plane);
+        s.pid[b] = (uint32_t*)take(slots);
         if ((s.dim == 2 && !s.pos[b][0]) || !s.pos[b][1] || !s.vel[b][0] || !s.vel[b][1] || !s.vel[b][2] || !s.pid[b]) {
             free_particles(h);
             return fail(h, USP_ERR_OOM, "particle storage allocation failed");
         }
     }
-    s.cell = (uint32_t*)grab(4 * cap);
+    s.cell = blk ? (uint32_t*)blk : nullptr;
     if (s.weighted) {
         s.wgt[0] = (double*)grab(8 * cap);
         s.wgt[1] = (double*)grab(8 * cap);
@@ -618,13 +637,14 @@ static int reset_dynamic(usp_handle* h, uint32_t n, uint32_t next_pid) {
     d.n = n;
     d.next_pid = next_pid;
     const int K = h->host.K;
-    CK(cudaMemcpyAsync(h->d_dyn, &d, sizeof(d), cudaMemcpyHostToDevice, h->stream));
-    CK(cudaMemsetAsync(h->host.count, 0, sizeof(uint32_t) * (K + 1), h->stream));
-    CK(cudaMemsetAsync(h->host.fill, 0, sizeof(uint32_t) * (K + 1), h->stream));
-    CK(cudaMemsetAsync(h->host.ushift, 0, sizeof(double) * 3 * K, h->stream));
-    CK(cudaMemsetAsync(h->host.inst, 0, sizeof(double) * kNFields * K, h->stream));
-    CK(cudaMemsetAsync(h->host.avg, 0, sizeof(double) * kNFields * K, h->stream));
-    CK(cudaMemsetAsync(h->host.prm, 0, sizeof(double) * kNPrm * K, h->stream));
+    CK(cudaMemcpyAsync(h->d_dyn, &d, sizeof(d), cudaMemcpyHostToDevice, h->stream));   // pageable: copied out now
+    // counts, shifts, fields, averages and parameters cleared in one launch
+    const size_t k = (size_t)K;
+    ZeroList z{{h->host.count, h->host.fill, h->host.ushift, h->host.inst, h->host.avg, h->host.prm},
+               {k + 1, k + 1, 2 * 3 * k, 2 * (size_t)kNFields * k, 2 * (size_t)kNFields * k, 2 * (size_t)kNPrm * k},
+               6};
+    launch_zero(z, h->stream);
+    CK(cudaGetLastError());
     return USP_OK;
 }
 
@@ -747,6 +767,17 @@ static int fused_from_unsorted(usp_handle* h) {
     return USP_OK;
 }
 
+// the device address of a page-locked host array (mapped into the device's
+// address space), or null for pageable memory
+static const void* mapped_host(const void* p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 extern "C" int usp_set_particles(usp_handle* h, int64_t n, const double* pos, const double* vel, const uint32_t* pid,
                                  uint32_t next_pid, uint64_t seed) {
     if (!h) return USP_ERR_INVALID_ARG;
@@ -759,38 +790,54 @@ extern "C" int usp_set_particles(usp_handle* h, int64_t n, const double* pos, co
     s.key0 = (uint32_t)seed;
     s.key1 = (uint32_t)(seed >> 32);
     if ((rc = upload_sim(h)) != 0) return rc;
-    // the caller's arrays go to the device as they are (one copy each; fast
-    // when they are pinned), the transpose into planes runs on the GPU
     const bool fp64 = h->precision == USP_FP64;
+    const bool auto_pid = next_pid == USP_NEXT_PID_AUTO;
+    // the dynamic state first: with auto_pid its next_pid starts at 0 and
+    // the unpack pass raises it to one past the largest loaded id
+    if ((rc = reset_dynamic(h, (uint32_t)n, auto_pid ? 0u : next_pid)) != 0) return rc;
+    uint32_t* d_next = auto_pid ? &h->d_dyn->next_pid : nullptr;
     cudaError_t e = cudaSuccess;
-    if (n > 0) {
-        // the staging area grows and stays with the handle (no allocation,
-        // free or synchronisation per upload once it is large enough)
-        const size_t need = sizeof(double) * 5 * (size_t)n;
-        if (need > h->stage_bytes) {
-            if (h->stage) {
-                CK(cudaStreamSynchronize(h->stream));
-                dfree(h, h->stage);
-            }
-            h->stage = dalloc(h, need);
-            h->stage_bytes = h->stage ? need : 0;
-            if (!h->stage) return fail(h, USP_ERR_OOM, "staging buffer for the particle upload");
-        }
-        double* dpos = (double*)h->stage;
-        double* dvel = dpos + 2 * n;
-        e = cudaMemcpyAsync(dpos, pos, sizeof(double) * 2 * n, cudaMemcpyHostToDevice, h->stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(dvel, vel, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(s.pid[0], pid, 4 * n, cudaMemcpyHostToDevice, h->stream);
+    const double* mpos = n > 0 ? (const double*)mapped_host(pos) : nullptr;
+    const double* mvel = n > 0 ? (const double*)mapped_host(vel) : nullptr;
+    const uint32_t* mpid = n > 0 ? (const uint32_t*)mapped_host(pid) : nullptr;
+    const bool direct = mpos && mvel && mpid;
+    if (direct) {
+        // page-locked arrays: one pass reads them in place over the host
+        // link (measured faster than copy-engine transfers plus a transpose)
+        launch_unpack(s, fp64, mpos, mvel, mpid, true, d_next, n, h->stream);
+        e = cudaGetLastError();
+    } else if (n > 0) {
+        // pageable arrays go to the device as they are: the ids into their
+        // plane, the FP64 positions and then the velocities into buffer 1
+        // and the cell plane (at least 24 bytes per slot, filled by the sort
+        // only afterwards), each transposed into buffer 0's planes
+        if (h->b1_bytes < 24 * (size_t)n) return fail(h, USP_ERR_CAPACITY, "staging area smaller than the load");
+        double* stg = (double*)h->b1_block;
+        e = cudaMemcpyAsync(s.pid[0], pid, 4 * n, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(stg, pos, sizeof(double) * 2 * n, cudaMemcpyHostToDevice, h->stream);
         if (e == cudaSuccess) {
-            launch_unpack(s, fp64, dpos, dvel, n, h->stream);
+            launch_unpack(s, fp64, stg, nullptr, nullptr, false, nullptr, n, h->stream);
             e = cudaGetLastError();
         }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(stg, vel, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream);
     }
+    // the point on the stream after which the caller's arrays are no longer read
+    if (e == cudaSuccess && !h->upload_ev) e = cudaEventCreateWithFlags(&h->upload_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(h->upload_ev, h->stream);
+    if (e == cudaSuccess && !direct && n > 0) {
+        launch_unpack(s, fp64, nullptr, (const double*)h->b1_block, s.pid[0], false, d_next, n, h->stream);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(h->stream);
+        return fail(h, USP_ERR_CUDA, cudaGetErrorString(e));
+    }
+    if (h->pipeline == USP_PIPE_FUSED) rc = fused_from_unsorted(h);
+    // return once the arrays have been read; the set-up kernels behind the
+    // event run on the handle's stream like a step
+    e = cudaEventSynchronize(h->upload_ev);
+    if (rc) return rc;
     if (e != cudaSuccess) return fail(h, USP_ERR_CUDA, cudaGetErrorString(e));
-    if ((rc = reset_dynamic(h, (uint32_t)n, next_pid)) != 0) return rc;
-    if (h->pipeline == USP_PIPE_FUSED && (rc = fused_from_unsorted(h)) != 0) return rc;
-    // one synchronisation: the caller's arrays are free to reuse on return
-    CK(cudaStreamSynchronize(h->stream));
     if ((rc = weighted_setup(h)) != 0) return rc;
     h->initialised = true;
     h->mid_step = false;
@@ -1086,6 +1133,7 @@ extern "C" int usp_get_info(usp_handle* h, usp_info* info) {
     info->mu_ref = h->host.mu_ref;
     for (int i = 0; i < 8; ++i) info->counters[i] = (int64_t)d.counters[i];
     info->device_bytes = h->cell_bytes + h->part_bytes;
+    info->next_pid = d.next_pid;
     return rc;
 }
 
@@ -1114,7 +1162,7 @@ extern "C" int usp_destroy(usp_handle* h) {
     free_particles(h);
     for (void* p : h->cell_allocs) dfree(h, p);
     h->cell_allocs.clear();
-    if (h->stage) dfree(h, h->stage);
+    if (h->upload_ev) cudaEventDestroy(h->upload_ev);
     h->fork.release();
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;

@@ -247,7 +247,15 @@ void launch_relax(const Launch& L, bool fp64);
 void launch_finish(const Launch& L);
 void launch_init(const Launch& L, bool fp64, const double* reg_theta, const double* reg_u, const int* cell_reg);
 void launch_assign(const Launch& L, bool fp64);
-void launch_unpack(const SimDev& s, bool fp64, const double* pos, const double* vel, int64_t n, cudaStream_t st);
+void launch_unpack(const SimDev& s, bool fp64, const double* pos, const double* vel, const uint32_t* ids,
+                   bool ids_to_plane, uint32_t* next_pid, int64_t n, cudaStream_t st);
+constexpr int kZeroRanges = 8;
+struct ZeroList {   // device ranges of 32-bit words to clear
+    void* p[kZeroRanges];
+    size_t words[kZeroRanges];
+    int n;
+};
+void launch_zero(const ZeroList& z, cudaStream_t st);
 // fused FP32 pipeline (usp_fused.cu); R = particles per lane held in registers
 void launch_fused_setup(const Launch& L);
 void launch_fused_relax_stream(const Launch& L, int R, bool flush_only);

@@ -728,29 +728,71 @@ void launch_relax(const Launch& L, bool fp64) {
 }
 void launch_finish(const Launch& L) { k_finish<<<(L.nsims + 127) / 128, 128, 0, L.stream>>>(L.sims, L.nsims); }
 
-// user-supplied particles (host layout: pos[n][2], vel[n][3] in FP64, copied
-// to the device as they are) into the storage planes of buffer 0
+// user-supplied particles (host layout: pos[n][2], vel[n][3] in FP64) into
+// the storage planes of buffer 0.  pos, vel and ids are device copies of the
+// caller's arrays or, for page-locked host memory, the arrays themselves
+// read through their mapped device addresses; any of pos, vel, ids may be
+// null (that part is not read).  ids go to pid (when non-null); with
+// next_pid non-null, one past the largest id is folded into *next_pid (one
+// atomic per warp).
 template <class T>
-__global__ void k_unpack(const double* __restrict__ pos, const double* __restrict__ vel, int64_t n, int dim, T* x,
-                         T* y, T* v0, T* v1, T* v2) {
+__global__ void k_unpack(const double* __restrict__ pos, const double* __restrict__ vel,
+                         const uint32_t* __restrict__ ids, int64_t n, int dim, T* x, T* y, T* v0, T* v1, T* v2,
+                         uint32_t* pid, uint32_t* next_pid) {
+    uint32_t top = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        if (dim == 2) x[i] = (T)pos[2 * i];
-        y[i] = (T)pos[2 * i + 1];
-        v0[i] = (T)vel[3 * i];
-        v1[i] = (T)vel[3 * i + 1];
-        v2[i] = (T)vel[3 * i + 2];
+        if (pos) {
+            if (dim == 2) x[i] = (T)pos[2 * i];
+            y[i] = (T)pos[2 * i + 1];
+        }
+        if (vel) {
+            v0[i] = (T)vel[3 * i];
+            v1[i] = (T)vel[3 * i + 1];
+            v2[i] = (T)vel[3 * i + 2];
+        }
+        if (ids) {
+            const uint32_t id = ids[i];
+            if (pid) pid[i] = id;
+            top = max(top, id + 1u);
+        }
+    }
+    if (next_pid) {
+        top = __reduce_max_sync(0xffffffffu, top);
+        if ((threadIdx.x & 31) == 0 && top) atomicMax(next_pid, top);
     }
 }
 
-void launch_unpack(const SimDev& s, bool fp64, const double* pos, const double* vel, int64_t n, cudaStream_t st) {
+void launch_unpack(const SimDev& s, bool fp64, const double* pos, const double* vel, const uint32_t* ids,
+                   bool ids_to_plane, uint32_t* next_pid, int64_t n, cudaStream_t st) {
     if (n <= 0) return;
     const int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+    uint32_t* pid = ids_to_plane ? s.pid[0] : nullptr;
     if (fp64)
-        k_unpack<double><<<grid, 256, 0, st>>>(pos, vel, n, s.dim, (double*)s.pos[0][0], (double*)s.pos[0][1],
-                                               (double*)s.vel[0][0], (double*)s.vel[0][1], (double*)s.vel[0][2]);
+        k_unpack<double><<<grid, 256, 0, st>>>(pos, vel, ids, n, s.dim, (double*)s.pos[0][0], (double*)s.pos[0][1],
+                                               (double*)s.vel[0][0], (double*)s.vel[0][1], (double*)s.vel[0][2],
+                                               pid, next_pid);
     else
-        k_unpack<float><<<grid, 256, 0, st>>>(pos, vel, n, s.dim, (float*)s.pos[0][0], (float*)s.pos[0][1],
-                                              (float*)s.vel[0][0], (float*)s.vel[0][1], (float*)s.vel[0][2]);
+        k_unpack<float><<<grid, 256, 0, st>>>(pos, vel, ids, n, s.dim, (float*)s.pos[0][0], (float*)s.pos[0][1],
+                                              (float*)s.vel[0][0], (float*)s.vel[0][1], (float*)s.vel[0][2],
+                                              pid, next_pid);
+}
+
+// clear up to kZeroRanges device ranges of 32-bit words in one launch
+__global__ void k_zero(ZeroList z) {
+    for (int r = 0; r < z.n; ++r) {
+        uint32_t* p = (uint32_t*)z.p[r];
+        for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < z.words[r];
+             i += (size_t)gridDim.x * blockDim.x)
+            p[i] = 0u;
+    }
+}
+
+void launch_zero(const ZeroList& z, cudaStream_t st) {
+    size_t most = 0;
+    for (int r = 0; r < z.n; ++r) most = std::max(most, z.words[r]);
+    if (most == 0) return;
+    const int grid = (int)std::min<size_t>((most + 255) / 256, 152 * 8);
+    k_zero<<<grid, 256, 0, st>>>(z);
 }
 
 void launch_init(const Launch& L, bool fp64, const double* reg_theta, const double* reg_u, const int* cell_reg) {

@@ -17,6 +17,7 @@ from . import build as _build
 
 LIB_PATH = _build.LIB
 
+NEXT_PID_AUTO = 0xFFFFFFFF   # usp_set_particles: one past the largest loaded id
 OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "CAPACITY", -5: "TIMEOUT", -6: "STATE"}
 NFIELDS = 16
@@ -78,7 +79,7 @@ class Allocator(ctypes.Structure):
 class Info(ctypes.Structure):
     _fields_ = [("n_particles", c_int64), ("capacity", c_int64), ("n_cells", c_int32), ("precision", c_int32),
                 ("pipeline", c_int32), ("step", c_uint32), ("dt", c_double), ("mu_ref", c_double),
-                ("counters", c_int64 * 8), ("device_bytes", c_size_t)]
+                ("counters", c_int64 * 8), ("device_bytes", c_size_t), ("next_pid", c_uint32)]
 
 
 class UspError(RuntimeError):
@@ -294,7 +295,7 @@ class Simulation:
         vel = np.ascontiguousarray(vel, dtype=np.float64).reshape(-1, 3)
         pid = np.ascontiguousarray(pid, dtype=np.uint32)
         n = len(pid)
-        nxt = (int(pid.max()) + 1 if n else 0) if next_pid is None else int(next_pid)
+        nxt = NEXT_PID_AUTO if next_pid is None else int(next_pid)   # AUTO: found on the device
         seed = self.w["seed"] if seed is None else seed
         self._check(lib().usp_set_particles(self._h, n, pos.ctypes.data, vel.ctypes.data, pid.ctypes.data, nxt,
                                             int(seed)), "usp_set_particles")
@@ -316,7 +317,8 @@ class Simulation:
         self._check(lib().usp_get_info(self._h, ctypes.byref(inf)), "usp_get_info")
         return {"n_particles": inf.n_particles, "capacity": inf.capacity, "n_cells": inf.n_cells,
                 "precision": inf.precision, "pipeline": inf.pipeline, "step": inf.step, "dt": inf.dt,
-                "mu_ref": inf.mu_ref, "counters": list(inf.counters), "device_bytes": inf.device_bytes}
+                "mu_ref": inf.mu_ref, "counters": list(inf.counters), "device_bytes": inf.device_bytes,
+                "next_pid": inf.next_pid}
 
     def sample(self, averaged=False, out=None):
         """Fields [16, K] as numpy (host) or into a device tensor `out`."""

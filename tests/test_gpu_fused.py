@@ -395,6 +395,40 @@ def test_fused_stages_compose_a_step(usp):
     assert ia["counters"][4] == 0 and b.info()["counters"][4] > 0   # the read-back applied b's relaxation
 
 
+@pytest.mark.parametrize("pipeline", ["plain", "fused"])
+@pytest.mark.parametrize("dim", [1, 2])
+def test_set_particles_pinned_and_pageable_agree(usp, pipeline, dim):
+    """usp_set_particles from page-locked and from pageable arrays gives the
+    same state bit for bit, and the caller may overwrite its arrays as soon
+    as the call returns (the set-up kernels behind the copies are
+    asynchronous); stepped on, the two agree to the rounding of the sums."""
+    import torch
+    w = W.couette(ny=30, ppc=40, seed=9) if dim == 1 else W.cavity(n=12, ppc=30, seed=9)
+    w = _fused(w) if pipeline == "fused" else W.with_precision(w, "fp64")
+    P = usp.Simulation(w).init_particles().particles()
+    pin = {k: torch.from_numpy(np.ascontiguousarray(P[k])).pin_memory() for k in ("pos", "vel", "pid")}
+    a = usp.Simulation(w).set_particles(P["pos"].copy(), P["vel"].copy(), P["pid"].copy())
+    b = usp.Simulation(w).set_particles(pin["pos"].numpy(), pin["vel"].numpy(), pin["pid"].numpy())
+    for t in pin.values():
+        t.zero_()
+    from tests._util import KB_M_AR, assert_particles_close, by_pid
+    pa, pb = by_pid(a.particles()), by_pid(b.particles())
+    for k in ("pid", "pos", "vel", "cell"):
+        assert np.array_equal(pa[k], pb[k]), k
+    assert len(pa["pid"]) == len(P["pid"])
+    # next_pid found on the device (USP_NEXT_PID_AUTO) on both paths, or as given
+    assert a.info()["next_pid"] == b.info()["next_pid"] == int(P["pid"].max()) + 1
+    c = usp.Simulation(w).set_particles(P["pos"], P["vel"], P["pid"], next_pid=123457)
+    assert c.info()["next_pid"] == 123457
+    # stepped: the within-cell order of the atomic scatter, and with it the
+    # summation order of the moments, differs from run to run
+    a.step(3)
+    b.step(3)
+    dy = (w["grid"]["hi"][1] - w["grid"]["lo"][1]) / w["grid"]["ny"]
+    assert_particles_close(a.particles(), b.particles(), (KB_M_AR * W.T0) ** 0.5, dy,
+                           rtol=1e-12 if pipeline == "plain" else 1e-4, check_cells=False)
+
+
 def test_fused_empty_and_single_particle(usp):
     """Degenerate loads: no particle at all, and one particle (no cell can
     relax: fewer than two particles)."""
@@ -407,6 +441,7 @@ def test_fused_empty_and_single_particle(usp):
     pos = np.array([[0.0, w["grid"]["lo"][1] + 0.37 * h]])
     vel = np.array([[10.0, 120.0, -5.0]])
     one = usp.Simulation(w).set_particles(pos, vel, np.array([7], dtype=np.uint32))
+    assert g.info()["next_pid"] == 0 and one.info()["next_pid"] == 8
     one.step(5)
     P = one.particles()
     assert P["pid"].tolist() == [7]
