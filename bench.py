@@ -33,7 +33,7 @@ FUSED_SRC = os.path.join(ROOT, "paper_1808_03801_gb300", "csrc", "usp_fused.cu")
 # dram__bytes_write.sum of the 32-tube Sod case divided by its particles),
 # valid only for the k_g2 source with this SHA-1; any other source reports
 # traffic as null until it is captured again
-KG2_TRAFFIC = {"sha1": "457b722e98bf31a08f53d7535213d4a2cfddae41", "bytes_per_particle": 39.01}
+KG2_TRAFFIC = {"sha1": "c8068930dd8fadfe0692a64c667f3a533efa6603", "bytes_per_particle": 38.84}
 
 
 def parse():

@@ -1413,15 +1413,31 @@ __global__ void __launch_bounds__(32 * (NC + 1), 16 / (NC + 1)) k_g2(const SimDe
 // FP32 sums of the centred velocities do not cancel; k_params_f promotes
 // them to FP64 with the shift taken into account.
 // ---------------------------------------------------------------------------
-constexpr int kG1Pre = 64;    // slots of a cell loaded ahead (a multiple of 32)
+constexpr int kG1Warps = 4;     // warps per block; a block takes one 32-cell tile at a time
+constexpr int kG1Stage = 384;   // slots of one pipeline stage (a multiple of 4)
 
-__global__ void __launch_bounds__(256) k_g1(const SimDev* __restrict__ sims, const int2* __restrict__ tiles,
-                                            const int* __restrict__ ntiles) {
-    __shared__ uint32_t spl_all[8][32];
+// per-lane asynchronous global -> shared copies (completion waited with
+// cp.async.wait_group by the issuing lane, then made visible to the warp
+// with __syncwarp)
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+__global__ void __launch_bounds__(32 * kG1Warps) k_g1(const SimDev* __restrict__ sims, const int2* __restrict__ tiles,
+                                                     const int* __restrict__ ntiles) {
+    __shared__ uint32_t spl_all[kG1Warps][32];
     // the tile's per-cell headers, fetched in one round for all 32 cells:
     // bucket start, particles in the bucket, arrivals, and the shift u_s
     __shared__ uint32_t h_base[kCTile], h_nb[kCTile], h_arr[kCTile];
     __shared__ float4 h_us[kCTile];
+    // each warp's two pipeline stages of the three velocity planes
+    __shared__ __align__(16) float stage[kG1Warps][2][3][kG1Stage];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     __shared__ SimDev sim_sh;
     const int nt = *ntiles;
@@ -1448,36 +1464,53 @@ __global__ void __launch_bounds__(256) k_g1(const SimDev* __restrict__ sims, con
         const float* V0 = (const float*)s.vel[q][0];
         const float* V1 = (const float*)s.vel[q][1];
         const float* V2 = (const float*)s.vel[q][2];
-        // the first kG1Pre slots of the warp's next cell are loaded while the
-        // current one is summed and reduced, so each cell's first round trip
-        // overlaps the previous cell's work
-        float px[kG1Pre / 32], py[kG1Pre / 32], pz[kG1Pre / 32];
-        auto prefetch = [&](int c) {
-            const bool live = c < kCTile && tile.y + c < K;
-            const uint32_t b0 = live ? h_base[c] : 0u, n0 = live ? h_nb[c] : 0u;
-#pragma unroll
-            for (int r = 0; r < kG1Pre / 32; ++r) {
-                const uint32_t j = (uint32_t)(32 * r + lane);
-                const bool ok = j < n0;
-                px[r] = ok ? __ldcs(V0 + b0 + j) : 0.0f;
-                py[r] = ok ? __ldcs(V1 + b0 + j) : 0.0f;
-                pz[r] = ok ? __ldcs(V2 + b0 + j) : 0.0f;
+        // The warp's cells (cc = warp, warp + kG1Warps, ...) are read as a
+        // sequence of chunks of at most kG1Stage slots, each copied into one
+        // of two stages while the chunk before it is summed: a cell's whole
+        // bucket is in flight at once, and its round trip overlaps the
+        // previous chunk's work.  (c, o) is the next chunk to copy.
+        auto live = [&](int c) { return c < kCTile && tile.y + c < K; };
+        auto copy_chunk = [&](int c, uint32_t o, int b) {
+            const uint32_t g = h_base[c] + o;
+            const uint32_t len = min(h_nb[c] - o, (uint32_t)kG1Stage);
+            float* d0 = stage[warp][b][0];
+            float* d1 = stage[warp][b][1];
+            float* d2 = stage[warp][b][2];
+            if ((g & 3u) == 0u) {
+                // 16-byte groups up to the next multiple of four slots: the
+                // bucket start and the capacity are multiples of four, so the
+                // copy stays inside the plane
+                const uint32_t n4 = (len + 3u) >> 2;
+                for (uint32_t k = lane; k < n4; k += 32) {
+                    cp_async16(d0 + 4 * k, V0 + g + 4 * k);
+                    cp_async16(d1 + 4 * k, V1 + g + 4 * k);
+                    cp_async16(d2 + 4 * k, V2 + g + 4 * k);
+                }
+            } else {   // the compact layout right after a set-up sort
+                for (uint32_t k = lane; k < len; k += 32) {
+                    cp_async4(d0 + k, V0 + g + k);
+                    cp_async4(d1 + k, V1 + g + k);
+                    cp_async4(d2 + k, V2 + g + k);
+                }
             }
+            cp_async_commit();
         };
-        prefetch(warp);
-        for (int cc = warp; cc < kCTile; cc += 8) {
+        // the chunk after (c, o), skipping cells with an empty bucket
+        auto advance = [&](int& c, uint32_t& o) {
+            o += kG1Stage;
+            if (o < h_nb[c]) return;
+            o = 0;
+            c += kG1Warps;
+            while (live(c) && h_nb[c] == 0) c += kG1Warps;
+        };
+        int ic = warp;
+        uint32_t io = 0;
+        while (live(ic) && h_nb[ic] == 0) ic += kG1Warps;
+        if (live(ic)) copy_chunk(ic, io, 0);
+        int done = 0;   // chunks summed so far (stage done & 1 holds the next)
+        for (int cc = warp; live(cc); cc += kG1Warps) {
             const int cell = tile.y + cc;
-            if (cell >= K) break;
-            const uint32_t base = h_base[cc];
             const uint32_t nb = h_nb[cc];
-            float cx[kG1Pre / 32], cy[kG1Pre / 32], cz[kG1Pre / 32];
-#pragma unroll
-            for (int r = 0; r < kG1Pre / 32; ++r) {
-                cx[r] = px[r];
-                cy[r] = py[r];
-                cz[r] = pz[r];
-            }
-            prefetch(cc + 8);
             const uint32_t arrived = h_arr[cc];
             const float4 us = h_us[cc];
             const float u0 = us.x, u1 = us.y, u2 = us.z;
@@ -1495,12 +1528,25 @@ __global__ void __launch_bounds__(256) k_g1(const SimDev* __restrict__ sims, con
                 S[6] += C0 * C1; S[7] += C0 * C2; S[8] += C1 * C2;
                 S[9] += c2 * C0; S[10] += c2 * C1; S[11] += c2 * C2;
             };
-#pragma unroll
-            for (int r = 0; r < kG1Pre / 32; ++r)
-                if ((uint32_t)(32 * r + lane) < nb) add(cx[r], cy[r], cz[r]);
+            for (uint32_t o = 0; o < nb; o += kG1Stage) {
+                // (ic, io) is this chunk: copy the next one, then wait for this one
+                advance(ic, io);
+                if (live(ic)) {
+                    copy_chunk(ic, io, (done + 1) & 1);
+                    cp_async_wait<1>();
+                } else {
+                    cp_async_wait<0>();
+                }
+                __syncwarp();
+                const float* b0 = stage[warp][done & 1][0];
+                const float* b1 = stage[warp][done & 1][1];
+                const float* b2 = stage[warp][done & 1][2];
+                const uint32_t len = min(nb - o, (uint32_t)kG1Stage);
 #pragma unroll 4
-            for (uint32_t j = kG1Pre + lane; j < nb; j += 32)
-                add(__ldcs(V0 + base + j), __ldcs(V1 + base + j), __ldcs(V2 + base + j));
+                for (uint32_t j = lane; j < len; j += 32) add(b0[j], b1[j], b2[j]);
+                __syncwarp();   // the stage is refilled by the copy issued two chunks on
+                ++done;
+            }
             for (uint32_t j = nb + lane; j < n; j += 32) {   // spill-list entries of the cell
                 const uint32_t i = spl_all[warp][j - nb];
                 add(s.sp_vel[q][0][i], s.sp_vel[q][1][i], s.sp_vel[q][2][i]);
@@ -2295,7 +2341,7 @@ void launch_fused_inject(const Launch& L) {
 
 void launch_fused_moments(const Launch& L, int R) {
     (void)R;
-    k_g1<<<L.grid_c, 256, 0, L.stream>>>(L.sims, L.ctiles, L.nctiles);
+    k_g1<<<L.grid_c, 32 * kG1Warps, 0, L.stream>>>(L.sims, L.ctiles, L.nctiles);
 }
 
 void launch_fused_params(const Launch& L) { k_params_f<<<L.grid_c, 32, 0, L.stream>>>(L.sims, L.ctiles, L.nctiles); }
