@@ -62,7 +62,8 @@ def test_invalid_arguments_rejected_without_gpu(mutate):
 
 def test_struct_layouts_match_header(tmp_path):
     """The ctypes mirrors of the public structs have the C compiler's sizes
-    and field offsets (include/usp.h compiled as plain C)."""
+    and field offsets, and the binding's USP_NEXT_PID_AUTO is the header's
+    (include/usp.h compiled as plain C)."""
     import shutil
     import subprocess
     cc = shutil.which("gcc") or shutil.which("cc")
@@ -76,6 +77,7 @@ def test_struct_layouts_match_header(tmp_path):
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
         for f in py._fields_:
             lines.append(f'printf("{cname} {f[0]} %zu\\n", offsetof({cname}, {f[0]}));')
+    lines.append('printf("USP_NEXT_PID_AUTO value %u\\n", USP_NEXT_PID_AUTO);')
     lines.append("return 0; }")
     src = tmp_path / "layout.c"
     src.write_text("\n".join(lines))
@@ -84,6 +86,7 @@ def test_struct_layouts_match_header(tmp_path):
     subprocess.run([cc, "-std=c99", "-I", inc, str(src), "-o", str(exe)], check=True)
     out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
     got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l}
+    assert got[("USP_NEXT_PID_AUTO", "value")] == U.NEXT_PID_AUTO
     for cname, py in structs.items():
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for f in py._fields_:
