@@ -297,8 +297,12 @@ def e2e_rate(U, W, torch, batch, pipeline, steps, warmup, stream):
     B = U.Batch(hbm_budget=200 << 30, max_sims=batch, stream=stream)
 
     def solve(nsteps):
+        # every upload first (each returns once its arrays are read, its sort
+        # running on the tube's stream), then the admissions, which wait for
+        # each tube's stream
         for s, h in zip(sims, hosts):
             s.set_particles(h["pos"], h["vel"], h["pid"])
+        for s in sims:
             B.admit(s)
         B.step(nsteps)
         for s in sims:
