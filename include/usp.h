@@ -221,7 +221,10 @@ typedef struct {
 } usp_region;
 
 /* Optional device allocator (for example a framework's caching allocator).
- * alloc returns a device pointer or NULL; NULL allocator => cudaMalloc. */
+ * alloc returns a device pointer aligned to 256 bytes (as cudaMalloc's are:
+ * the kernels copy particle planes in 16-byte units) or NULL; a pointer
+ * with a coarser alignment is handed back to free and the call that needed
+ * it fails with OOM.  NULL allocator => cudaMalloc. */
 typedef struct {
     void* (*alloc)(size_t bytes, void* ctx);
     void (*free)(void* ptr, void* ctx);

@@ -79,6 +79,7 @@ struct usp_handle {
     bool own_stream = false;
     usp_allocator alloc{};
     bool has_alloc = false;
+    bool misaligned_alloc = false;    // the last allocator call was rejected for its alignment
     std::vector<void*> cell_allocs;   // per-cell arrays (lifetime of the handle)
     std::vector<void*> part_allocs;   // particle storage (replaced on re-init)
     size_t cell_bytes = 0, part_bytes = 0;
@@ -127,7 +128,11 @@ struct usp_batch {
 // helpers
 // ---------------------------------------------------------------------------
 static int fail(usp_handle* h, int code, const std::string& msg) {
-    if (h) h->err = msg;
+    if (h) {
+        h->err = msg;
+        if (h->misaligned_alloc) h->err += " (the allocator returned memory not aligned to 256 bytes)";
+        h->misaligned_alloc = false;
+    }
     return code;
 }
 
@@ -143,6 +148,11 @@ static void* dalloc(usp_handle* h, size_t bytes) {
     void* p = nullptr;
     if (h->has_alloc) {
         p = h->alloc.alloc(bytes, h->alloc.ctx);
+        if (p && ((uintptr_t)p & 255u) != 0) {   // the bulk copies need 16-byte aligned planes
+            h->alloc.free(p, h->alloc.ctx);
+            h->misaligned_alloc = true;
+            p = nullptr;
+        }
     } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
         cudaGetLastError();
         p = nullptr;
