@@ -335,3 +335,26 @@ def test_fp64_ablation_parity(usp, name, opts):
     scale = np.maximum(np.abs(fo), np.abs(fo).max(axis=1, keepdims=True) * 1e-3)
     assert np.all(np.abs(fg - fo) <= 1e-10 * scale + 1e-300)
     assert g.info()["counters"][0] == o.counters()[0]
+
+
+def test_torch_allocator_handle_matches_cudamalloc(usp):
+    """A handle whose device memory comes from PyTorch's caching allocator
+    (usp_allocator) holds it in torch's accounting while it lives, hands it
+    all back on close, and steps like a handle on cudaMalloc (FP64, to the
+    rounding of the sums)."""
+    import torch
+    w = W.couette(ny=20, ppc=50, precision="fp64", seed=3)
+    torch.cuda.synchronize()
+    before = torch.cuda.memory_allocated()
+    a = usp.Simulation(w, allocator="torch").init_particles()
+    held = torch.cuda.memory_allocated() - before
+    assert held >= a.info()["device_bytes"] > 0
+    b = usp.Simulation(w).init_particles()
+    a.step(5)
+    b.step(5)
+    dy = (w["grid"]["hi"][1] - w["grid"]["lo"][1]) / w["grid"]["ny"]
+    assert_particles_close(a.particles(), b.particles(), math.sqrt(KB_M_AR * W.T0), dy)
+    a.close()
+    b.close()
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() == before
